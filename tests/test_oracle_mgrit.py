@@ -1,0 +1,154 @@
+"""Pins of the oracle's sequential stepper and MGRIT against mathematics and
+against Table 3 (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import coefficients as co
+from oracle import lfa
+from oracle import mgrit
+from oracle import operators as ops
+from oracle import rng
+from workloads import ic_sin4
+
+
+def test_splitmix64_reference_stream(golden):
+    rows = golden("splitmix64.txt")
+    seed = int(rows[0][1])
+    want = [int(r[0]) for r in rows[1:]]
+    assert [int(x) for x in rng.sequence(seed, len(want))] == want
+    # the grid form is the same stream: counter n*nx + i + 1
+    g = rng.uniform_grid(seed, np.array([0]), 5)
+    assert np.allclose(g[0], np.array(want, dtype=np.float64) / 2.0 ** 64, rtol=0, atol=2.0 ** -52)
+
+
+@pytest.mark.parametrize("p,kind,c", [(1, "erk", 0.85), (3, "erk", 1.3), (3, "sdirk", 5.0)])
+def test_sequential_matches_fourier_closed_form(p, kind, c):
+    """u_n = F^{-1}[lambda(omega)^n F u_0] for the circulant one-step map."""
+    nx, nt = 64, 40
+    u0 = ic_sin4(nx)
+    Phi = ops.FineOperator(p, kind, p, c)
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    u = mgrit.sequential(Phi, g)
+    omega = 2 * np.pi * np.fft.fftfreq(nx)
+    lam = Phi.symbol(omega)
+    for n in (1, 7, nt):
+        want = np.real(np.fft.ifft(lam ** n * np.fft.fft(u0)))
+        assert np.max(np.abs(u[n] - want)) < 1e-12
+
+
+def _space_time_matrix(Phi, nx, nt):
+    """Block lower-bidiagonal A with rows u_0 = b_0, u_n - Phi u_{n-1} = b_n."""
+    P = np.stack([Phi.apply(e) for e in np.eye(nx)], axis=1)  # columns Phi e_j
+    A = np.eye((nt + 1) * nx)
+    for n in range(1, nt + 1):
+        A[n * nx:(n + 1) * nx, (n - 1) * nx:n * nx] = -P
+    return A
+
+
+@pytest.mark.parametrize("p,kind,c,m,levels", [(1, "erk", 0.85, 4, 2), (3, "erk", 1.0, 2, 3),
+                                               (3, "sdirk", 5.0, 4, 2)])
+def test_mgrit_converges_to_dense_space_time_solve(p, kind, c, m, levels):
+    """Brute force on a tiny grid: LAPACK solve of the assembled space-time
+    system == sequential stepping == converged MGRIT."""
+    nx, nt = 8, 32
+    u0 = ic_sin4(nx) + 0.1 * np.arange(nx) / nx
+    h = mgrit.Hierarchy(p, kind, p, c, m, levels)
+    A = _space_time_matrix(h.fine, nx, nt)
+    b = np.zeros((nt + 1) * nx)
+    b[:nx] = u0
+    direct = np.linalg.solve(A, b).reshape(nt + 1, nx)
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = mgrit.sequential(h.fine, g)
+    assert np.max(np.abs(seq - direct)) < 1e-12
+    res = mgrit.solve(h, u0, nt, nu=1, tol=1e-13, max_iter=60, seed=11)
+    assert res["converged"]
+    assert np.max(np.abs(res["u"] - direct)) < 1e-10
+
+
+def test_two_level_f_relaxation_exact_after_nt_over_m_iterations():
+    """With F-relaxation only, iteration k makes C-point k exact, so two-level
+    MGRIT solves the system after nt/m iterations whatever Psi is (Sec. 2.2)."""
+    nx, nt, m = 16, 48, 4
+    u0 = ic_sin4(nx)
+    h = mgrit.Hierarchy(3, "erk", 3, 1.2, m, 2)
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = mgrit.sequential(h.fine, g)
+    res = mgrit.solve(h, u0, nt, nu=0, tol=0.0, max_iter=nt // m, seed=2)
+    exact_err = np.max(np.abs(res["u"] - seq))
+    assert exact_err < 1e-13
+    res_short = mgrit.solve(h, u0, nt, nu=0, tol=0.0, max_iter=nt // m - 1, seed=2)
+    assert np.max(np.abs(res_short["u"] - seq)) > 1e-11
+
+
+def test_ideal_coarse_operator_converges_in_one_iteration():
+    """Psi = Phi^m makes the coarse correction exact (Sec. 2.2)."""
+    nx, nt, m = 16, 64, 4
+    u0 = ic_sin4(nx)
+    fine = ops.FineOperator(3, "erk", 3, 1.2)
+    h = mgrit.Hierarchy(3, "erk", 3, 1.2, m, 2, coarse=ops.PowerOperator(fine, m))
+    res = mgrit.solve(h, u0, nt, nu=1, tol=1e-12, max_iter=5, seed=3)
+    assert res["iterations"] == 1
+    assert res["history"][1] < 1e-13 * res["history"][0]
+
+
+def test_mgrit_mass_conservation():
+    nx, nt = 32, 128
+    u0 = ic_sin4(nx)
+    h = mgrit.Hierarchy(1, "erk", 1, 0.85, 4, 3)
+    res = mgrit.solve(h, u0, nt, nu=1, tol=1e-12, max_iter=40, seed=0)
+    mass = res["u"].sum(axis=1)
+    assert np.max(np.abs(mass - u0.sum())) < 1e-9
+
+
+def _levels_until_two(nt, m):
+    L, N = 1, nt
+    while N // m >= 2:
+        N //= m
+        L += 1
+    return L
+
+
+def _table3_rows(golden, nx_max):
+    rows = []
+    for kind, nx, nt, m, two, vc in golden("table3_iterations.txt"):
+        if int(nx) <= nx_max:
+            rows.append((kind, int(nx), int(nt), int(m), int(two), int(vc)))
+    return rows
+
+
+def test_table3_iteration_counts_small(golden):
+    """Table 3 (2^6 x 2^8): iteration counts within 2 of the printed ones,
+    two-level and V-cycle (coarsen until fewer than two time points)."""
+    cmax = co.cfl_limit(3)
+    for kind, nx, nt, m, two, vc in _table3_rows(golden, 64):
+        c = 0.85 * cmax if kind == "erk" else 5.0
+        u0 = ic_sin4(nx)
+        r2 = mgrit.solve(mgrit.Hierarchy(3, kind, 3, c, m, 2), u0, nt, tol=1e-10, max_iter=40)
+        assert abs(r2["iterations"] - two) <= 2, (kind, nx, m, r2["iterations"], two)
+        L = _levels_until_two(nt, m)
+        rv = mgrit.solve(mgrit.Hierarchy(3, kind, 3, c, m, L), u0, nt, tol=1e-10, max_iter=40)
+        assert abs(rv["iterations"] - vc) <= 2, (kind, nx, m, rv["iterations"], vc)
+
+
+@pytest.mark.slow
+def test_table3_iteration_counts_medium(golden):
+    cmax = co.cfl_limit(3)
+    for kind, nx, nt, m, two, vc in _table3_rows(golden, 256):
+        if nx != 256:
+            continue
+        c = 0.85 * cmax if kind == "erk" else 5.0
+        r2 = mgrit.solve(mgrit.Hierarchy(3, kind, 3, c, m, 2), ic_sin4(nx), nt, tol=1e-10, max_iter=40)
+        assert abs(r2["iterations"] - two) <= 2, (kind, nx, m, r2["iterations"], two)
+
+
+def test_measured_factor_near_lfa():
+    """The final-iteration factor of two-level MGRIT on a long interval is
+    close to (and not above) the LFA prediction (Sec. 5.1)."""
+    nx, nt, m, c = 256, 1024, 4, 0.85
+    res = mgrit.solve(mgrit.Hierarchy(1, "erk", 1, c, m, 2), ic_sin4(nx), nt, tol=1e-10, max_iter=30)
+    pred = lfa.two_level_factor(1, "erk", c, m)
+    assert res["converged"]
+    assert 0.5 * pred < res["factor"] < 1.15 * pred
