@@ -1,0 +1,243 @@
+#!/usr/bin/env python
+"""Benchmark: space-time DOF/s of a full MGRIT solve to a 1e-10 relative
+residual on one GB300, against GPU sequential time-stepping and the CPU oracle.
+
+Workload (one "step" = one whole solve, every row of the hot path):
+  1D periodic advection, nx = 4096, nt = 16384, 3rd-order upwind + ERK3
+  (c = 0.85), FP64, V-cycle MGRIT with m = 8 and 4 levels, FCF relaxation,
+  corrected semi-Lagrangian coarse operators, IC sin^4(pi x) + N(0, 1e-2)
+  noise, random initial iterate (seed 0), stop at ||r|| <= 1e-10 ||r_0||.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs are independent replicas (one solve per rank; the path does
+not shard on one node here): value = N * DOF / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="advection1d_erk3u3_vcycle_fp64", nx=4096, nt=16384, p=3, cfl=0.85, m=8,
+                levels=4, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4+N(0,1e-2)")
+METRIC = "space-time DOF/s to 1e-10 residual vs GPU seq. stepping; p50/p99 latency"
+UNIT = "DOF/s"
+# FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM (4 flop/clk/SM) x 2.07 GHz
+FP64_PEAK_FLOPS = 152 * 4 * 2.07e9
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def clocks_sampler_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_sampler_stop(p, f, path, device):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(device):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def cpu_baseline(sample_nt=2048):
+    """The CPU oracle (plain numpy FP64 V-cycle MGRIT, as it stands) on a
+    bounded sample of the workload: the same nx, scheme, m, levels and
+    tolerance over the first sample_nt steps."""
+    from oracle import mgrit as omg
+    from workloads import ic_sin4_noise
+    w = WORKLOAD
+    h = omg.Hierarchy(w["p"], "erk", w["p"], w["cfl"], w["m"], w["levels"])
+    u0 = ic_sin4_noise(w["nx"], seed=w["seed"])
+    t = time.perf_counter()
+    r = omg.solve(h, u0, sample_nt, nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"])
+    dt = time.perf_counter() - t
+    return {"value": w["nx"] * sample_nt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "nx=%d, nt=%d (first %d of %d steps), same scheme/m/levels/tol, %d iterations, %.1f s"
+                      % (w["nx"], sample_nt, sample_nt, w["nt"], r["iterations"], dt)}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sample_nt=512)
+        if i >= args.warmup:
+            times.append(cb)
+    vals = [c["value"] for c in times]
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "nx": WORKLOAD["nx"], "nt": 512,
+                       "note": "CPU oracle on a 512-step sample of the 16384-step workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": times[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2209_06916_gb300 as pkg
+    from workloads import ic_sin4_noise
+
+    w = WORKLOAD
+    nx, nt, m = w["nx"], w["nt"], w["m"]
+    stream = torch.cuda.current_stream()
+    prm = pkg.make_params(nx, nt, w["cfl"], w["p"], m=m, levels=w["levels"], nu=w["nu"], tol=w["tol"],
+                          max_iter=w["max_iter"], seed=w["seed"])
+    s = pkg.Solver(prm, stream=stream.cuda_stream)
+    u0_h = ic_sin4_noise(nx, seed=w["seed"])
+    u0 = torch.tensor(u0_h, dtype=torch.float64, device="cuda")
+    out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+
+    for _ in range(args.warmup):
+        st = s.solve(u0, out)
+    torch.cuda.synchronize()
+
+    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    cp, cf = clocks_sampler_start(clk_path)
+    time.sleep(0.5)
+
+    launches0 = s.launch_count()
+    s.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        st = s.solve(u0, out)
+        iters.append(st["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read()
+    s.profile(False)
+    launches = s.launch_count() - launches0
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    u0_pin = torch.tensor(u0_h, dtype=torch.float64).pin_memory()
+    out_pin = torch.empty((nt // m + 1, nx), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.solve(u0_pin, out_pin)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    clocks = clocks_sampler_stop(cp, cf, clk_path, local)
+
+    # accuracy of the benched solve against the FP64 ... (reported, not a gate)
+    dof = nx * nt
+    value = ws * dof * args.steps / (ms / 1e3)
+    cnt, kms, kfl = prof["stencil0"]
+    achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "stencil_rows_kernel<double,4> (level-0 composite Phi^m)",
+            "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+            "peak_source": "derived FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
+            "launches": cnt, "ms_per_launch": kms / max(1, cnt),
+            "share_of_step": kms / ms if ms > 0 else None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "nx": nx, "nt": nt, "scheme": "ERK3+U3", "cfl": w["cfl"],
+                       "m": m, "levels": w["levels"], "relax": "FCF", "tol": w["tol"],
+                       "iterations": iters, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (
+                           (2 * (nt // m + 1) + (nt // m + 1) + 2 * (nt // m ** 2 + 1)) * nx * 8 / 1e6)},
+            "roofline": roof,
+            "e2e": {"value": ws * dof * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8},
+            "gpu_launches": launches, "clocks": clocks,
+            "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * mgrit.h -- C ABI of the GB300 (sm_103a) MGRIT library for method-of-lines
+ * discretisations of 1D periodic linear advection (De Sterck, Falgout,
+ * Krzysik, Schroder, arXiv 2209.06916).
+ *
+ * Problem (Sec. 2.1, Eq. ad and Eq. one-step-general): u_t + alpha u_x = 0 on
+ * [-1, 1) with periodic boundaries, nx equispaced points x_i = -1 + i h
+ * (h = 2/nx), nt steps of size dt, CFL number c = alpha dt / h (Sec. 4.3).
+ * The fine one-step map is Phi = R_q(-c L_p) (Eq. MOL_M_def): order-p upwind
+ * finite differences L_p (Sec. 4.1) with an ERKq or SDIRKq method (Sec. 4.2).
+ * Coarse level l >= 1 uses the corrected semi-Lagrangian operator
+ * Phi^{(m^l dt)} = (I - phi_l D^{(p+1)}_2)^{-1} S_p^{(m^l dt)} (Eq.
+ * MOL-SL-corrected and its multilevel form with the phi recursion, Sec. 6.2).
+ * MGRIT itself is the linear two-level / V-cycle method of Sec. 2.2 with
+ * F(CF)^nu pre-relaxation and F post-relaxation.
+ *
+ * Conventions for every entry point
+ *  - Return value: MGRIT_OK (0) or a negative MGRIT_ERR_* code; the text of a
+ *    code is mgrit_strerror(code).  No entry point aborts the process.
+ *  - Pointers marked "host or device" may point to host memory or to device
+ *    memory of the handle's GPU; the kind is detected with
+ *    cudaPointerGetAttributes.  "device" pointers must be device memory.
+ *  - Vectors are FP64, row-major: index [k * nx + i] for time row k and grid
+ *    index i.  The caller owns every pointer it passes; the handle owns every
+ *    buffer it allocates (freed by mgrit_destroy).
+ *  - All GPU work of a handle is issued on the stream given to mgrit_setup
+ *    (0 = the legacy default stream).  Entry points that return host results
+ *    synchronise that stream before returning.
+ *  - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef MGRIT_H_
+#define MGRIT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define MGRIT_OK 0
+#define MGRIT_ERR_INVALID_ARG -1   /* bad size / parameter / pointer            */
+#define MGRIT_ERR_OOM -2           /* device allocation failed or over budget   */
+#define MGRIT_ERR_NOT_CONVERGED -3 /* max_iter reached; stats are filled        */
+#define MGRIT_ERR_DIVERGED -4      /* residual non-finite or growing 1e3-fold    */
+#define MGRIT_ERR_TIMEOUT -5       /* a bounded device-side wait gave up        */
+#define MGRIT_ERR_CUDA -6          /* a CUDA runtime call failed                */
+#define MGRIT_ERR_UNSTABLE -7      /* a coarse correction matrix is singular or */
+                                   /* has an unstable factorisation             */
+#define MGRIT_ERR_UNSUPPORTED -8   /* valid parameters this build cannot run    */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define MGRIT_ERK 0   /* explicit RK, stability polynomial R_q (Sec. 4.2)      */
+#define MGRIT_SDIRK 1 /* singly diagonally implicit RK (Sec. 4.2)              */
+
+#define MGRIT_FP64 0  /* every kernel in FP64                                  */
+#define MGRIT_MIXED 1 /* FP32 relaxation sweeps inside FP64 iterative          */
+                      /* refinement: FP64 C-point residual, norm, coarsest    */
+                      /* solve and correction solves                          */
+
+#define MGRIT_MAX_LEVELS 16
+#define MGRIT_MAX_HISTORY 128
+
+/* ---- parameters -------------------------------------------------------- */
+typedef struct mgrit_params {
+  int64_t nx;       /* grid points, 32 <= nx, nx % 8 == 0                       */
+  int64_t nt;       /* time steps; nt % m^(levels-1) == 0                       */
+  double cfl;       /* c = alpha dt / h, absolute (not a fraction of c_max)     */
+  double alpha;     /* wave speed > 0 (only c enters the discrete operators)    */
+  int order_p;      /* upwind order p in {1, 3, 5} (odd: Sec. 6.3)              */
+  int rk_kind;      /* MGRIT_ERK or MGRIT_SDIRK                                 */
+  int rk_order_q;   /* q; 0 means q = p.  ERK q = p only; SDIRK q in 1..5       */
+  int m;            /* coarsening factor >= 2                                   */
+  int levels;       /* levels incl. the fine one, 2 <= levels <= 16; 0 means    */
+                    /* "coarsen until fewer than two time points" (Sec. 6.3)    */
+  int nu;           /* CF sweeps in the pre-relaxation F(CF)^nu, 0 <= nu <= 4   */
+  double tol;       /* stop when ||r_it|| <= tol ||r_0|| (default 1e-10)        */
+  int max_iter;     /* iteration cap (default 30, Sec. 6.3)                     */
+  int precision;    /* MGRIT_FP64 or MGRIT_MIXED                                */
+  uint64_t seed;    /* seed of the random initial iterate (SplitMix64)          */
+} mgrit_params;
+
+/* ---- statistics -------------------------------------------------------- */
+typedef struct mgrit_stats {
+  int iterations;      /* coarse corrections applied before the stop test    */
+  int converged;       /* 1 if ||r|| <= tol ||r_0||                          */
+  int levels;          /* levels actually used                               */
+  int history_len;     /* entries in rnorm_history                           */
+  double rnorm0;       /* ||r_0||                                            */
+  double rnorm;        /* last residual norm                                 */
+  double conv_factor;  /* rnorm_it / rnorm_{it-1} at the last iteration      */
+  double rnorm_history[MGRIT_MAX_HISTORY];
+  double ms_total;     /* wall time of mgrit_solve (host clock)              */
+  int inner_cycles;    /* MIXED: FP32 V-cycles run in total                  */
+  int outer_iterations;/* MIXED: FP64 residual evaluations after the first   */
+} mgrit_stats;
+
+typedef struct mgrit_handle mgrit_handle;
+
+/*
+ * mgrit_setup -- validate *params, build the level hierarchy and allocate all
+ * device buffers on the current CUDA device.
+ *   params : host pointer, read only.  Section and equation of each field are
+ *            given above.  Derived per-level data (SL shift k_l and eps_l,
+ *            phi_l, Phi^m stencil, factorised correction solves) are computed
+ *            on the host in FP64 (Sec. 3, Lemma 6.1, Sec. 6.2).
+ *   stream : cudaStream_t (as void*) on which all work of the handle runs.
+ *   out    : receives the new handle (NULL on failure).
+ * Errors: INVALID_ARG (sizes, p even, nt % m^(levels-1), stencil wider than
+ * nx), UNSTABLE (singular correction matrix), OOM, CUDA.
+ */
+int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out);
+
+/* Release every buffer of the handle (NULL is accepted). */
+int mgrit_destroy(mgrit_handle* h);
+
+/* Static text of an error code. */
+const char* mgrit_strerror(int code);
+
+/*
+ * mgrit_set_initial -- set the initial condition u0 (nx values, host or
+ * device) and the initial C-point iterate of level 0.  init (host or device,
+ * (nt/m + 1) * nx values for time rows n = k m) may be NULL: then the rows
+ * k >= 1 are uniform random in [0, 1) from SplitMix64 with params.seed and
+ * counter n * nx + i + 1 (Sec. 5.2 setup: random except at t = 0).  Row 0 is
+ * always u0.
+ */
+int mgrit_set_initial(mgrit_handle* h, const double* u0, const double* init);
+
+/*
+ * mgrit_relax -- nu CF sweeps on `level` (Sec. 2.2).  F-points are not
+ * stored: the F-relaxation is implied by every kernel that reads C-points, so
+ * F(CF)^nu amounts to nu C-relaxations, each preceded by the F-relaxation of
+ * its interval.  Level 0 acts on the C-point iterate; level l >= 1 on the
+ * level's C-point unknowns with the RHS last written by mgrit_residual of
+ * level l-1 (zero initial guess if `reset` semantics are wanted: call
+ * mgrit_level_io to clear it).  Asynchronous on the handle's stream.
+ */
+int mgrit_relax(mgrit_handle* h, int level, int nu);
+
+/*
+ * mgrit_residual -- F-relax `level` and form the C-point residual
+ * r_k = g_{km} + Phi_l u_{km-1} - u_{km}, k = 1..N_l/m (Sec. 2.2; r_0 = 0),
+ * store it as the RHS of level+1 (injection) and return ||r||_2 (over all
+ * C-points and grid points) in *norm_out (host pointer; may be NULL).
+ * Synchronises the stream when norm_out is not NULL.
+ */
+int mgrit_residual(mgrit_handle* h, int level, double* norm_out);
+
+/*
+ * mgrit_coarse_apply -- y = Phi_l x for nvec vectors (device pointers, nvec *
+ * nx FP64 each).  level 0: the fine step R_q(-c L_p) (Eq. MOL_M_def);
+ * level l >= 1: (I - phi_l D)^{-1} S_p^{(m^l dt)} (Eq. MOL-SL-corrected /
+ * multilevel form).  x and y must not overlap.  Asynchronous.
+ */
+int mgrit_coarse_apply(mgrit_handle* h, int level, const double* d_in, double* d_out, int64_t nvec);
+
+/*
+ * mgrit_solve -- full MGRIT solve (two-level if levels == 2, else V-cycles):
+ * set_initial(u0, NULL) unless `keep_initial` was requested with
+ * mgrit_set_initial beforehand (u0 == NULL keeps the current state), then
+ * iterate until ||r_it|| <= tol ||r_0|| or max_iter.  u_out (host or device,
+ * may be NULL) receives the (nt/m + 1) * nx level-0 C-point values whose
+ * residual was measured last; stats (host, may be NULL) is filled.
+ * Returns OK, NOT_CONVERGED or DIVERGED (u_out and stats are still written).
+ */
+int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* stats);
+
+/*
+ * mgrit_vcycle -- one MGRIT iteration without the stop test: coarse
+ * correction from the current level-1 RHS (written by mgrit_residual(0)),
+ * then the level-0 pre-relaxation F(CF)^nu and residual; *norm_out (host,
+ * may be NULL) receives the new ||r||.  Used to compare iterates step by step.
+ */
+int mgrit_vcycle(mgrit_handle* h, double* norm_out);
+
+/*
+ * mgrit_level_io -- copy a level buffer to or from the caller.
+ *   field 0: C-point unknowns of the level (level 0: (nt/m+1) rows; level l:
+ *            N_{l+1}+1 rows, N_l = nt/m^l), field 1: RHS g of the level
+ *            (N_l + 1 rows, l >= 1).
+ *   ptr    : host or device, rows * nx doubles; to_device != 0 copies ptr ->
+ *            handle, else handle -> ptr.  *rows_out (may be NULL) gets rows.
+ * Synchronises the stream.
+ */
+int mgrit_level_io(mgrit_handle* h, int level, int field, double* ptr, int to_device, int64_t* rows_out);
+
+/*
+ * mgrit_fine_propagate -- GPU sequential time-stepping u_{n+1} = Phi u_n
+ * (Eq. one-step-general) for nsteps steps from u0 (host or device, nx) into
+ * u_out (host or device, nx), with the fine operator of the handle, in one
+ * persistent launch (the vector stays on chip).  This is the baseline MGRIT
+ * is measured against.  If `every` > 0 and traj (device) is not NULL, rows
+ * n = every, 2 every, ... are also written to traj[(n/every - 1) * nx].
+ */
+int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps,
+                         int64_t every, double* traj);
+
+/*
+ * mgrit_level_info -- host-side derived data of a level (no GPU work):
+ * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
+ * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite
+ * stencil taps (level 0), out[6] = chunk length of the in-block solves.
+ */
+int mgrit_level_info(const mgrit_handle* h, int level, double out[8]);
+
+/* Number of CUDA kernels this handle launched since setup (kernel-launch
+ * counter maintained by the library). */
+int64_t mgrit_launch_count(const mgrit_handle* h);
+
+/*
+ * mgrit_profile -- enable (1) or disable (0) per-kernel timing with CUDA
+ * events recorded on the handle's stream around every launch; enabling
+ * clears the counters.  Not in the paper: measurement support.
+ * mgrit_profile_read -- out[3c+0] launches, out[3c+1] summed device ms,
+ * out[3c+2] algorithmic flops (2 per multiply-add the kernel must do) for
+ * category c = 0 level-0 composite stencil, 1 coarse step kernel,
+ * 2 reductions, 3 sequential stepping.  Synchronises the stream.
+ */
+int mgrit_profile(mgrit_handle* h, int enable);
+int mgrit_profile_read(mgrit_handle* h, double out[12]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGRIT_H_ */

@@ -1,0 +1,219 @@
+"""Python binding of libmgrit.so, the GB300 MGRIT library for method-of-lines
+linear advection (arXiv 2209.06916).  Argument marshalling only: every step
+of the method runs in the library's CUDA kernels.
+
+Arrays: host arrays are numpy float64 (C-contiguous); device arrays are any
+object with ``data_ptr()`` (torch CUDA tensors, float64, contiguous).  The
+library detects the pointer kind itself.
+
+If libmgrit.so is missing this import raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgrit.so")
+
+MGRIT_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "OOM", -3: "NOT_CONVERGED", -4: "DIVERGED", -5: "TIMEOUT",
+    -6: "CUDA", -7: "UNSTABLE", -8: "UNSUPPORTED",
+}
+ERK, SDIRK = 0, 1
+FP64, MIXED = 0, 1
+MAX_HISTORY = 128
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int64), ("nt", ctypes.c_int64), ("cfl", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("order_p", ctypes.c_int), ("rk_kind", ctypes.c_int),
+        ("rk_order_q", ctypes.c_int), ("m", ctypes.c_int), ("levels", ctypes.c_int),
+        ("nu", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("levels", ctypes.c_int),
+        ("history_len", ctypes.c_int), ("rnorm0", ctypes.c_double), ("rnorm", ctypes.c_double),
+        ("conv_factor", ctypes.c_double), ("rnorm_history", ctypes.c_double * MAX_HISTORY),
+        ("ms_total", ctypes.c_double), ("inner_cycles", ctypes.c_int),
+        ("outer_iterations", ctypes.c_int),
+    ]
+
+    def to_dict(self):
+        return {
+            "iterations": self.iterations, "converged": bool(self.converged), "levels": self.levels,
+            "rnorm0": self.rnorm0, "rnorm": self.rnorm, "conv_factor": self.conv_factor,
+            "history": [self.rnorm_history[i] for i in range(self.history_len)],
+            "ms_total": self.ms_total, "inner_cycles": self.inner_cycles,
+            "outer_iterations": self.outer_iterations,
+        }
+
+
+class MgritError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, ERRORS.get(code, "?"), code))
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmgrit.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libmgrit.so not built at %s: run `python -m paper_2209_06916_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.mgrit_setup.argtypes = [ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+    lib.mgrit_destroy.argtypes = [P]
+    lib.mgrit_strerror.argtypes = [ctypes.c_int]
+    lib.mgrit_strerror.restype = ctypes.c_char_p
+    lib.mgrit_set_initial.argtypes = [P, P, P]
+    lib.mgrit_relax.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.mgrit_residual.argtypes = [P, ctypes.c_int, dp]
+    lib.mgrit_coarse_apply.argtypes = [P, ctypes.c_int, P, P, ctypes.c_int64]
+    lib.mgrit_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]
+    lib.mgrit_vcycle.argtypes = [P, dp]
+    lib.mgrit_level_io.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int64)]
+    lib.mgrit_fine_propagate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P]
+    lib.mgrit_level_info.argtypes = [P, ctypes.c_int, dp]
+    lib.mgrit_launch_count.argtypes = [P]
+    lib.mgrit_launch_count.restype = ctypes.c_int64
+    lib.mgrit_profile.argtypes = [P, ctypes.c_int]
+    lib.mgrit_profile_read.argtypes = [P, dp]
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array (host) or a tensor-like (device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if hasattr(a, "dtype") and str(a.dtype) != "torch.float64":
+            raise ValueError("device arrays must be float64")
+        if hasattr(a, "is_contiguous") and not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous")
+        return a.data_ptr()
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _check(code, what):
+    if code != MGRIT_OK:
+        raise MgritError(code, what)
+
+
+def make_params(nx, nt, cfl, p, kind=ERK, q=0, m=4, levels=2, nu=1, tol=1e-10, max_iter=30,
+                precision=FP64, seed=0, alpha=1.0):
+    return Params(nx=nx, nt=nt, cfl=cfl, alpha=alpha, order_p=p, rk_kind=kind, rk_order_q=q, m=m,
+                  levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed)
+
+
+class Solver:
+    """One MGRIT problem (level hierarchy resident on the current GPU)."""
+
+    def __init__(self, params, stream=0):
+        self.lib = load_library()
+        self.params = params
+        h = ctypes.c_void_p()
+        _check(self.lib.mgrit_setup(ctypes.byref(params), ctypes.c_void_p(stream), ctypes.byref(h)),
+               "mgrit_setup")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.mgrit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_initial(self, u0, init=None):
+        _check(self.lib.mgrit_set_initial(self.h, _ptr(u0), _ptr(init)), "mgrit_set_initial")
+
+    def relax(self, level, nu):
+        _check(self.lib.mgrit_relax(self.h, level, nu), "mgrit_relax")
+
+    def residual(self, level):
+        v = ctypes.c_double()
+        _check(self.lib.mgrit_residual(self.h, level, ctypes.byref(v)), "mgrit_residual")
+        return v.value
+
+    def coarse_apply(self, level, d_in, d_out, nvec):
+        _check(self.lib.mgrit_coarse_apply(self.h, level, _ptr(d_in), _ptr(d_out), nvec),
+               "mgrit_coarse_apply")
+
+    def vcycle(self):
+        v = ctypes.c_double()
+        _check(self.lib.mgrit_vcycle(self.h, ctypes.byref(v)), "mgrit_vcycle")
+        return v.value
+
+    def solve(self, u0=None, u_out=None, allow_unconverged=False):
+        st = Stats()
+        code = self.lib.mgrit_solve(self.h, _ptr(u0), _ptr(u_out), ctypes.byref(st))
+        if code != MGRIT_OK and not (allow_unconverged and code in (-3, -4)):
+            raise MgritError(code, "mgrit_solve")
+        d = st.to_dict()
+        d["status"] = code
+        return d
+
+    def level_rows(self, level, field):
+        """Rows of a level buffer: field 0 (C-point unknowns) N_l/m + 1,
+        field 1 (RHS) N_l + 1."""
+        N = int(self.level_info(level)[0])
+        return (N // self.params.m + 1) if field == 0 else (N + 1)
+
+    def level_get(self, level, field):
+        rows = self.level_rows(level, field)
+        out = np.empty((rows, self.params.nx), dtype=np.float64)
+        r = ctypes.c_int64()
+        _check(self.lib.mgrit_level_io(self.h, level, field, _ptr(out), 0, ctypes.byref(r)),
+               "mgrit_level_io")
+        return out
+
+    def level_set(self, level, field, arr):
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+        r = ctypes.c_int64()
+        _check(self.lib.mgrit_level_io(self.h, level, field, _ptr(arr), 1, ctypes.byref(r)),
+               "mgrit_level_io")
+
+    def level_info(self, level):
+        out = (ctypes.c_double * 8)()
+        _check(self.lib.mgrit_level_info(self.h, level, out), "mgrit_level_info")
+        return list(out)
+
+    def fine_propagate(self, u0, u_out, nsteps, every=0, traj=None):
+        _check(self.lib.mgrit_fine_propagate(self.h, _ptr(u0), _ptr(u_out), nsteps, every, _ptr(traj)),
+               "mgrit_fine_propagate")
+
+    def launch_count(self):
+        return int(self.lib.mgrit_launch_count(self.h))
+
+    def profile(self, enable):
+        _check(self.lib.mgrit_profile(self.h, 1 if enable else 0), "mgrit_profile")
+
+    def profile_read(self):
+        """{category: (launches, device ms, algorithmic flops)} for
+        'stencil0' (level-0 composite stencil), 'coarse', 'reduce'."""
+        out = (ctypes.c_double * 12)()
+        _check(self.lib.mgrit_profile_read(self.h, out), "mgrit_profile_read")
+        names = ("stencil0", "coarse", "reduce", "sequential")
+        return {n: (int(out[3 * i]), out[3 * i + 1], out[3 * i + 2]) for i, n in enumerate(names)}

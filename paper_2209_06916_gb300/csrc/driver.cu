@@ -1,0 +1,863 @@
+// Host driver and C ABI of the MGRIT library (see include/mgrit.h).
+//
+// Level data layout in HBM (FP64, row-major rows of nx):
+//   level 0:  uC0[2] -- C-point iterate, nt/m + 1 rows, double buffered so a
+//             C-relaxation reads one buffer and writes the other;
+//   level l:  g_l    -- RHS, N_l + 1 rows (the injected C-point residual of
+//                       level l-1, Sec. 2.2), row 0 is always 0;
+//             uC_l[2] -- C-point unknowns, N_{l+1} + 1 rows (l < L-1).
+// F-points are never stored: every kernel regenerates them from C-points.
+// The post F-relaxation of level 0 is skipped inside the iteration because
+// the next pre-relaxation recomputes every F-point from the C-points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mgrit.h"
+#include "coeffs.h"
+#include "kernels.h"
+
+using namespace mg;
+
+namespace {
+
+struct LevelData {
+  int64_t N = 0;  // steps on the level
+  int64_t K = 0;  // CF-intervals (N / m); 0 on the coarsest level
+  double* uC[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* g = nullptr;
+  // coarse operator (l >= 1)
+  CoarseParams<double> cp;
+  long long kshift = 0;
+  double eps = 0.0, phi = 0.0, phi_q = 0.0;
+};
+
+}  // namespace
+
+struct mgrit_handle {
+  mgrit_params prm;
+  cudaStream_t st = nullptr;
+  int L = 0;
+  int64_t nx = 0;
+  int m = 0;
+  int device = 0;
+  std::unique_ptr<StencilParams<double>> fineM;  // Phi^m composite
+  std::unique_ptr<StencilParams<double>> fine1;  // Phi (one step)
+  int fineM_taps_raw = 0;
+  std::vector<LevelData> lev;
+  double* partials = nullptr;
+  int64_t npart = 0;
+  double* dnorm = nullptr;
+  double* hnorm = nullptr;  // pinned
+  double* du0 = nullptr;
+  int64_t launches = 0;
+  bool have_initial = false;
+  // optional per-category CUDA-event timing (0: level-0 stencil, 1: coarse
+  // step kernel, 2: reductions / utilities, 3: sequential stepping)
+  struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    double flops[4] = {0, 0, 0, 0};
+    int64_t count[4] = {0, 0, 0, 0};
+  } prof;
+};
+
+static cudaEvent_t prof_event(mgrit_handle* h) {
+  if (!h->prof.pool.empty()) {
+    cudaEvent_t e = h->prof.pool.back();
+    h->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch of category `cat` with events when profiling is on.
+struct ProfScope {
+  mgrit_handle* h;
+  int cat;
+  cudaEvent_t a = nullptr;
+  ProfScope(mgrit_handle* hh, int c, double flops) : h(hh), cat(c) {
+    if (!h->prof.on) return;
+    a = prof_event(h);
+    cudaEventRecord(a, h->st);
+    h->prof.flops[cat] += flops;
+    h->prof.count[cat] += 1;
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(h);
+    cudaEventRecord(b, h->st);
+    h->prof.ev[cat].push_back({a, b});
+  }
+};
+
+#define CUDA_TRY(expr)                           \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return MGRIT_ERR_CUDA; \
+  } while (0)
+
+static int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MGRIT_OK : MGRIT_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// setup helpers
+// ---------------------------------------------------------------------------
+
+// Chunk geometry of the in-block solves: nthr (a power of two <= 256) chunks
+// of P points, P as close to 32 as possible, 8 <= P <= 64.
+static bool pick_chunks(int64_t n, int* P, int* nthr) {
+  int best = -1, bestP = 0;
+  for (int t = 256; t >= 1; t >>= 1) {
+    if (n % t) continue;
+    int64_t p = n / t;
+    if (p < 8 || p > 64) continue;
+    int score = (int)std::abs(p - 32);
+    if (best < 0 || score < best || (score == best && p > bestP)) {
+      best = score;
+      bestP = (int)p;
+      *P = (int)p;
+      *nthr = t;
+    }
+  }
+  return best >= 0;
+}
+
+template <typename T>
+static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int Hpad, int P, int nthr) {
+  std::memset((void*)d, 0, sizeof(*d));
+  double c3[3] = {0, 0, 0};
+  for (int q = 0; q < horder; ++q) c3[q] = coef[q];
+  ScanTables tb = scan_tables(c3, Hpad, P, nthr);
+  d->h = Hpad;
+  d->rounds = tb.rounds;
+  int full = 0;
+  while ((1 << full) < nthr) ++full;
+  d->closure = (tb.rounds == full) ? 1 : 0;
+  for (int q = 0; q < 3; ++q) d->ncoef[q] = (T)(-c3[q]);
+  for (int r = 0; r < tb.rounds && r < kMaxRounds; ++r)
+    for (int i = 0; i < 9; ++i) d->Mpow[r][i] = (T)tb.Mpow[r * 9 + i];
+  for (int i = 0; i < 9; ++i) d->Cl[i] = (T)tb.Cl[i];
+  for (int j = 0; j < P && j < kPMax; ++j)
+    for (int q = 0; q < 3; ++q) d->G[j * 3 + q] = (T)tb.G[(size_t)j * 3 + q];
+}
+
+static Stencil fold_mod(const Stencil& s, int64_t nx) {
+  if (s.width() <= nx) return s;
+  Stencil f;
+  f.lo = s.lo;
+  f.hi = s.lo + (int)nx - 1;
+  f.a.assign((size_t)nx, 0.0);
+  for (int t = s.lo; t <= s.hi; ++t) {
+    int64_t off = ((int64_t)(t - s.lo)) % nx;
+    f.a[(size_t)off] += s.a[t - s.lo];
+  }
+  return f;
+}
+
+static int set_stencil(StencilParams<double>* sp, const Stencil& s0, int64_t nx) {
+  Stencil s = fold_mod(s0, nx);
+  if (s.width() > kMaxTaps) return MGRIT_ERR_UNSUPPORTED;
+  std::memset((void*)sp, 0, sizeof(*sp));
+  sp->nx = nx;
+  sp->lo = s.lo;
+  sp->ntaps = s.width();
+  for (int i = 0; i < s.width(); ++i) sp->taps[i] = s.a[i];
+  return MGRIT_OK;
+}
+
+// phi recursion (Lemma 6.1 / Eq. 6.4) and the generalised two-term form
+// for q != p.  Returns per-level (phi_p, phi_q), level index 1..L-1.
+static void phi_recursion(const mgrit_params& P, int L, std::vector<double>* php,
+                          std::vector<double>* phq, std::vector<long long>* ks,
+                          std::vector<double>* es) {
+  int p = P.order_p, q = P.rk_order_q;
+  double c = P.cfl;
+  double efd = e_fd(p), erk = e_rk(P.rk_kind == MGRIT_SDIRK ? 1 : 0, q);
+  double sgn = ((p + 1) % 2) ? -1.0 : 1.0;
+  php->assign(L, 0.0);
+  phq->assign(L, 0.0);
+  ks->assign(L, 0);
+  es->assign(L, 0.0);
+  double mpow = 1.0;
+  for (int l = 1; l < L; ++l) {
+    mpow *= P.m;
+    long long k;
+    double eps;
+    sl_shift(c * mpow, &k, &eps);
+    (*ks)[l] = k;
+    (*es)[l] = eps;
+    double f = f_poly(p, eps);
+    double cq = std::pow(-c, q + 1) * erk;
+    if (l == 1) {
+      (*php)[l] = P.m * c * efd + sgn * f;
+      (*phq)[l] = P.m * cq;
+    } else {
+      double fprev = f_poly(p, (*es)[l - 1]);
+      (*php)[l] = sgn * (-P.m * fprev + f) + P.m * (*php)[l - 1];
+      (*phq)[l] = P.m * (*phq)[l - 1];
+    }
+  }
+  if (q == p) {  // single correction constant phi = phi_p + phi_q (Eq. varphi-constant-MOL-SL)
+    for (int l = 1; l < L; ++l) {
+      (*php)[l] += (*phq)[l];
+      (*phq)[l] = 0.0;
+    }
+  }
+}
+
+static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long long k, double eps,
+                        std::string* why) {
+  const mgrit_params& P = h->prm;
+  LevelData& Lv = h->lev[l];
+  int p = P.order_p, q = P.rk_order_q;
+  Stencil A = stencil_identity();
+  A = stencil_add(A, central_diff(p + 1), -phi_p);
+  if (q != p && phi_q != 0.0) A = stencil_add(A, central_diff(q + 1), -phi_q);
+  BandFactor bf;
+  if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
+  const int H = (p + 1) / 2;
+  if (bf.hc > H || bf.ha > H) {
+    if (why) *why = "correction band wider than the SL stencil order supports";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  int Pc, nthr;
+  if (!pick_chunks(h->nx, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
+  CoarseParams<double>& cp = Lv.cp;
+  std::memset((void*)&cp, 0, sizeof(cp));
+  cp.n = (int)h->nx;
+  cp.P = Pc;
+  cp.nthr = nthr;
+  cp.p1 = p + 1;
+  cp.jlo = -(p + 1) / 2;
+  cp.kshift = (int)(((k % h->nx) + h->nx) % h->nx);
+  cp.shift = (int)(((bf.shift % h->nx) + h->nx) % h->nx);
+  std::vector<double> w = sl_weights(p, eps);
+  for (int a = 0; a <= p; ++a) cp.w[a] = w[a] * bf.inv_kappa;
+  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, Pc, nthr);
+  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, Pc, nthr);
+  cp.m = h->m;
+  Lv.kshift = k;
+  Lv.eps = eps;
+  Lv.phi = phi_p;
+  Lv.phi_q = phi_q;
+  if (coarse_smem_bytes(cp.n, cp.P, cp.nthr, 8) > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
+  return MGRIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels on levels
+// ---------------------------------------------------------------------------
+
+// level 0: out rows 1..K = Phi^m in rows 0..K-1 (+ optional residual form)
+static int l0_cf(mgrit_handle* h) {
+  LevelData& L0 = h->lev[0];
+  StencilParams<double>& sp = *h->fineM;
+  sp.in = L0.uC[L0.cur];
+  sp.out = L0.uC[1 - L0.cur] + h->nx;
+  sp.rhs = nullptr;
+  sp.sub = nullptr;
+  sp.partial = nullptr;
+  sp.rows = L0.K;
+  {
+    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    launch_stencil_rows(sp, h->st);
+  }
+  ++h->launches;
+  L0.cur = 1 - L0.cur;
+  return check_launch();
+}
+
+static int l0_fres(mgrit_handle* h) {
+  LevelData& L0 = h->lev[0];
+  StencilParams<double>& sp = *h->fineM;
+  sp.in = L0.uC[L0.cur];
+  sp.sub = L0.uC[L0.cur] + h->nx;
+  sp.out = h->lev[1].g + h->nx;
+  sp.rhs = nullptr;
+  sp.partial = h->partials;
+  sp.rows = L0.K;
+  int64_t nb;
+  {
+    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    nb = launch_stencil_rows(sp, h->st);
+  }
+  ++h->launches;
+  {
+    ProfScope ps(h, 2, 0.0);
+    launch_reduce_sum(h->partials, nb, h->dnorm, h->st);
+  }
+  ++h->launches;
+  return check_launch();
+}
+
+static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const double* start,
+                         double* out, const double* sub, double* parent, int nsteps, int64_t K,
+                         const double* g) {
+  CoarseParams<double> cp = h->lev[l].cp;
+  cp.mode = mode;
+  cp.zero_start = zero_start;
+  cp.start = start;
+  cp.out = out;
+  cp.sub = sub;
+  cp.parent = parent;
+  cp.nsteps = nsteps;
+  cp.K = K;
+  cp.g = g;
+  cp.partial = (mode == kModeFRES) ? h->partials : nullptr;
+  const int H = cp.p1 / 2;
+  double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
+  ProfScope ps(h, 1, 2.0 * (double)h->nx * steps * (double)(cp.p1 + 2 * H));
+  if (launch_coarse(cp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  ++h->launches;
+  return check_launch();
+}
+
+static int coarse_correct(mgrit_handle* h, int l);
+
+static int level_pre_and_residual(mgrit_handle* h, int l, bool zero_guess) {
+  LevelData& Lv = h->lev[l];
+  const int nu = h->prm.nu;
+  int rc;
+  if (nu == 0) {
+    if (zero_guess) {
+      CUDA_TRY(cudaMemsetAsync(Lv.uC[Lv.cur], 0, sizeof(double) * (Lv.K + 1) * h->nx, h->st));
+      rc = coarse_launch(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].g, nullptr, nullptr, h->m, Lv.K, Lv.g);
+    } else {
+      rc = coarse_launch(h, l, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[l + 1].g, Lv.uC[Lv.cur],
+                         nullptr, h->m, Lv.K, Lv.g);
+    }
+    return rc;
+  }
+  for (int s = 0; s < nu; ++s) {
+    bool zs = zero_guess && s == 0;
+    rc = coarse_launch(h, l, kModeCF, zs ? 1 : 0, zs ? nullptr : Lv.uC[Lv.cur], Lv.uC[1 - Lv.cur],
+                       nullptr, nullptr, h->m, Lv.K, Lv.g);
+    if (rc) return rc;
+    Lv.cur = 1 - Lv.cur;
+  }
+  rc = coarse_launch(h, l, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[l + 1].g, Lv.uC[Lv.cur], nullptr,
+                     h->m, Lv.K, Lv.g);
+  return rc;
+}
+
+// Solve the level-l error equation (RHS lev[l].g, zero initial guess) with
+// one cycle and add the result to the C-point unknowns of level l-1.
+static int coarse_correct(mgrit_handle* h, int l) {
+  LevelData& Lv = h->lev[l];
+  LevelData& Par = h->lev[l - 1];
+  double* parent = Par.uC[Par.cur];
+  int rc;
+  if (l == h->L - 1) {
+    return coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, parent, (int)Lv.N, 1, Lv.g);
+  }
+  rc = level_pre_and_residual(h, l, true);
+  if (rc) return rc;
+  rc = coarse_correct(h, l + 1);
+  if (rc) return rc;
+  return coarse_launch(h, l, kModeFOUT, 0, Lv.uC[Lv.cur], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.g);
+}
+
+static int level0_relax_residual(mgrit_handle* h, double* norm) {
+  int rc;
+  for (int s = 0; s < h->prm.nu; ++s) {
+    rc = l0_cf(h);
+    if (rc) return rc;
+  }
+  rc = l0_fres(h);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  *norm = std::sqrt(std::max(0.0, *h->hnorm));
+  return MGRIT_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+  return MGRIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* mgrit_strerror(int code) {
+  switch (code) {
+    case MGRIT_OK:
+      return "ok";
+    case MGRIT_ERR_INVALID_ARG:
+      return "invalid argument";
+    case MGRIT_ERR_OOM:
+      return "out of device memory";
+    case MGRIT_ERR_NOT_CONVERGED:
+      return "not converged within max_iter";
+    case MGRIT_ERR_DIVERGED:
+      return "diverged (non-finite or growing residual)";
+    case MGRIT_ERR_TIMEOUT:
+      return "bounded device wait timed out";
+    case MGRIT_ERR_CUDA:
+      return "CUDA runtime error";
+    case MGRIT_ERR_UNSTABLE:
+      return "singular or unstable coarse correction";
+    case MGRIT_ERR_UNSUPPORTED:
+      return "unsupported parameter combination";
+    default:
+      return "unknown error";
+  }
+}
+
+int mgrit_destroy(mgrit_handle* h) {
+  if (!h) return MGRIT_OK;
+  for (auto& Lv : h->lev) {
+    cudaFree(Lv.uC[0]);
+    cudaFree(Lv.uC[1]);
+    cudaFree(Lv.g);
+  }
+  for (int c = 0; c < 4; ++c)
+    for (auto& pr : h->prof.ev[c]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : h->prof.pool) cudaEventDestroy(e);
+  cudaFree(h->partials);
+  cudaFree(h->dnorm);
+  cudaFree(h->du0);
+  if (h->hnorm) cudaFreeHost(h->hnorm);
+  delete h;
+  return MGRIT_OK;
+}
+
+int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
+  if (!params || !out) return MGRIT_ERR_INVALID_ARG;
+  *out = nullptr;
+  mgrit_params P = *params;
+  if (P.rk_order_q == 0) P.rk_order_q = P.order_p;
+  if (P.tol <= 0.0) P.tol = 1e-10;
+  if (P.max_iter <= 0) P.max_iter = 30;
+  if (P.alpha <= 0.0) P.alpha = 1.0;
+  if (P.nx < 32 || P.nx % 8 || P.nt < 2 || P.m < 2 || P.cfl <= 0.0 || P.nu < 0 || P.nu > 4)
+    return MGRIT_ERR_INVALID_ARG;
+  if (P.order_p != 1 && P.order_p != 3 && P.order_p != 5) return MGRIT_ERR_INVALID_ARG;
+  if (P.rk_kind != MGRIT_ERK && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_INVALID_ARG;
+  if (P.rk_kind == MGRIT_ERK && P.rk_order_q != P.order_p) return MGRIT_ERR_INVALID_ARG;
+  if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
+  if (P.precision != MGRIT_FP64 && P.precision != MGRIT_MIXED) return MGRIT_ERR_INVALID_ARG;
+  if (P.rk_kind == MGRIT_SDIRK || P.precision == MGRIT_MIXED) return MGRIT_ERR_UNSUPPORTED;
+  if (P.nt % P.m) return MGRIT_ERR_INVALID_ARG;
+  int L = P.levels;
+  if (L == 0) {  // coarsen until fewer than two time points would result
+    L = 1;
+    int64_t N = P.nt;
+    while (N % P.m == 0 && N / P.m >= 2) {
+      N /= P.m;
+      ++L;
+    }
+    if (L < 2) L = 2;
+  }
+  if (L < 2 || L > MGRIT_MAX_LEVELS) return MGRIT_ERR_INVALID_ARG;
+  {
+    int64_t N = P.nt;
+    for (int l = 1; l < L; ++l) {
+      if (N % P.m) return MGRIT_ERR_INVALID_ARG;
+      N /= P.m;
+    }
+    if (N < 1) return MGRIT_ERR_INVALID_ARG;
+  }
+  int P0, T0;
+  if (!pick_chunks(P.nx, &P0, &T0)) return MGRIT_ERR_INVALID_ARG;
+  // stencil wider than the grid is rejected (wrap-around of one step)
+  if ((int64_t)(P.order_p + 1) * P.rk_order_q + 1 > P.nx) return MGRIT_ERR_INVALID_ARG;
+
+  struct Del {
+    void operator()(mgrit_handle* x) const { mgrit_destroy(x); }
+  };
+  auto h = std::unique_ptr<mgrit_handle, Del>(new mgrit_handle());
+  h->prm = P;
+  h->prm.levels = L;
+  h->st = (cudaStream_t)stream;
+  h->L = L;
+  h->nx = P.nx;
+  h->m = P.m;
+  cudaGetDevice(&h->device);
+  h->lev.resize(L);
+  int64_t N = P.nt;
+  for (int l = 0; l < L; ++l) {
+    h->lev[l].N = N;
+    h->lev[l].K = (l < L - 1) ? N / P.m : 0;
+    N /= P.m;
+  }
+  // level-0 operators
+  Stencil step = erk_step_stencil(P.order_p, P.rk_order_q, P.cfl);
+  h->fine1.reset(new StencilParams<double>());
+  h->fineM.reset(new StencilParams<double>());
+  int rc = set_stencil(h->fine1.get(), step, P.nx);
+  if (rc) return rc;
+  Stencil stepM = stencil_power(step, P.m);
+  h->fineM_taps_raw = stepM.width();
+  rc = set_stencil(h->fineM.get(), stepM, P.nx);
+  if (rc) return rc;
+  // coarse operators
+  std::vector<double> php, phq, es;
+  std::vector<long long> ks;
+  phi_recursion(P, L, &php, &phq, &ks, &es);
+  std::string why;
+  for (int l = 1; l < L; ++l) {
+    rc = build_coarse(h.get(), l, php[l], phq[l], ks[l], es[l], &why);
+    if (rc) return rc;
+  }
+  // buffers
+  const size_t row = sizeof(double) * (size_t)P.nx;
+  auto alloc = [&](double** p, size_t bytes) -> int {
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return MGRIT_ERR_OOM;
+    }
+    return MGRIT_OK;
+  };
+  for (int l = 0; l < L; ++l) {
+    LevelData& Lv = h->lev[l];
+    if (l < L - 1) {
+      for (int b = 0; b < 2; ++b) {
+        if ((rc = alloc(&Lv.uC[b], row * (Lv.K + 1)))) return rc;
+        CUDA_TRY(cudaMemsetAsync(Lv.uC[b], 0, row * (Lv.K + 1), h->st));
+      }
+    }
+    if (l >= 1) {
+      if ((rc = alloc(&Lv.g, row * (Lv.N + 1)))) return rc;
+      CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
+    }
+  }
+  h->npart = std::max<int64_t>(h->lev[0].K * stencil_tiles(P.nx), h->lev[0].K) + 1;
+  if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
+  if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
+  if ((rc = alloc(&h->du0, row))) return rc;
+  CUDA_TRY(cudaMemsetAsync(h->du0, 0, row, h->st));
+  if (cudaMallocHost((void**)&h->hnorm, sizeof(double)) != cudaSuccess) return MGRIT_ERR_OOM;
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  *out = h.release();
+  return MGRIT_OK;
+}
+
+int mgrit_set_initial(mgrit_handle* h, const double* u0, const double* init) {
+  if (!h || !u0) return MGRIT_ERR_INVALID_ARG;
+  LevelData& L0 = h->lev[0];
+  const size_t row = sizeof(double) * (size_t)h->nx;
+  int rc = copy_any(h->du0, u0, row, h->st);
+  if (rc) return rc;
+  if (init) {
+    rc = copy_any(L0.uC[0], init, row * (L0.K + 1), h->st);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(L0.uC[0], h->du0, row, cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, h->st);
+    ++h->launches;
+    if ((rc = check_launch())) return rc;
+  }
+  CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, h->st));
+  L0.cur = 0;
+  h->have_initial = true;
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return MGRIT_OK;
+}
+
+int mgrit_relax(mgrit_handle* h, int level, int nu) {
+  if (!h || level < 0 || level >= h->L - 1 || nu < 0) return MGRIT_ERR_INVALID_ARG;
+  int rc;
+  for (int s = 0; s < nu; ++s) {
+    if (level == 0) {
+      rc = l0_cf(h);
+    } else {
+      LevelData& Lv = h->lev[level];
+      rc = coarse_launch(h, level, kModeCF, 0, Lv.uC[Lv.cur], Lv.uC[1 - Lv.cur], nullptr, nullptr, h->m,
+                         Lv.K, Lv.g);
+      Lv.cur = 1 - Lv.cur;
+    }
+    if (rc) return rc;
+  }
+  return MGRIT_OK;
+}
+
+int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
+  if (!h || level < 0 || level >= h->L - 1) return MGRIT_ERR_INVALID_ARG;
+  int rc;
+  if (level == 0) {
+    rc = l0_fres(h);
+  } else {
+    LevelData& Lv = h->lev[level];
+    rc = coarse_launch(h, level, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[level + 1].g, Lv.uC[Lv.cur],
+                       nullptr, h->m, Lv.K, Lv.g);
+    if (!rc) {
+      launch_reduce_sum(h->partials, Lv.K, h->dnorm, h->st);
+      ++h->launches;
+      rc = check_launch();
+    }
+  }
+  if (rc) return rc;
+  if (norm_out) {
+    CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    *norm_out = std::sqrt(std::max(0.0, *h->hnorm));
+  }
+  return MGRIT_OK;
+}
+
+int mgrit_coarse_apply(mgrit_handle* h, int level, const double* d_in, double* d_out, int64_t nvec) {
+  if (!h || level < 0 || level >= h->L || !d_in || !d_out || nvec < 0) return MGRIT_ERR_INVALID_ARG;
+  if (nvec == 0) return MGRIT_OK;
+  if (level == 0) {
+    StencilParams<double>& sp = *h->fine1;
+    sp.in = d_in;
+    sp.out = d_out;
+    sp.rhs = nullptr;
+    sp.sub = nullptr;
+    sp.partial = nullptr;
+    sp.rows = nvec;
+    launch_stencil_rows(sp, h->st);
+    ++h->launches;
+    return check_launch();
+  }
+  return coarse_launch(h, level, kModeAPPLY, 0, d_in, d_out, nullptr, nullptr, 1, nvec, nullptr);
+}
+
+int mgrit_vcycle(mgrit_handle* h, double* norm_out) {
+  if (!h) return MGRIT_ERR_INVALID_ARG;
+  int rc = coarse_correct(h, 1);
+  if (rc) return rc;
+  double nrm = 0.0;
+  rc = level0_relax_residual(h, &nrm);
+  if (rc) return rc;
+  if (norm_out) *norm_out = nrm;
+  return MGRIT_OK;
+}
+
+int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* stats) {
+  if (!h) return MGRIT_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  int rc;
+  if (u0) {
+    rc = mgrit_set_initial(h, u0, nullptr);
+    if (rc) return rc;
+  } else if (!h->have_initial) {
+    return MGRIT_ERR_INVALID_ARG;
+  }
+  mgrit_stats st;
+  std::memset(&st, 0, sizeof(st));
+  st.levels = h->L;
+  double nrm = 0.0;
+  int it = 0;
+  int status = MGRIT_OK;
+  while (true) {
+    rc = level0_relax_residual(h, &nrm);
+    if (rc) return rc;
+    if (st.history_len < MGRIT_MAX_HISTORY) st.rnorm_history[st.history_len++] = nrm;
+    if (it == 0) st.rnorm0 = nrm;
+    st.rnorm = nrm;
+    if (!std::isfinite(nrm) || (it > 0 && nrm > 1e3 * st.rnorm0)) {
+      status = MGRIT_ERR_DIVERGED;
+      break;
+    }
+    if (nrm <= h->prm.tol * st.rnorm0) {
+      st.converged = 1;
+      break;
+    }
+    if (it >= h->prm.max_iter) {
+      status = MGRIT_ERR_NOT_CONVERGED;
+      break;
+    }
+    rc = coarse_correct(h, 1);
+    if (rc) return rc;
+    ++it;
+  }
+  st.iterations = it;
+  if (st.history_len >= 2 && st.rnorm_history[st.history_len - 2] > 0)
+    st.conv_factor = st.rnorm_history[st.history_len - 1] / st.rnorm_history[st.history_len - 2];
+  if (u_out) {
+    LevelData& L0 = h->lev[0];
+    rc = copy_any(u_out, L0.uC[L0.cur], sizeof(double) * (size_t)h->nx * (L0.K + 1), h->st);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return status;
+}
+
+int mgrit_level_io(mgrit_handle* h, int level, int field, double* ptr, int to_device, int64_t* rows_out) {
+  if (!h || level < 0 || level >= h->L || !ptr) return MGRIT_ERR_INVALID_ARG;
+  LevelData& Lv = h->lev[level];
+  double* buf = nullptr;
+  int64_t rows = 0;
+  if (field == 0) {
+    if (level == h->L - 1) return MGRIT_ERR_INVALID_ARG;
+    buf = Lv.uC[Lv.cur];
+    rows = Lv.K + 1;
+  } else if (field == 1) {
+    if (level == 0) return MGRIT_ERR_INVALID_ARG;
+    buf = Lv.g;
+    rows = Lv.N + 1;
+  } else {
+    return MGRIT_ERR_INVALID_ARG;
+  }
+  size_t bytes = sizeof(double) * (size_t)h->nx * rows;
+  int rc = to_device ? copy_any(buf, ptr, bytes, h->st) : copy_any(ptr, buf, bytes, h->st);
+  if (rc) return rc;
+  if (to_device && field == 0) {
+    // keep both buffers' row 0 consistent (the t = 0 row never changes)
+    size_t row = sizeof(double) * (size_t)h->nx;
+    CUDA_TRY(cudaMemcpyAsync(Lv.uC[1 - Lv.cur], buf, row, cudaMemcpyDeviceToDevice, h->st));
+    if (level == 0) CUDA_TRY(cudaMemcpyAsync(h->du0, buf, row, cudaMemcpyDeviceToDevice, h->st));
+    if (level == 0) h->have_initial = true;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (rows_out) *rows_out = rows;
+  return MGRIT_OK;
+}
+
+int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps, int64_t every,
+                         double* traj) {
+  if (!h || !u0 || !u_out || nsteps < 0 || every < 0) return MGRIT_ERR_INVALID_ARG;
+  if (h->prm.rk_kind != MGRIT_ERK) return MGRIT_ERR_UNSUPPORTED;
+  const int64_t nx = h->nx;
+  Stencil step = erk_step_stencil(h->prm.order_p, h->prm.rk_order_q, h->prm.cfl);
+  // cluster size: power of two <= 16 dividing nx with >= 256 points per CTA
+  int C = 1;
+  while (C < 16 && nx % (2 * C) == 0 && nx / (2 * C) >= 256) C *= 2;
+  int64_t npc = nx / C;
+  // passes of Phi^B: B <= 64, halo within one neighbour, taps <= kSeqMaxTaps,
+  // and B | every when a trajectory is requested
+  int B = 1;
+  for (int b = 64; b >= 1; --b) {
+    if (every > 0 && every % b) continue;
+    if (nsteps > 0 && b > nsteps) continue;
+    int64_t hl = (int64_t)b * (-step.lo), hr = (int64_t)b * step.hi;
+    if (hl > npc || hr > npc || b * (step.width() - 1) + 1 > kSeqMaxTaps) continue;
+    B = b;
+    break;
+  }
+  std::unique_ptr<SeqParams> sp(new SeqParams());
+  std::memset((void*)sp.get(), 0, sizeof(SeqParams));
+  Stencil SB = stencil_power(step, B);
+  sp->nx = nx;
+  sp->npc = (int)npc;
+  sp->halo_l = -SB.lo;
+  sp->halo_r = SB.hi;
+  sp->lo = SB.lo;
+  sp->ntaps = SB.width();
+  for (int i = 0; i < SB.width(); ++i) sp->taps[i] = SB.a[i];
+  sp->passes = nsteps / B;
+  sp->tail_passes = (int)(nsteps % B);
+  sp->tail_lo = step.lo;
+  sp->tail_ntaps = step.width();
+  if (step.width() > 64) return MGRIT_ERR_UNSUPPORTED;
+  for (int i = 0; i < step.width(); ++i) sp->tail_taps[i] = step.a[i];
+  sp->every_passes = (every > 0 && traj) ? (int)(every / B) : 0;
+  sp->traj = (every > 0) ? traj : nullptr;
+  size_t smem = 2 * sizeof(double) * (size_t)(sp->halo_l + npc + sp->halo_r);
+  if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
+  int Cmax = seq_max_cluster(C, smem);
+  while (C > Cmax) {
+    C /= 2;
+    npc = nx / C;
+    sp->npc = (int)npc;
+    smem = 2 * sizeof(double) * (size_t)(sp->halo_l + npc + sp->halo_r);
+    if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
+  }
+  sp->csize = C;
+  const size_t row = sizeof(double) * (size_t)nx;
+  double* din = h->du0;
+  int rc = copy_any(din, u0, row, h->st);
+  if (rc) return rc;
+  bool out_dev = is_device_ptr(u_out);
+  double* dout = out_dev ? u_out : h->lev[0].uC[1 - h->lev[0].cur];  // scratch row when host
+  sp->u0 = din;
+  sp->u_out = dout;
+  {
+    ProfScope ps(h, 3, 2.0 * (double)nx * ((double)sp->passes * sp->ntaps + (double)sp->tail_passes * sp->tail_ntaps));
+    if (launch_seq(*sp, h->st) != 0) return MGRIT_ERR_CUDA;
+  }
+  ++h->launches;
+  if ((rc = check_launch())) return rc;
+  if (!out_dev) {
+    rc = copy_any(u_out, dout, row, h->st);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  return MGRIT_OK;
+}
+
+int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
+  if (!h || level < 0 || level >= h->L || !out) return MGRIT_ERR_INVALID_ARG;
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  const LevelData& Lv = h->lev[level];
+  out[0] = (double)Lv.N;
+  if (level == 0) {
+    out[5] = (double)h->fineM->ntaps;
+    return MGRIT_OK;
+  }
+  out[1] = (double)Lv.kshift;
+  out[2] = Lv.eps;
+  out[3] = Lv.phi;
+  out[4] = Lv.phi_q;
+  out[6] = (double)Lv.cp.P;
+  return MGRIT_OK;
+}
+
+int64_t mgrit_launch_count(const mgrit_handle* h) { return h ? h->launches : 0; }
+
+int mgrit_profile(mgrit_handle* h, int enable) {
+  if (!h) return MGRIT_ERR_INVALID_ARG;
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  for (int c = 0; c < 4; ++c) {
+    for (auto& pr : h->prof.ev[c]) {
+      h->prof.pool.push_back(pr.first);
+      h->prof.pool.push_back(pr.second);
+    }
+    h->prof.ev[c].clear();
+    h->prof.flops[c] = 0.0;
+    h->prof.count[c] = 0;
+  }
+  h->prof.on = enable != 0;
+  return MGRIT_OK;
+}
+
+int mgrit_profile_read(mgrit_handle* h, double out[12]) {
+  if (!h || !out) return MGRIT_ERR_INVALID_ARG;
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  for (int c = 0; c < 4; ++c) {
+    double ms = 0.0;
+    for (auto& pr : h->prof.ev[c]) {
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, pr.first, pr.second));
+      ms += t;
+    }
+    out[c * 3 + 0] = (double)h->prof.count[c];
+    out[c * 3 + 1] = ms;
+    out[c * 3 + 2] = h->prof.flops[c];
+  }
+  return MGRIT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Launch interface of the MGRIT device kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+constexpr int kMaxTaps = 1024;   // composite level-0 stencil taps (folded mod nx)
+constexpr int kMaxRounds = 11;   // chunk-scan rounds (up to 2048 chunks)
+constexpr int kPMax = 64;        // chunk length of the in-block banded solves
+
+// ---------------------------------------------------------------------------
+// Level-0 composite stencil: out[r] = sum_t a_t in[r][i+t] (+ rhs[r]) (- sub[r])
+// for rows r = 0..rows-1 (pointers are pre-offset by the caller).  With
+// `partial`, each CTA also writes sum(out^2) of its tile (FP64).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StencilParams {
+  const T* in;
+  T* out;
+  const T* rhs;
+  const T* sub;
+  double* partial;
+  int64_t nx;
+  int64_t rows;
+  int lo;
+  int ntaps;
+  T taps[kMaxTaps];
+};
+
+int stencil_tiles(int64_t nx);
+// Launch; returns the number of CTAs (= partial slots written).
+int64_t launch_stencil_rows(const StencilParams<double>& p, cudaStream_t st);
+int64_t launch_stencil_rows(const StencilParams<float>& p, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// In-block periodic banded solve tables (one direction).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct SolveDir {
+  int h;
+  int rounds;
+  int closure;         // 1: apply Cl to the carry (full circular scan)
+  T ncoef[3];          // negated recurrence coefficients
+  T Mpow[kMaxRounds][9];
+  T Cl[9];
+  T G[kPMax * 3];      // impulse responses G[j*3+q]
+};
+
+// Coarse-level step Phi_l v + g: SL gather (weights pre-scaled by 1/kappa),
+// then the factored periodic solve (causal then anticausal recurrences).
+enum CoarseMode { kModeCF = 0, kModeFRES = 1, kModeFOUT = 2, kModeSEQ = 3, kModeAPPLY = 4 };
+
+template <typename T>
+struct CoarseParams {
+  int n, P, nthr;
+  int p1;              // p + 1 SL weights
+  int jlo;             // node offset of weight 0: -(p+1)/2
+  int kshift;          // SL shift k_l mod n
+  int shift;           // y_i = v_{i+shift}
+  T w[8];
+  SolveDir<T> c, a;
+  int mode;
+  int zero_start;
+  int nsteps;
+  int m;
+  int64_t K;
+  const T* start;
+  const T* g;
+  T* out;
+  const T* sub;
+  T* parent;
+  double* partial;
+};
+
+size_t coarse_smem_bytes(int n, int P, int nthr, int elem);
+int launch_coarse(const CoarseParams<double>& p, cudaStream_t st);
+int launch_coarse(const CoarseParams<float>& p, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Utilities
+// ---------------------------------------------------------------------------
+// sum of partial[0..n) in a fixed order, written to out[0] (FP64)
+void launch_reduce_sum(const double* partial, int64_t n, double* out, cudaStream_t st);
+// C-point iterate: row 0 = u0, rows k >= 1 uniform [0,1) at time index k*m
+void launch_random_cpoints(double* uC, const double* u0, int64_t rows, int64_t nx, int m,
+                           uint64_t seed, cudaStream_t st);
+
+}  // namespace mg
+
+namespace mg {
+// ---------------------------------------------------------------------------
+// GPU sequential time-stepping u_{n+1} = Phi u_n: one thread-block cluster
+// per vector, the vector split over the cluster's CTAs in shared memory,
+// halos exchanged through distributed shared memory once per pass of the
+// composite stencil Phi^B.
+// ---------------------------------------------------------------------------
+constexpr int kSeqMaxTaps = 1024;
+struct SeqParams {
+  const double* u0;   // nx
+  double* u_out;      // nx
+  double* traj;       // optional rows written after every `every_passes` passes
+  int64_t nx;
+  int csize;          // CTAs per cluster
+  int npc;            // points per CTA
+  int halo_l, halo_r; // -lo, hi of the composite stencil
+  int64_t passes;     // passes of the main stencil
+  int every_passes;   // trajectory stride in passes (0: none)
+  int lo, ntaps;
+  double taps[kSeqMaxTaps];
+  // tail: `tail_steps` single steps with the one-step stencil afterwards
+  int tail_passes, tail_lo, tail_ntaps;
+  double tail_taps[64];
+};
+int launch_seq(const SeqParams& p, cudaStream_t st);
+int seq_max_cluster(int want, size_t smem);
+}  // namespace mg

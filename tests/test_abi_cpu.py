@@ -1,0 +1,70 @@
+"""The C-ABI library loads on a CPU-only machine, exports every entry point
+declared in include/mgrit.h, and rejects invalid parameters before touching a
+GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2209_06916_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mgrit_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(pkg.LIB_PATH):
+        pytest.skip("libmgrit.so not built (run __graft_entry__.build())")
+    return pkg.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("mgrit_setup", "mgrit_relax", "mgrit_residual", "mgrit_coarse_apply",
+                     "mgrit_solve", "mgrit_destroy", "mgrit_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_texts(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.mgrit_strerror(code)
+    assert lib.mgrit_strerror(-7) == b"singular or unstable coarse correction"
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=30, nt=128, cfl=0.85, p=1),            # nx too small / not a multiple of 8
+    dict(nx=64, nt=128, cfl=0.85, p=2),            # even p
+    dict(nx=64, nt=130, cfl=0.85, p=1, m=4),       # nt % m
+    dict(nx=64, nt=128, cfl=0.85, p=1, m=4, levels=5),  # nt % m^(L-1)
+    dict(nx=64, nt=128, cfl=-1.0, p=1),            # c <= 0
+    dict(nx=64, nt=128, cfl=0.85, p=3, q=1),       # ERK needs q = p
+    dict(nx=64, nt=128, cfl=0.85, p=1, nu=7),      # nu range
+    dict(nx=8 * 67, nt=128, cfl=0.85, p=1),        # no chunking with 8 <= P <= 64
+])
+def test_invalid_parameters_rejected_on_host(lib, kw):
+    prm = pkg.make_params(**kw)
+    h = ctypes.c_void_p()
+    assert lib.mgrit_setup(ctypes.byref(prm), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+def test_binding_refuses_wrong_dtypes():
+    import numpy as np
+    with pytest.raises(ValueError):
+        pkg._ptr(np.zeros(4, dtype=np.float32))
