@@ -254,3 +254,34 @@ def test_full_size_vcycle_against_sequential_stepping():
             err = max(err, float(np.max(np.abs(got[n // m] - u))))
     print("full-size: iterations=%d rel err vs sequential=%.3e" % (st["iterations"], err / scale))
     assert err / scale < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# GPU sequential time-stepping (the baseline MGRIT is measured against)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,c,nx,nsteps,every", [(1, 0.85, 256, 1000, 0), (3, 0.85, 4096, 1000, 0),
+                                                  (3, 1.2, 96, 77, 7), (5, 0.9, 512, 130, 13),
+                                                  (3, 0.85, 4096, 512, 64)])
+def test_sequential_stepping_matches_oracle(p, c, nx, nsteps, every):
+    s = solver(nx, 64, c, p, 4, 2)
+    u0 = ic_sin4_noise(nx, seed=5)
+    out = torch.empty(nx, dtype=torch.float64, device="cuda")
+    traj = None
+    if every:
+        traj = torch.zeros((nsteps // every, nx), dtype=torch.float64, device="cuda")
+    s.fine_propagate(dev(u0), out, nsteps, every, traj)
+    fine = oops.FineOperator(p, "erk", p, c)
+    u = u0.copy()
+    rows = []
+    for n in range(1, nsteps + 1):
+        u = fine.apply(u)
+        if every and n % every == 0:
+            rows.append(u.copy())
+    # FP64 rounding accumulates linearly in the number of steps
+    assert _rel(host(out), u) < 1e-13 * nsteps
+    if every:
+        assert _rel(host(traj), np.array(rows)) < 1e-13 * nsteps
+    host_out = np.zeros(nx)
+    s.fine_propagate(u0, host_out, nsteps)  # host pointers
+    assert _rel(host_out, u) < 1e-13 * nsteps
