@@ -220,6 +220,39 @@ int64_t mgrit_launch_count(const mgrit_handle* h);
 int mgrit_profile(mgrit_handle* h, int enable);
 int mgrit_profile_read(mgrit_handle* h, double out[12]);
 
+/*
+ * mgrit_residual_noalloc -- the level-0 C-point residual of mgrit_residual
+ * (level 0) and its l2 norm, for callers that cannot allocate device memory
+ * when they need it: code recording a CUDA graph by stream capture (device
+ * allocation is not a capturable operation) and applications whose device
+ * memory belongs to a pool or caching allocator that must not be bypassed.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * It takes no handle (mgrit_setup allocates) and allocates nothing, on the
+ * device or the host heap.  Its scratch (the per-CTA partial sums of the
+ * norm) lives in one static device array of 65536 + 32 doubles (512 KB) that
+ * every GPU loading the library holds until the process exits.
+ *   params  : host; fields nx, cfl, order_p, rk_order_q (0 or p), m are used;
+ *             rk_kind must be MGRIT_ERK and precision MGRIT_FP64.
+ *   d_uC    : device, rows * nx C-point values u_{k m}, k = 0..rows-1.
+ *   rows    : >= 2; (rows - 1) * ceil(nx / 1024) must not exceed 65536
+ *             (nx >= 1024; ceil(nx / 512) or ceil(nx / 256) below), else
+ *             MGRIT_ERR_INVALID_ARG and nothing runs.
+ *   d_r     : device, (rows - 1) * nx outputs r_k = Phi^m u_{(k-1)m} - u_{km},
+ *             k = 1..rows-1 (Sec. 2.2); must not overlap d_uC.
+ *   norm_out: host, receives ||r||_2; NULL skips the copy (the call is then
+ *             fully asynchronous).  With norm_out the stream is synchronised.
+ *   stream  : cudaStream_t as void*.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current) and may load the
+ * library's device code; make that first call before any stream capture.
+ * Every call shares the one array and overwrites its contents, so calls
+ * whose kernels overlap on the GPU (different streams, or different host
+ * threads) race on it: serialise them.
+ */
+int mgrit_residual_noalloc(const mgrit_params* params, const double* d_uC, int64_t rows, double* d_r,
+                           double* norm_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
