@@ -122,7 +122,7 @@ const char* mgrit_strerror(int code);
  * device) and the initial C-point iterate of level 0.  init (host or device,
  * (nt/m + 1) * nx values for time rows n = k m) may be NULL: then the rows
  * k >= 1 are uniform random in [0, 1) from SplitMix64 with params.seed and
- * counter n * nx + i + 1 (Sec. 5.2 setup: random except at t = 0).  Row 0 is
+ * counter n * nx + i + 1 (Sec. 5.3 setup: random except at t = 0).  Row 0 is
  * always u0.
  */
 int mgrit_set_initial(mgrit_handle* h, const double* u0, const double* init);

@@ -25,7 +25,7 @@ diff_taps(p)                 Eq. (Dp+1_def); s = 2 symmetric for    moments: (p+
                              odd p (Sec. 6.3), s = 1 one-point
                              left bias for even p (Sec. 6.4)
 phi_levels(...)              Lemma 6.1 Eq. (varphi-constant-MOL-SL) Lemma 6.1 O(h^{p+2}) order test
-                             and Eq. (6.4) multilevel recursion
+                             and the Sec. 6.2 multilevel recursion
 phi_levels_general(...)      builder reading for q != p: Lemma 4.2   parity unpinned against the paper
                              carries both D^{(p+1)} and D^{(q+1)}     (only an O(h) order test)
                              terms; App. B steps applied to each
@@ -388,7 +388,7 @@ def diff_taps(order, p_for_bias=None):
 
 
 # ----------------------------------------------------------------------------
-# Lemma 6.1 and Eq. (6.4): the truncation-error correction constants
+# Lemma 6.1 and Sec. 6.2: the truncation-error correction constants
 # ----------------------------------------------------------------------------
 
 
@@ -404,7 +404,7 @@ def phi_levels(p, kind, c, m, levels):
     l = 1:  m [c e_FD + (-c)^{p+1} e_RK] + (-1)^{p+1} f_{p+1}(eps_1)
             (Lemma 6.1, Eq. varphi-constant-MOL-SL)
     l > 1:  (-1)^{p+1} [ -m f_{p+1}(eps_{l-1}) + f_{p+1}(eps_l) ] + m phi_{l-1}
-            (Eq. 6.4).
+            (Sec. 6.2, the phi recursion below Eq. MOL-SL-corrected-multilevel).
     q = p is assumed, as in the paper.
     """
     q = p

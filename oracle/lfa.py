@@ -8,8 +8,8 @@ with lambda, mu the Fourier symbols of Phi and Psi, omega sampled at 2^11
 equispaced points of [-pi, pi); omega = 0 and the ``omit`` samples nearest to
 it on each side are dropped (footnote to Eq. rho-asym).
 
-Parity pins: P. 1360 (FCF factors of the third-order schemes bounded by 0.6)
-and P. 1435 (ERK4+U4, m = 2: about 0.15 just below c/c_max = 0.24 and about
+Parity pins: Sec. 6.3.4 (FCF factors of the third-order schemes bounded by 0.6)
+and Sec. 6.4 (ERK4+U4, m = 2: about 0.15 just below c/c_max = 0.24 and about
 0.84 just above).
 """
 import numpy as np

@@ -17,7 +17,7 @@ vcycle            Sec. 2.2 / Sec. 6.2: F(CF)^nu pre-relaxation, coarse  two-leve
                   correction (recursive, the coarsest level by           after nt/m iterations; ideal
                   sequential stepping), F post-relaxation                 Psi = Phi^m exact in one
                                                                           iteration; Table 3 counts
-solve             Sec. 5.2 / 6.3 setup: random initial iterate except    converged solution == sequential
+solve             Sec. 5.3 / 6.3 setup: random initial iterate except    converged solution == sequential
                   at t = 0, stop when the l2 norm of the residual has     stepping; final factor near LFA
                   dropped by ``tol`` (10 orders) or after max_iter
 """
@@ -66,7 +66,7 @@ def c_residual(op, u, g, m):
 
 class Hierarchy:
     """Level operators of a uniform-m hierarchy: level 0 is the fine MOL step
-    Phi, level l >= 1 the corrected SL operator Phi^{(m^l dt)} (Eq. 6.3).
+    Phi, level l >= 1 the corrected SL operator Phi^{(m^l dt)} (Eq. MOL-SL-corrected-multilevel).
     ``coarse`` may replace the level-1 operator (e.g. the ideal Phi^m) for a
     two-level hierarchy."""
 

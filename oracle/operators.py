@@ -17,8 +17,8 @@ FineOperator.apply       Eq. (MOL_M_def): one RK step of du/dt =         Fourier
                          on the practical form of a step)
 SLOperator.apply         Sec. 3: S_p^{(Delta)} interpolation at the       exact shift for integer offset;
                          departure point                                 Lemma 3.1 order
-CoarseOperator.apply     Eq. (MOL-SL-corrected) / (6.3):                  Lemma 6.1 O(h^{p+2}) match with
-                         (I - phi D)^{-1} S_p^{(m^l dt)}                  Phi^m; LFA values (P. 1360, 1435)
+CoarseOperator.apply     Eq. (MOL-SL-corrected[-multilevel])                Lemma 6.1 O(h^{p+2}) match with
+                         (I - phi D)^{-1} S_p^{(m^l dt)}                  Phi^m; LFA values (Sec. 6.3.4, 6.4)
 """
 import numpy as np
 import scipy.linalg
@@ -179,7 +179,7 @@ class SLOperator:
 class CoarseOperator:
     """Phi^{(m^l dt)} = (I - sum_t phi_t D^{(o_t)})^{-1} S_p^{(m^l dt)}.
 
-    With one term (phi, p+1) this is Eq. (MOL-SL-corrected) / (6.3); the
+    With one term (phi, p+1) this is Eq. (MOL-SL-corrected) / (MOL-SL-corrected-multilevel); the
     two-term form is the q != p reading (see coefficients.phi_levels_general).
     ``terms`` is a list of (phi, derivative order).
     """
@@ -204,7 +204,7 @@ class CoarseOperator:
 
 def coarse_operator(p, kind, q, c, m, level, levels):
     """Level-``level`` (>= 1) corrected SL operator of a ``levels``-level
-    hierarchy with uniform coarsening m (Eq. 6.3 and 6.4)."""
+    hierarchy with uniform coarsening m (Eq. MOL-SL-corrected-multilevel and the Sec. 6.2 phi recursion)."""
     s = c * m ** level
     if q == p:
         phi = co.phi_levels(p, kind, c, m, levels)[level - 1]

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 The numerical tests start MGRIT from a uniformly random iterate except at
-t = 0, where it equals the initial condition (Sec. 5.2, numerical setup).  The
+t = 0, where it equals the initial condition (Sec. 5.3, numerical setup).  The
 random value at time index n and grid index i is the SplitMix64 output
 function (Steele, Lea, Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014; the constants of Vigna's public-domain

@@ -179,7 +179,7 @@ static int set_stencil(StencilParams<double>* sp, const Stencil& s0, int64_t nx)
   return MGRIT_OK;
 }
 
-// phi recursion (Lemma 6.1 / Eq. 6.4) and the generalised two-term form
+// phi recursion (Lemma 6.1 / the multilevel recursion of Sec. 6.2) and the generalised two-term form
 // for q != p.  Returns per-level (phi_p, phi_q), level index 1..L-1.
 static void phi_recursion(const mgrit_params& P, int L, std::vector<double>* php,
                           std::vector<double>* phq, std::vector<long long>* ks,

@@ -202,7 +202,7 @@ def test_lemma_6_1_corrected_operator_order(p, kind, c, m):
 
 
 def test_multilevel_phi_recursion_order():
-    """Eq. (6.4): the level-2 operator matches (level-1 operator)^m to
+    """Sec. 6.2 phi recursion: the level-2 operator matches (level-1 operator)^m to
     O(h^{p+2}) for the recursive phi_2; using the two-level formula at step
     m^2 dt instead drops an order."""
     p, kind, c, m = 3, "erk", 0.85, 4

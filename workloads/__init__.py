@@ -6,7 +6,7 @@ mixes of the batched and served workloads.  Both the CUDA path's tests and
 the oracle draw their inputs from here.
 
   mesh(nx)                 x_i = -1 + i h, h = 2/nx, i = 0..nx-1 (Sec. 2.1)
-  ic_sin4(nx)              u_0(x) = sin^4(pi x) (Sec. 5.2 numerical setup)
+  ic_sin4(nx)              u_0(x) = sin^4(pi x) (Sec. 5.3 numerical setup)
   ic_sin4_noise(nx, seed)  sin^4(pi x) plus N(0, 1e-2) noise (variance 1e-2)
   ic_fourier(nx, seed)     sum_{k=1}^{20} (a_k cos(pi k x) + b_k sin(pi k x))/k^2,
                            a_k, b_k ~ N(0, 1): a smooth periodic random IC
