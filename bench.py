@@ -203,7 +203,25 @@ def main():
         t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    # GPU sequential time-stepping of the same problem (the baseline), and the
+    # accuracy of the MGRIT solution against it at the final time
+    seq_out = torch.empty(nx, dtype=torch.float64, device="cuda")
+    s.fine_propagate(u0, seq_out, nt)
+    s.profile(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.fine_propagate(u0, seq_out, nt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    sprof = s.profile_read()
+    s.profile(False)
+    s.solve(u0, out)
+    torch.cuda.synchronize()
+    err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
     clocks = clocks_sampler_stop(cp, cf, clk_path, local)
+    scnt, sms, sfl = sprof["sequential"]
 
     # accuracy of the benched solve against the FP64 ... (reported, not a gate)
     dof = nx * nt
@@ -228,6 +246,12 @@ def main():
             "e2e": {"value": ws * dof * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8},
             "gpu_launches": launches, "clocks": clocks,
+            "sequential": {"value": dof / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
+                           "kernel": "seq_kernel (thread-block cluster, DSMEM halos, composite Phi^B)",
+                           "achieved_tflops": sfl / (sms / 1e3) / 1e12 if sms > 0 else None,
+                           "frac": (sfl / (sms / 1e3)) / FP64_PEAK_FLOPS if sms > 0 else None},
+            "mgrit_over_sequential": (dof / (ms / 1e3 / args.steps)) / (dof / (seq_ms / 1e3)),
+            "max_rel_err_vs_sequential": err,
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -516,4 +516,58 @@ ScanTables scan_tables(const double* coef, int h, int P, int T) {
   return t;
 }
 
+static double mat3_norm(const double* a) {
+  double n = 0.0;
+  for (int i = 0; i < 9; ++i) n = std::max(n, std::fabs(a[i]));
+  return n;
+}
+
+DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) {
+  DistScanTables d;
+  d.h = h;
+  ScanTables base = scan_tables(coef, h, P, 1);  // G only
+  d.G = base.G;
+  const double I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < h; ++a)
+    for (int q = 0; q < h; ++q) M[a * 3 + q] = d.G[(size_t)(P - 1 - a) * 3 + q];
+  // intra-CTA rounds: 2^r < T and M^{2^r} not yet negligible
+  double pw[9];
+  for (int i = 0; i < 9; ++i) pw[i] = M[i];
+  for (int r = 0; (1 << r) < T; ++r) {
+    if (mat3_norm(pw) < 1e-18) break;
+    d.Mpow.insert(d.Mpow.end(), pw, pw + 9);
+    ++d.rounds;
+    mat3_mul(pw, pw, pw);
+  }
+  // per-chunk carry table M^t, t < T, until negligible
+  double mt[9];
+  for (int i = 0; i < 9; ++i) mt[i] = I3[i];
+  for (int t = 0; t < T; ++t) {
+    if (t > 0 && mat3_norm(mt) < 1e-18) break;
+    d.Mt.insert(d.Mt.end(), mt, mt + 9);
+    ++d.tcut;
+    mat3_mul(mt, M, mt);
+  }
+  // Mc = M^T (transfer across a whole CTA)
+  double Mc[9];
+  for (int i = 0; i < 9; ++i) Mc[i] = I3[i];
+  for (int t = 0; t < T; ++t) mat3_mul(Mc, M, Mc);
+  double mcj[9];
+  for (int i = 0; i < 9; ++i) mcj[i] = I3[i];
+  for (int j = 0; j < C; ++j) {
+    if (j > 0 && mat3_norm(mcj) < 1e-18) break;
+    d.McPow.insert(d.McPow.end(), mcj, mcj + 9);
+    ++d.jterms;
+    mat3_mul(mcj, Mc, mcj);
+  }
+  if (d.jterms == C && mat3_norm(mcj) >= 1e-18) {
+    // the sum wraps the ring: closure (I - Mc^C)^{-1}; mcj = Mc^C here
+    double IM[9];
+    for (int i = 0; i < 9; ++i) IM[i] = I3[i] - mcj[i];
+    if (mat3_inv(IM, h, d.Clc)) d.closure = 1;
+  }
+  return d;
+}
+
 }  // namespace mg

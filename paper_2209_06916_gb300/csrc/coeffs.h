@@ -74,4 +74,20 @@ struct ScanTables {
 };
 ScanTables scan_tables(const double* coef, int h, int P, int T);
 
+// Tables of the cluster-distributed chunk scan: T chunks of P points per CTA,
+// C CTAs per vector (see the SolveDir description in kernels.h).
+struct DistScanTables {
+  int h = 0;
+  int rounds = 0;            // intra-CTA (non-circular) Hillis-Steele rounds
+  std::vector<double> G;     // P * 3 impulse responses
+  std::vector<double> Mpow;  // rounds * 9: M^{2^r}
+  std::vector<double> Mt;    // tcut * 9: M^t, t = 0..tcut-1
+  int tcut = 0;
+  int jterms = 0;            // cluster-level terms
+  std::vector<double> McPow; // jterms * 9: (M^T)^j
+  double Clc[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  int closure = 0;
+};
+DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C);
+
 }  // namespace mg

@@ -36,6 +36,7 @@ struct LevelData {
   double* g = nullptr;
   // coarse operator (l >= 1)
   CoarseParams<double> cp;
+  double* Mt_dev[2] = {nullptr, nullptr};  // per-chunk carry tables (causal, anticausal)
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
 };
@@ -136,23 +137,58 @@ static bool pick_chunks(int64_t n, int* P, int* nthr) {
   return best >= 0;
 }
 
+// Geometry of a coarse level with K vectors (CF-intervals) of n points:
+// C CTAs per vector (a thread-block cluster, power of two <= 16), nthr
+// threads per CTA, P points per thread.  Grow C until the level has about
+// two CTAs per SM (keeping >= 256 points per CTA), then shrink P towards 8
+// while the level has fewer than ~4 warps per SM.
+static bool pick_coarse_geometry(int64_t n, int64_t K, int* C, int* P, int* nthr) {
+  int c = 1;
+  while (c < 16 && K * c < 2 * 152 && n % (2 * c) == 0 && n / (2 * c) >= 256) c *= 2;
+  int64_t npc = n / c;
+  int bestP = -1;
+  double bestScore = 0.0;
+  for (int p = 8; p <= 64; ++p) {
+    if (npc % p) continue;
+    int64_t t = npc / p;
+    if (t > 256) continue;
+    // prefer P = 32, but P = 16 / 8 when the level is short of warps
+    double warps_per_sm = (double)K * c * ((t + 31) / 32) / 152.0;
+    double target = warps_per_sm * 32.0 / p < 4.0 ? 8.0 : 32.0;
+    double score = std::fabs(std::log((double)p / target));
+    if (bestP < 0 || score < bestScore - 1e-12) {
+      bestP = p;
+      bestScore = score;
+    }
+  }
+  if (bestP < 0) return false;
+  *C = c;
+  *P = bestP;
+  *nthr = (int)(npc / bestP);
+  return true;
+}
+
 template <typename T>
-static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int Hpad, int P, int nthr) {
+static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int Hpad, int P, int nthr, int C,
+                           std::vector<T>* mt_out) {
   std::memset((void*)d, 0, sizeof(*d));
   double c3[3] = {0, 0, 0};
   for (int q = 0; q < horder; ++q) c3[q] = coef[q];
-  ScanTables tb = scan_tables(c3, Hpad, P, nthr);
+  DistScanTables tb = dist_scan_tables(c3, Hpad, P, nthr, C);
   d->h = Hpad;
-  d->rounds = tb.rounds;
-  int full = 0;
-  while ((1 << full) < nthr) ++full;
-  d->closure = (tb.rounds == full) ? 1 : 0;
+  d->rounds = std::min(tb.rounds, kMaxRounds);
+  d->tcut = tb.tcut;
+  d->jterms = std::min(tb.jterms, 16);
+  d->closure = tb.closure;
   for (int q = 0; q < 3; ++q) d->ncoef[q] = (T)(-c3[q]);
-  for (int r = 0; r < tb.rounds && r < kMaxRounds; ++r)
+  for (int r = 0; r < d->rounds; ++r)
     for (int i = 0; i < 9; ++i) d->Mpow[r][i] = (T)tb.Mpow[r * 9 + i];
-  for (int i = 0; i < 9; ++i) d->Cl[i] = (T)tb.Cl[i];
+  for (int j = 0; j < d->jterms; ++j)
+    for (int i = 0; i < 9; ++i) d->McPow[j][i] = (T)tb.McPow[j * 9 + i];
+  for (int i = 0; i < 9; ++i) d->Clc[i] = (T)tb.Clc[i];
   for (int j = 0; j < P && j < kPMax; ++j)
     for (int q = 0; q < 3; ++q) d->G[j * 3 + q] = (T)tb.G[(size_t)j * 3 + q];
+  mt_out->assign(tb.Mt.begin(), tb.Mt.end());
 }
 
 static Stencil fold_mod(const Stencil& s, int64_t nx) {
@@ -234,27 +270,55 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
     if (why) *why = "correction band wider than the SL stencil order supports";
     return MGRIT_ERR_UNSUPPORTED;
   }
-  int Pc, nthr;
-  if (!pick_chunks(h->nx, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
+  if (bf.shift != 0) {
+    if (why) *why = "correction factorisation needs an index shift";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  int Cc, Pc, nthr;
+  int64_t Kl = (l == h->L - 1) ? 1 : Lv.K;
+  if (!pick_coarse_geometry(h->nx, Kl, &Cc, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
+  size_t smem = coarse_smem_bytes((int)(h->nx / Cc), Pc, nthr, 8);
+  if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
+  while (Cc > 1 && coarse_max_cluster(Cc, smem, nthr) < Cc) {
+    // fall back to a smaller cluster with the same chunk length
+    Cc /= 2;
+    nthr *= 2;
+    if (nthr > 256) return MGRIT_ERR_UNSUPPORTED;
+    smem = coarse_smem_bytes((int)(h->nx / Cc), Pc, nthr, 8);
+    if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
+  }
   CoarseParams<double>& cp = Lv.cp;
   std::memset((void*)&cp, 0, sizeof(cp));
   cp.n = (int)h->nx;
   cp.P = Pc;
   cp.nthr = nthr;
+  cp.csize = Cc;
+  cp.npc = (int)(h->nx / Cc);
   cp.p1 = p + 1;
   cp.jlo = -(p + 1) / 2;
   cp.kshift = (int)(((k % h->nx) + h->nx) % h->nx);
-  cp.shift = (int)(((bf.shift % h->nx) + h->nx) % h->nx);
+  cp.shift = 0;
   std::vector<double> w = sl_weights(p, eps);
   for (int a = 0; a <= p; ++a) cp.w[a] = w[a] * bf.inv_kappa;
-  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, Pc, nthr);
-  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, Pc, nthr);
+  std::vector<double> mtc, mta;
+  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, Pc, nthr, Cc, &mtc);
+  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, Pc, nthr, Cc, &mta);
+  for (int d = 0; d < 2; ++d) {
+    std::vector<double>& mt = d ? mta : mtc;
+    if (cudaMalloc((void**)&Lv.Mt_dev[d], sizeof(double) * std::max<size_t>(9, mt.size())) != cudaSuccess) {
+      cudaGetLastError();
+      return MGRIT_ERR_OOM;
+    }
+    if (cudaMemcpy(Lv.Mt_dev[d], mt.data(), sizeof(double) * mt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MGRIT_ERR_CUDA;
+  }
+  cp.c.Mt = Lv.Mt_dev[0];
+  cp.a.Mt = Lv.Mt_dev[1];
   cp.m = h->m;
   Lv.kshift = k;
   Lv.eps = eps;
   Lv.phi = phi_p;
   Lv.phi_q = phi_q;
-  if (coarse_smem_bytes(cp.n, cp.P, cp.nthr, 8) > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
   return MGRIT_OK;
 }
 
@@ -435,6 +499,8 @@ int mgrit_destroy(mgrit_handle* h) {
     cudaFree(Lv.uC[0]);
     cudaFree(Lv.uC[1]);
     cudaFree(Lv.g);
+    cudaFree(Lv.Mt_dev[0]);
+    cudaFree(Lv.Mt_dev[1]);
   }
   for (int c = 0; c < 4; ++c)
     for (auto& pr : h->prof.ev[c]) {
@@ -550,7 +616,8 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
       CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
     }
   }
-  h->npart = std::max<int64_t>(h->lev[0].K * stencil_tiles(P.nx), h->lev[0].K) + 1;
+  h->npart = h->lev[0].K * stencil_tiles(P.nx) + 1;
+  for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * h->lev[l].cp.csize);
   if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
   if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
   if ((rc = alloc(&h->du0, row))) return rc;
@@ -610,7 +677,7 @@ int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
     rc = coarse_launch(h, level, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[level + 1].g, Lv.uC[Lv.cur],
                        nullptr, h->m, Lv.K, Lv.g);
     if (!rc) {
-      launch_reduce_sum(h->partials, Lv.K, h->dnorm, h->st);
+      launch_reduce_sum(h->partials, Lv.K * Lv.cp.csize, h->dnorm, h->st);
       ++h->launches;
       rc = check_launch();
     }
@@ -822,6 +889,7 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   out[3] = Lv.phi;
   out[4] = Lv.phi_q;
   out[6] = (double)Lv.cp.P;
+  out[7] = (double)Lv.cp.csize;
   return MGRIT_OK;
 }
 

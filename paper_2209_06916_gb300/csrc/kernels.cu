@@ -148,106 +148,173 @@ int64_t launch_stencil_rows(const StencilParams<float>& p, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Coarse-level step kernel
+// Coarse-level step kernel (vector distributed over a thread-block cluster)
 // ---------------------------------------------------------------------------
+}  // namespace mg
+#include <cooperative_groups.h>
+namespace mg {
+namespace cgc = cooperative_groups;
 
-// Circular Hillis-Steele scan of chunk carries: on return S holds the true
-// recurrence state entering this thread's chunk (from chunk t-1 when
-// dir = -1, from chunk t+1 when dir = +1).
+// Non-circular inclusive Hillis-Steele scan of chunk states inside the CTA in
+// direction dir (-1: from lower chunks, +1: from higher chunks).  On return
+// the final states are in sq (buffer index returned) and Q holds this
+// chunk's prefix.
 template <int H, typename T>
-__device__ __forceinline__ void chunk_scan(const T (&e)[H], T (&S)[H], const SolveDir<T>& D, T* sq,
-                                           int t, int NT, int dir) {
-  T Q[H];
-#pragma unroll
-  for (int a = 0; a < H; ++a) Q[a] = e[a];
+__device__ __forceinline__ int hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, int t, int NT, int dir) {
   int buf = 0;
   for (int r = 0; r < D.rounds; ++r) {
 #pragma unroll
     for (int a = 0; a < H; ++a) sq[(buf * 3 + a) * NT + t] = Q[a];
     __syncthreads();
-    const int src = (t + dir * (1 << r)) & (NT - 1);
-    T Qo[H];
+    const int src = t + dir * (1 << r);
+    if (src >= 0 && src < NT) {
+      T Qo[H];
 #pragma unroll
-    for (int a = 0; a < H; ++a) Qo[a] = sq[(buf * 3 + a) * NT + src];
+      for (int a = 0; a < H; ++a) Qo[a] = sq[(buf * 3 + a) * NT + src];
 #pragma unroll
-    for (int a = 0; a < H; ++a)
+      for (int a = 0; a < H; ++a)
 #pragma unroll
-      for (int q = 0; q < H; ++q) Q[a] = fma(D.Mpow[r][a * 3 + q], Qo[q], Q[a]);
+        for (int q = 0; q < H; ++q) Q[a] = fma(D.Mpow[r][a * 3 + q], Qo[q], Q[a]);
+    }
     buf ^= 1;
   }
 #pragma unroll
   for (int a = 0; a < H; ++a) sq[(buf * 3 + a) * NT + t] = Q[a];
-  __syncthreads();
-  const int src = (t + dir) & (NT - 1);
-  T Rv[H];
+  return buf;
+}
+
+// Carry S entering this thread's chunk in direction dir, from the final
+// intra-CTA prefixes (sq[buf]) and the cluster-level carry.  `agg` is this
+// CTA's cluster-visible aggregate slot (H values), already published and
+// synchronised across the cluster by the caller.
+template <int H, typename T>
+__device__ __forceinline__ void chunk_carry(T (&S)[H], const SolveDir<T>& D, const T* sq, int buf, T* agg,
+                                            int t, int NT, int dir, int rank, int C) {
+  cgc::cluster_group cl = cgc::this_cluster();
+  T X[H];
 #pragma unroll
-  for (int a = 0; a < H; ++a) Rv[a] = sq[(buf * 3 + a) * NT + src];
+  for (int a = 0; a < H; ++a) X[a] = T(0);
+  for (int j = 0; j < D.jterms; ++j) {
+    int src = rank + dir * (1 + j);
+    src %= C;
+    if (src < 0) src += C;
+    const T* Ap = (C == 1) ? agg : cl.map_shared_rank(agg, src);
+    T Aj[H];
+#pragma unroll
+    for (int a = 0; a < H; ++a) Aj[a] = Ap[a];
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+      for (int q = 0; q < H; ++q) X[a] = fma(D.McPow[j][a * 3 + q], Aj[q], X[a]);
+  }
   if (D.closure) {
+    T Y[H];
 #pragma unroll
     for (int a = 0; a < H; ++a) {
       T v = T(0);
 #pragma unroll
-      for (int q = 0; q < H; ++q) v = fma(D.Cl[a * 3 + q], Rv[q], v);
-      S[a] = v;
+      for (int q = 0; q < H; ++q) v = fma(D.Clc[a * 3 + q], X[q], v);
+      Y[a] = v;
     }
-  } else {
 #pragma unroll
-    for (int a = 0; a < H; ++a) S[a] = Rv[a];
+    for (int a = 0; a < H; ++a) X[a] = Y[a];
+  }
+  // distance (in chunks) from the CTA edge the carry enters through
+  const int tdist = (dir < 0) ? t : (NT - 1 - t);
+#pragma unroll
+  for (int a = 0; a < H; ++a) S[a] = T(0);
+  if (tdist > 0) {
+    const int src = t + dir;
+#pragma unroll
+    for (int a = 0; a < H; ++a) S[a] = sq[(buf * 3 + a) * NT + src];
+  }
+  if (tdist < D.tcut) {
+    const T* Mt = D.Mt + (size_t)tdist * 9;
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+      for (int q = 0; q < H; ++q) S[a] = fma(__ldg(Mt + a * 3 + q), X[q], S[a]);
   }
 }
 
-// Periodic banded solve of the chunk x (in registers) in place:
-// causal recurrence, carry scan, fixup fused with the anticausal local pass,
-// carry scan, fixup.  Every thread of the block must call it.
-template <int H, typename T, int PM>
+// Periodic banded solve of the thread's chunk x (registers) in place: causal
+// recurrence, carry, fixup fused with the anticausal local pass, carry,
+// fixup.  Every thread of every CTA of the cluster must call it.
+template <int HC, int HA, typename T, int PM>
 __device__ __forceinline__ void banded_solve(T (&x)[PM], const CoarseParams<T>& A, T* sqc, T* sqa,
-                                             int t) {
-  const int P = A.P, NT = A.nthr;
-  T e[H];
+                                             T* aggc, T* agga, int t, int rank) {
+  cgc::cluster_group cl = cgc::this_cluster();
+  const int P = A.P, NT = A.nthr, C = A.csize;
+  if (HC > 0) {
+    T Q[HC > 0 ? HC : 1];
 #pragma unroll
-  for (int a = 0; a < H; ++a) e[a] = T(0);
+    for (int a = 0; a < HC; ++a) Q[a] = T(0);
 #pragma unroll
-  for (int j = 0; j < PM; ++j) {
-    if (j < P) {
-      T v = x[j];
+    for (int j = 0; j < PM; ++j) {
+      if (j < P) {
+        T v = x[j];
 #pragma unroll
-      for (int q = 1; q <= H; ++q)
-        if (j - q >= 0) v = fma(A.c.ncoef[q - 1], x[j - q], v);
-      x[j] = v;
+        for (int q = 1; q <= HC; ++q)
+          if (j - q >= 0) v = fma(A.c.ncoef[q - 1], x[j - q], v);
+        x[j] = v;
 #pragma unroll
-      for (int a = 0; a < H; ++a)
-        if (j == P - 1 - a) e[a] = v;
+        for (int a = 0; a < HC; ++a)
+          if (j == P - 1 - a) Q[a] = v;
+      }
+    }
+    int buf = hs_scan<HC>(Q, A.c, sqc, t, NT, -1);
+    if (t == NT - 1) {
+#pragma unroll
+      for (int a = 0; a < HC; ++a) aggc[a] = Q[a];
+    }
+    cl.sync();
+    T S[HC > 0 ? HC : 1];
+    chunk_carry<HC>(S, A.c, sqc, buf, aggc, t, NT, -1, rank, C);
+#pragma unroll
+    for (int j = 0; j < PM; ++j) {
+      if (j < P) {
+        T v = x[j];
+#pragma unroll
+        for (int q = 0; q < HC; ++q) v = fma(A.c.G[j * 3 + q], S[q], v);
+        x[j] = v;
+      }
     }
   }
-  T S[H];
-  chunk_scan<H>(e, S, A.c, sqc, t, NT, -1);
+  if (HA > 0) {
+    T Q[HA > 0 ? HA : 1];
 #pragma unroll
-  for (int j = PM - 1; j >= 0; --j) {
-    if (j < P) {
-      T v = x[j];
+    for (int a = 0; a < HA; ++a) Q[a] = T(0);
 #pragma unroll
-      for (int q = 0; q < H; ++q) v = fma(A.c.G[j * 3 + q], S[q], v);
+    for (int j = PM - 1; j >= 0; --j) {
+      if (j < P) {
+        T v = x[j];
 #pragma unroll
-      for (int q = 1; q <= H; ++q)
-        if (j + q < PM) {
-          if (j + q < P) v = fma(A.a.ncoef[q - 1], x[j + q], v);
-        }
-      x[j] = v;
+        for (int q = 1; q <= HA; ++q)
+          if (j + q < PM) {
+            if (j + q < P) v = fma(A.a.ncoef[q - 1], x[j + q], v);
+          }
+        x[j] = v;
+      }
     }
-  }
-  T ea[H];
 #pragma unroll
-  for (int a = 0; a < H; ++a) ea[a] = x[a];
-  T Sa[H];
-  chunk_scan<H>(ea, Sa, A.a, sqa, t, NT, +1);
+    for (int a = 0; a < HA; ++a) Q[a] = x[a];
+    int buf = hs_scan<HA>(Q, A.a, sqa, t, NT, +1);
+    if (t == 0) {
 #pragma unroll
-  for (int j = 0; j < PM; ++j) {
-    if (j < P) {
-      const int d = P - 1 - j;
-      T v = x[j];
+      for (int a = 0; a < HA; ++a) agga[a] = Q[a];
+    }
+    cl.sync();
+    T S[HA > 0 ? HA : 1];
+    chunk_carry<HA>(S, A.a, sqa, buf, agga, t, NT, +1, rank, C);
 #pragma unroll
-      for (int q = 0; q < H; ++q) v = fma(A.a.G[d * 3 + q], Sa[q], v);
-      x[j] = v;
+    for (int j = 0; j < PM; ++j) {
+      if (j < P) {
+        const int d = P - 1 - j;
+        T v = x[j];
+#pragma unroll
+        for (int q = 0; q < HA; ++q) v = fma(A.a.G[d * 3 + q], S[q], v);
+        x[j] = v;
+      }
     }
   }
 }
@@ -256,42 +323,51 @@ template <typename T, int PM, int P1>
 __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ CoarseParams<T> A) {
   constexpr int H = P1 / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = A.n, P = A.P, NT = A.nthr, t = threadIdx.x;
-  const int npad = n + (n + P - 1) / P;
-  T* sv = reinterpret_cast<T*>(smem_raw);
-  T* sg = sv + npad;
+  cgc::cluster_group cl = cgc::this_cluster();
+  const int n = A.n, P = A.P, NT = A.nthr, C = A.csize, npc = A.npc, t = threadIdx.x;
+  const int rank = (int)cl.block_rank();
+  const int npad = npc + (npc + P - 1) / P;
+  T* sv0 = reinterpret_cast<T*>(smem_raw);
+  T* sv1 = sv0 + npad;
+  T* sg = sv1 + npad;
   T* sqc = sg + npad;
   T* sqa = sqc + 6 * NT;
-  double* red = reinterpret_cast<double*>(sqa + 6 * NT);
-  const int64_t k = blockIdx.x;
+  T* aggc = sqa + 6 * NT;
+  T* agga = aggc + 4;
+  double* red = reinterpret_cast<double*>(agga + 4);
+  const int64_t k = blockIdx.x / C;
   const int64_t nn = n;
+  const int64_t off = (int64_t)rank * npc;  // first global point of this CTA
+  T* cur = sv0;
+  T* nxt = sv1;
 
-  // initial state
   if (A.zero_start) {
-    for (int i = t; i < n; i += NT) sv[i + i / P] = T(0);
+    for (int i = t; i < npc; i += NT) cur[i + i / P] = T(0);
   } else {
-    const T* src = A.start + k * nn;
-    for (int i = t; i < n; i += NT) sv[i + i / P] = src[i];
+    const T* src = A.start + k * nn + off;
+    for (int i = t; i < npc; i += NT) cur[i + i / P] = src[i];
   }
   if (A.mode == kModeFOUT) {
-    // the C-points themselves: parent row k m gets start[k]; the last CTA
-    // also adds start[K] to parent row K m
-    const T* src = A.start + k * nn;
-    T* par = A.parent + k * A.m * nn;
-    for (int i = t; i < n; i += NT) par[i] += src[i];
+    const T* src = A.start + k * nn + off;
+    T* par = A.parent + k * A.m * nn + off;
+    for (int i = t; i < npc; i += NT) par[i] += src[i];
     if (k == A.K - 1) {
-      const T* s2 = A.start + A.K * nn;
-      T* p2 = A.parent + A.K * A.m * nn;
-      for (int i = t; i < n; i += NT) p2[i] += s2[i];
+      const T* s2 = A.start + A.K * nn + off;
+      T* p2 = A.parent + A.K * A.m * nn + off;
+      for (int i = t; i < npc; i += NT) p2[i] += s2[i];
     }
   }
-  __syncthreads();
+  cl.sync();
+
+  // SL gather window of this thread: global indices gw0 + w, w < P + P1 - 1
+  int gw0 = (int)((off + (int64_t)t * P - A.kshift + A.jlo) % nn);
+  if (gw0 < 0) gw0 += n;
 
   const int64_t gbase = (A.mode == kModeSEQ) ? 0 : k * A.m;
   for (int s = 1; s <= A.nsteps; ++s) {
     if (A.g) {
-      const T* gr = A.g + (gbase + s) * nn;
-      for (int i = t; i < n; i += NT) sg[i + i / P] = gr[i];
+      const T* gr = A.g + (gbase + s) * nn + off;
+      for (int i = t; i < npc; i += NT) sg[i + i / P] = gr[i];
     }
     T x[PM];
     if (s == 1 && A.zero_start) {
@@ -299,25 +375,23 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
       for (int j = 0; j < PM; ++j) x[j] = T(0);
       __syncthreads();
     } else {
-      // SL gather over the own chunk with a sliding window of P1 values:
-      // (S v)_i = sum_a w_a v_{i - k + jlo + a}
-      int idx = (t * P - A.kshift + A.jlo) % n;
-      if (idx < 0) idx += n;
       T win[P1];
+      auto fetch = [&](int w) -> T {
+        int gi = gw0 + w;
+        if (gi >= n) gi -= n;
+        if (gi >= n) gi -= n;
+        if (C == 1) return cur[gi + gi / P];
+        const int owner = gi / npc;
+        const int li = gi - owner * npc;
+        const T* base = cl.map_shared_rank(cur, owner);
+        return base[li + li / P];
+      };
 #pragma unroll
-      for (int a = 0; a < P1 - 1; ++a) {
-        int ii = idx + a;
-        if (ii >= n) ii -= n;
-        if (ii >= n) ii -= n;
-        win[a] = sv[ii + ii / P];
-      }
+      for (int a = 0; a < P1 - 1; ++a) win[a] = fetch(a);
 #pragma unroll
       for (int j = 0; j < PM; ++j) {
         if (j < P) {
-          int ii = idx + j + P1 - 1;
-          if (ii >= n) ii -= n;
-          if (ii >= n) ii -= n;
-          win[P1 - 1] = sv[ii + ii / P];
+          win[P1 - 1] = fetch(j + P1 - 1);
           T acc = T(0);
 #pragma unroll
           for (int a = 0; a < P1; ++a) acc = fma(A.w[a], win[a], acc);
@@ -327,79 +401,107 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
         }
       }
       __syncthreads();
-      banded_solve<H, T, PM>(x, A, sqc, sqa, t);
+      banded_solve<H, H, T, PM>(x, A, sqc, sqa, aggc, agga, t, rank);
     }
-    // new state v_{i - shift} = x_i + g
+    // new state v_{i - shift} = x_i + g (the shift stays inside this CTA's
+    // range for the symmetric factorisation: shift = 0)
 #pragma unroll
     for (int j = 0; j < PM; ++j) {
       if (j < P) {
         int i2 = t * P + j - A.shift;
-        if (i2 < 0) i2 += n;
-        if (i2 >= n) i2 -= n;
+        if (i2 < 0) i2 += npc;
         T v = x[j];
         if (A.g) v += sg[i2 + i2 / P];
-        sv[i2 + i2 / P] = v;
+        nxt[i2 + i2 / P] = v;
       }
     }
-    __syncthreads();
+    cl.sync();
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
     if (A.mode == kModeFOUT || A.mode == kModeSEQ) {
-      T* par = A.parent + (gbase + s) * nn;
-      for (int i = t; i < n; i += NT) par[i] += sv[i + i / P];
+      T* par = A.parent + (gbase + s) * nn + off;
+      for (int i = t; i < npc; i += NT) par[i] += cur[i + i / P];
     }
   }
 
   if (A.mode == kModeCF) {
-    T* o = A.out + (k + 1) * nn;
-    for (int i = t; i < n; i += NT) o[i] = sv[i + i / P];
+    T* o = A.out + (k + 1) * nn + off;
+    for (int i = t; i < npc; i += NT) o[i] = cur[i + i / P];
   } else if (A.mode == kModeAPPLY) {
-    T* o = A.out + k * nn;
-    for (int i = t; i < n; i += NT) o[i] = sv[i + i / P];
+    T* o = A.out + k * nn + off;
+    for (int i = t; i < npc; i += NT) o[i] = cur[i + i / P];
   } else if (A.mode == kModeFRES) {
-    T* o = A.out + (k + 1) * nn;
-    const T* sb = A.sub ? A.sub + (k + 1) * nn : nullptr;
+    T* o = A.out + (k + 1) * nn + off;
+    const T* sb = A.sub ? A.sub + (k + 1) * nn + off : nullptr;
     double sq = 0.0;
-    for (int i = t; i < n; i += NT) {
-      T r = sv[i + i / P];
+    for (int i = t; i < npc; i += NT) {
+      T r = cur[i + i / P];
       if (sb) r -= sb[i];
       o[i] = r;
       sq += (double)r * (double)r;
     }
     if (A.partial) {
       double tot = block_sum(sq, red);
-      if (t == 0) A.partial[k] = tot;
+      if (t == 0) A.partial[blockIdx.x] = tot;
     }
   }
+  // keep this CTA's shared memory alive until the cluster has finished its
+  // remote reads of it
+  cl.sync();
 }
 
-size_t coarse_smem_bytes(int n, int P, int nthr, int elem) {
-  size_t npad = (size_t)n + (size_t)((n + P - 1) / P);
-  return (2 * npad + 12 * (size_t)nthr) * (size_t)elem + 32 * sizeof(double) + 16;
+size_t coarse_smem_bytes(int npc, int P, int nthr, int elem) {
+  size_t npad = (size_t)npc + (size_t)((npc + P - 1) / P);
+  return (3 * npad + 12 * (size_t)nthr + 8) * (size_t)elem + 32 * sizeof(double) + 16;
+}
+
+template <typename T, int PM, int P1>
+static void configure_coarse() {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(coarse_kernel<T, PM, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(coarse_kernel<T, PM, P1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    configured = true;
+  }
 }
 
 template <typename T, int PM, int P1>
 static int launch_coarse_t(const CoarseParams<T>& A, cudaStream_t st) {
-  size_t smem = coarse_smem_bytes(A.n, A.P, A.nthr, (int)sizeof(T));
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(coarse_kernel<T, PM, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    configured = true;
-  }
+  configure_coarse<T, PM, P1>();
   if (A.K <= 0) return 0;
-  coarse_kernel<T, PM, P1><<<(unsigned)A.K, A.nthr, smem, st>>>(A);
-  return 1;
+  size_t smem = coarse_smem_bytes(A.npc, A.P, A.nthr, (int)sizeof(T));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.K * A.csize));
+  cfg.blockDim = dim3((unsigned)A.nthr);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)A.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, coarse_kernel<T, PM, P1>, A) == cudaSuccess ? 1 : -1;
+}
+
+template <typename T, int P1>
+static int launch_coarse_p(const CoarseParams<T>& A, cudaStream_t st) {
+  if (A.P <= 16) return launch_coarse_t<T, 16, P1>(A, st);
+  if (A.P <= 32) return launch_coarse_t<T, 32, P1>(A, st);
+  return launch_coarse_t<T, 64, P1>(A, st);
 }
 
 template <typename T>
 static int launch_coarse_any(const CoarseParams<T>& A, cudaStream_t st) {
-  const bool big = A.P > 32;
   switch (A.p1) {
     case 2:
-      return big ? launch_coarse_t<T, 64, 2>(A, st) : launch_coarse_t<T, 32, 2>(A, st);
+      return launch_coarse_p<T, 2>(A, st);
     case 4:
-      return big ? launch_coarse_t<T, 64, 4>(A, st) : launch_coarse_t<T, 32, 4>(A, st);
+      return launch_coarse_p<T, 4>(A, st);
     case 6:
-      return big ? launch_coarse_t<T, 64, 6>(A, st) : launch_coarse_t<T, 32, 6>(A, st);
+      return launch_coarse_p<T, 6>(A, st);
     default:
       return -1;
   }
@@ -407,6 +509,29 @@ static int launch_coarse_any(const CoarseParams<T>& A, cudaStream_t st) {
 
 int launch_coarse(const CoarseParams<double>& p, cudaStream_t st) { return launch_coarse_any(p, st); }
 int launch_coarse(const CoarseParams<float>& p, cudaStream_t st) { return launch_coarse_any(p, st); }
+
+// Largest cluster size <= want (power of two) that can be co-scheduled.
+int coarse_max_cluster(int want, size_t smem, int nthr) {
+  configure_coarse<double, 32, 4>();
+  for (int c = want; c >= 1; c >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c);
+    cfg.blockDim = dim3((unsigned)nthr);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, coarse_kernel<double, 32, 4>, &cfg) == cudaSuccess && nc > 0)
+      return c;
+    cudaGetLastError();
+  }
+  return 1;
+}
 
 // ---------------------------------------------------------------------------
 // utilities

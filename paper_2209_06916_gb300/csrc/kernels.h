@@ -34,17 +34,27 @@ int64_t launch_stencil_rows(const StencilParams<double>& p, cudaStream_t st);
 int64_t launch_stencil_rows(const StencilParams<float>& p, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
-// In-block periodic banded solve tables (one direction).
+// Periodic banded solve tables (one recurrence direction).  A vector of n
+// points is split over C CTAs of a thread-block cluster, each CTA over NT
+// chunks of P points (one chunk per thread).  The carry between chunks is
+// found by an intra-CTA Hillis-Steele scan (transfer powers Mpow), then a
+// cluster-level sum over the previous `jterms` CTAs' aggregates (McPow, the
+// closure Clc when the sum wraps the whole ring), then the per-chunk term
+// M^t X (device table Mt, t < tcut; beyond tcut it is below 1e-18).
 // ---------------------------------------------------------------------------
 template <typename T>
 struct SolveDir {
   int h;
   int rounds;
-  int closure;         // 1: apply Cl to the carry (full circular scan)
+  int tcut;
+  int jterms;
+  int closure;
   T ncoef[3];          // negated recurrence coefficients
   T Mpow[kMaxRounds][9];
-  T Cl[9];
+  T McPow[16][9];
+  T Clc[9];
   T G[kPMax * 3];      // impulse responses G[j*3+q]
+  const T* Mt;         // tcut x 9 (device)
 };
 
 // Coarse-level step Phi_l v + g: SL gather (weights pre-scaled by 1/kappa),
@@ -54,6 +64,8 @@ enum CoarseMode { kModeCF = 0, kModeFRES = 1, kModeFOUT = 2, kModeSEQ = 3, kMode
 template <typename T>
 struct CoarseParams {
   int n, P, nthr;
+  int csize;           // CTAs per vector (thread-block cluster size)
+  int npc;             // points per CTA = nthr * P
   int p1;              // p + 1 SL weights
   int jlo;             // node offset of weight 0: -(p+1)/2
   int kshift;          // SL shift k_l mod n
@@ -70,12 +82,13 @@ struct CoarseParams {
   T* out;
   const T* sub;
   T* parent;
-  double* partial;
+  double* partial;     // FRES: one slot per CTA (K * csize)
 };
 
-size_t coarse_smem_bytes(int n, int P, int nthr, int elem);
+size_t coarse_smem_bytes(int npc, int P, int nthr, int elem);
 int launch_coarse(const CoarseParams<double>& p, cudaStream_t st);
 int launch_coarse(const CoarseParams<float>& p, cudaStream_t st);
+int coarse_max_cluster(int want, size_t smem, int nthr);
 
 // ---------------------------------------------------------------------------
 // Utilities

@@ -75,6 +75,8 @@ CASES = [  # p, c, m, levels, nx
     (3, 1.2, 2, 6, 64),
     (1, 0.5, 16, 3, 1536),
     (5, 1.5, 8, 3, 40),
+    (5, 0.9, 16, 4, 4096),   # deep level: |phi| ~ 1e3, slow decay, 16-CTA clusters
+    (1, 0.85, 4, 5, 2048),
 ]
 
 
@@ -92,6 +94,7 @@ def test_coarse_operators_match_oracle(p, c, m, levels, nx):
         k, eps = co.sl_shift(c * m ** lev)
         assert int(info[1]) == k and abs(info[2] - eps) < 1e-12
         assert abs(info[3] - co.phi_levels(p, "erk", c, m, levels)[lev - 1]) < 1e-9 * max(1, abs(info[3]))
+        assert info[7] >= 1
 
 
 # ---------------------------------------------------------------------------
