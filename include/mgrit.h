@@ -55,8 +55,10 @@ extern "C" {
 
 #define MGRIT_FP64 0  /* every kernel in FP64                                  */
 #define MGRIT_MIXED 1 /* FP32 relaxation sweeps inside FP64 iterative          */
-                      /* refinement: FP64 C-point residual, norm, coarsest    */
-                      /* solve and correction solves                          */
+                      /* refinement: FP64 C-point residual and norm (level 0) */
+                      /* and FP64 coarsest sequential solve; correction       */
+                      /* solves in FP64 on levels whose correction matrix has */
+                      /* condition number > 1e3, FP32 elsewhere               */
 
 #define MGRIT_MAX_LEVELS 16
 #define MGRIT_MAX_HISTORY 128
@@ -78,6 +80,7 @@ typedef struct mgrit_params {
   int max_iter;     /* iteration cap (default 30, Sec. 6.3)                     */
   int precision;    /* MGRIT_FP64 or MGRIT_MIXED                                */
   uint64_t seed;    /* seed of the random initial iterate (SplitMix64)          */
+  int inner_cycles; /* MIXED: FP32 inner cycles per FP64 residual (0: 2)       */
 } mgrit_params;
 
 /* ---- statistics -------------------------------------------------------- */
@@ -215,11 +218,13 @@ int64_t mgrit_launch_count(const mgrit_handle* h);
  * clears the counters.  Not in the paper: measurement support.
  * mgrit_profile_read -- out[3c+0] launches, out[3c+1] summed device ms,
  * out[3c+2] algorithmic flops (2 per multiply-add the kernel must do) for
- * category c = 0 level-0 composite stencil, 1 coarse step kernel,
- * 2 reductions, 3 sequential stepping.  Synchronises the stream.
+ * category c = 0 level-0 composite stencil, 1 coarse step kernel (all
+ * levels), 2 reductions, 3 sequential stepping, 4 + l coarse step kernel on
+ * level l (l = 1..15, the last slot collects deeper levels); 20 categories,
+ * out has 60 entries.  Synchronises the stream.
  */
 int mgrit_profile(mgrit_handle* h, int enable);
-int mgrit_profile_read(mgrit_handle* h, double out[12]);
+int mgrit_profile_read(mgrit_handle* h, double out[60]);
 
 /*
  * mgrit_residual_noalloc -- the level-0 C-point residual of mgrit_residual

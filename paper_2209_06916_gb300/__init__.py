@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
         ("alpha", ctypes.c_double), ("order_p", ctypes.c_int), ("rk_kind", ctypes.c_int),
         ("rk_order_q", ctypes.c_int), ("m", ctypes.c_int), ("levels", ctypes.c_int),
         ("nu", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-        ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int), ("seed", ctypes.c_uint64), ("inner_cycles", ctypes.c_int),
     ]
 
 
@@ -119,9 +119,10 @@ def _check(code, what):
 
 
 def make_params(nx, nt, cfl, p, kind=ERK, q=0, m=4, levels=2, nu=1, tol=1e-10, max_iter=30,
-                precision=FP64, seed=0, alpha=1.0):
+                precision=FP64, seed=0, alpha=1.0, inner_cycles=0):
     return Params(nx=nx, nt=nt, cfl=cfl, alpha=alpha, order_p=p, rk_kind=kind, rk_order_q=q, m=m,
-                  levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed)
+                  levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed,
+                  inner_cycles=inner_cycles)
 
 
 class Solver:
@@ -213,7 +214,8 @@ class Solver:
     def profile_read(self):
         """{category: (launches, device ms, algorithmic flops)} for
         'stencil0' (level-0 composite stencil), 'coarse', 'reduce'."""
-        out = (ctypes.c_double * 12)()
+        out = (ctypes.c_double * 60)()
         _check(self.lib.mgrit_profile_read(self.h, out), "mgrit_profile_read")
-        names = ("stencil0", "coarse", "reduce", "sequential")
-        return {n: (int(out[3 * i]), out[3 * i + 1], out[3 * i + 2]) for i, n in enumerate(names)}
+        names = ["stencil0", "coarse", "reduce", "sequential"] + ["coarse_l%d" % l for l in range(16)]
+        d = {n: (int(out[3 * i]), out[3 * i + 1], out[3 * i + 2]) for i, n in enumerate(names)}
+        return {k: v for k, v in d.items() if not k.startswith("coarse_l") or v[0] > 0}

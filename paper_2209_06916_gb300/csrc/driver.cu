@@ -37,11 +37,26 @@ struct LevelData {
   // coarse operator (l >= 1)
   CoarseParams<double> cp;
   double* Mt_dev[2] = {nullptr, nullptr};  // per-chunk carry tables (causal, anticausal)
+  // MIXED: FP32 inner-cycle data (level 0: uCf = error e, gf = its C-point
+  // RHS r; level l: uCf, gf as in FP64), FP32-SL operators with an FP32 or
+  // FP64 correction solve
+  float* uCf[2] = {nullptr, nullptr};
+  int curf = 0;
+  float* gf = nullptr;
+  CoarseParams<float, float> cpf;
+  CoarseParams<float, double> cpfd;
+  float* Mtf_dev[2] = {nullptr, nullptr};
+  bool solve64 = false;
+  double kappa = 1.0;
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
 };
 
 }  // namespace
+
+// profiling categories: 0 level-0 stencil, 1 coarse kernel (all levels),
+// 2 reductions, 3 sequential stepping, 4 + l coarse kernel on level l
+constexpr int kProfCats = 20;
 
 struct mgrit_handle {
   mgrit_params prm;
@@ -50,8 +65,16 @@ struct mgrit_handle {
   int64_t nx = 0;
   int m = 0;
   int device = 0;
-  std::unique_ptr<StencilParams<double>> fineM;  // Phi^m composite
-  std::unique_ptr<StencilParams<double>> fine1;  // Phi (one step)
+  std::unique_ptr<StencilParams<double>> fineM;  // Phi^m composite (ERK)
+  std::unique_ptr<StencilParams<double>> fine1;  // Phi (one step, ERK)
+  std::unique_ptr<SdirkParams<double>> sd0;      // SDIRK step program (level 0)
+  std::unique_ptr<StencilParams<float>> fineMf;  // MIXED: Phi^m in FP32 (ERK)
+  std::unique_ptr<SdirkParams<float>> sd0f;      // MIXED: SDIRK programme in FP32
+  float* sdf_Mt[2] = {nullptr, nullptr};
+  double* seq_tmp = nullptr;                     // MIXED: FP64 coarsest-level output
+  bool mixed = false;
+  double* sd_Mt[2] = {nullptr, nullptr};
+  bool sdirk = false;
   int fineM_taps_raw = 0;
   std::vector<LevelData> lev;
   double* partials = nullptr;
@@ -66,9 +89,9 @@ struct mgrit_handle {
   struct Prof {
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
-    double flops[4] = {0, 0, 0, 0};
-    int64_t count[4] = {0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kProfCats];
+    double flops[kProfCats] = {};
+    int64_t count[kProfCats] = {};
   } prof;
 };
 
@@ -204,15 +227,41 @@ static Stencil fold_mod(const Stencil& s, int64_t nx) {
   return f;
 }
 
-static int set_stencil(StencilParams<double>* sp, const Stencil& s0, int64_t nx) {
+template <typename T>
+static int set_stencil(StencilParams<T>* sp, const Stencil& s0, int64_t nx) {
   Stencil s = fold_mod(s0, nx);
   if (s.width() > kMaxTaps) return MGRIT_ERR_UNSUPPORTED;
   std::memset((void*)sp, 0, sizeof(*sp));
   sp->nx = nx;
   sp->lo = s.lo;
   sp->ntaps = s.width();
-  for (int i = 0; i < s.width(); ++i) sp->taps[i] = s.a[i];
+  for (int i = 0; i < s.width(); ++i) sp->taps[i] = (T)s.a[i];
   return MGRIT_OK;
+}
+
+template <typename T>
+static int upload_table(const std::vector<T>& v, T** dev) {
+  if (cudaMalloc((void**)dev, sizeof(T) * std::max<size_t>(9, v.size())) != cudaSuccess) {
+    cudaGetLastError();
+    return MGRIT_ERR_OOM;
+  }
+  if (!v.empty() && cudaMemcpy(*dev, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MGRIT_ERR_CUDA;
+  return MGRIT_OK;
+}
+
+// Condition number of a symmetric periodic banded matrix from its (real)
+// symbol sampled on the unit circle.
+static double band_condition(const Stencil& A) {
+  double amin = 1e300, amax = 0.0;
+  const int ns = 4096;
+  for (int i = 0; i < ns; ++i) {
+    double th = 2.0 * M_PI * i / ns, v = 0.0;
+    for (int t = A.lo; t <= A.hi; ++t) v += A.at(t) * std::cos(t * th);
+    amin = std::min(amin, std::fabs(v));
+    amax = std::max(amax, std::fabs(v));
+  }
+  return amin > 0.0 ? amax / amin : 1e300;
 }
 
 // phi recursion (Lemma 6.1 / the multilevel recursion of Sec. 6.2) and the generalised two-term form
@@ -315,11 +364,214 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   cp.c.Mt = Lv.Mt_dev[0];
   cp.a.Mt = Lv.Mt_dev[1];
   cp.m = h->m;
+  Lv.kappa = band_condition(A);
+  if (P.precision == MGRIT_MIXED) {
+    // FP32 storage and SL gather; the correction solve in FP64 where an FP32
+    // solve would lose more than about four of its seven digits
+    Lv.solve64 = Lv.kappa > 1e3;
+    auto geom = [&](auto& q) {
+      std::memset((void*)&q, 0, sizeof(q));
+      q.n = cp.n;
+      q.P = cp.P;
+      q.nthr = cp.nthr;
+      q.csize = cp.csize;
+      q.npc = cp.npc;
+      q.p1 = cp.p1;
+      q.jlo = cp.jlo;
+      q.kshift = cp.kshift;
+      q.shift = cp.shift;
+      q.m = cp.m;
+      for (int a = 0; a <= p; ++a) q.w[a] = (float)cp.w[a];
+    };
+    geom(Lv.cpfd);
+    Lv.cpfd.c = cp.c;
+    Lv.cpfd.a = cp.a;
+    geom(Lv.cpf);
+    std::vector<float> mtcf, mtaf;
+    fill_solve_dir(&Lv.cpf.c, bf.cc, bf.hc, H, Pc, nthr, Cc, &mtcf);
+    fill_solve_dir(&Lv.cpf.a, bf.ca, bf.ha, H, Pc, nthr, Cc, &mtaf);
+    int rc = upload_table(mtcf, &Lv.Mtf_dev[0]);
+    if (!rc) rc = upload_table(mtaf, &Lv.Mtf_dev[1]);
+    if (rc) return rc;
+    Lv.cpf.c.Mt = Lv.Mtf_dev[0];
+    Lv.cpf.a.Mt = Lv.Mtf_dev[1];
+  }
   Lv.kshift = k;
   Lv.eps = eps;
   Lv.phi = phi_p;
   Lv.phi_q = phi_q;
   return MGRIT_OK;
+}
+
+
+// Level-0 SDIRK step programme: stiffly accurate stages (q <= 4),
+//   R_i = u (i >= 1);  Y_i = (I + gamma c L)^{-1} R_i;  R_j += -c a_ji L Y_i,
+// u_new = Y_s; or the factored SDIRK5 stability function
+//   v <- (I + gamma c L)^{-1} f_k(-c L) v for each real factor f_k of P,
+// then the remaining solves.
+static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamma, std::string* why) {
+  int n = 0;
+  auto op = [&](int kind, int dst, int src, double cf) {
+    if (n >= kSdirkMaxOps) return;
+    sp->opk[n] = kind;
+    sp->opd[n] = dst;
+    sp->ops[n] = src;
+    sp->opc[n] = cf;
+    ++n;
+  };
+  if (q <= 4) {
+    SdirkTableau tb;
+    if (!sdirk_tableau(q, &tb)) return false;
+    *gamma = tb.A[0][0];
+    for (int i = 1; i < tb.s; ++i) op(kOpCopy, i, 0, 0.0);
+    for (int i = 0; i < tb.s; ++i) {
+      op(kOpSolve, i, i, 0.0);
+      for (int j = i + 1; j < tb.s; ++j) op(kOpAxpyL, j, i, -c * tb.A[j][i]);
+    }
+    sp->nslots = tb.s;
+    sp->result = tb.s - 1;
+  } else {
+    std::vector<std::vector<double>> f = sdirk5_factors(gamma);
+    for (auto& fk : f) {
+      op(kOpCopy, 1, 0, 0.0);
+      op(kOpZero, 2, 0, 0.0);
+      op(kOpAxpyL, 2, 0, 1.0);
+      op(kOpAxpy, 1, 2, -c * fk[1]);
+      if (fk.size() == 3) op(kOpAxpyL, 1, 2, c * c * fk[2]);
+      op(kOpSolve, 0, 1, 0.0);
+    }
+    for (int r = (int)f.size(); r < 5; ++r) op(kOpSolve, 0, 0, 0.0);
+    sp->nslots = 3;
+    sp->result = 0;
+  }
+  if (n >= kSdirkMaxOps) {
+    if (why) *why = "SDIRK programme too long";
+    return false;
+  }
+  sp->nops = n;
+  return true;
+}
+
+static int build_sdirk(mgrit_handle* h, std::string* why) {
+  const mgrit_params& P = h->prm;
+  const int p = P.order_p;
+  h->sd0.reset(new SdirkParams<double>());
+  SdirkParams<double>& sp = *h->sd0;
+  std::memset((void*)&sp, 0, sizeof(sp));
+  double gamma = 0.0;
+  if (!sdirk_program(P.rk_order_q, P.cfl, &sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
+  Stencil L = upwind_taps(p);
+  sp.p1 = L.width();
+  sp.llo = L.lo;
+  for (int i = 0; i < L.width(); ++i) sp.ltaps[i] = L.a[i];
+  BandFactor bf;
+  Stencil A = stencil_add(stencil_identity(), L, gamma * P.cfl);
+  if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
+  const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
+  if (bf.hc > HC || bf.ha > HA || bf.shift != 0) {
+    if (why) *why = "stage matrix factorisation outside the kernel's orders";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  sp.sscale = bf.inv_kappa;
+  // geometry: like a coarse level with K0 intervals, then more CTAs per
+  // vector until the slots fit in shared memory
+  int C, Pc, nthr;
+  if (!pick_coarse_geometry(h->nx, h->lev[0].K, &C, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
+  while (sdirk_smem_bytes((int)(h->nx / C), Pc, nthr, sp.nslots, 8) > 227 * 1024) {
+    if (C >= 16 || h->nx % (2 * C)) return MGRIT_ERR_UNSUPPORTED;
+    C *= 2;
+    if ((h->nx / C) % Pc) return MGRIT_ERR_UNSUPPORTED;
+    nthr = (int)(h->nx / C / Pc);
+  }
+  while (nthr > 256) {
+    if ((h->nx / C) % (2 * Pc) || 2 * Pc > kPMax) return MGRIT_ERR_UNSUPPORTED;
+    Pc *= 2;
+    nthr /= 2;
+  }
+  size_t smem = sdirk_smem_bytes((int)(h->nx / C), Pc, nthr, sp.nslots, 8);
+  if (C > 1 && coarse_max_cluster(C, smem, nthr) < C) return MGRIT_ERR_UNSUPPORTED;
+  sp.n = (int)h->nx;
+  sp.P = Pc;
+  sp.nthr = nthr;
+  sp.csize = C;
+  sp.npc = (int)(h->nx / C);
+  std::vector<double> mtc, mta;
+  fill_solve_dir(&sp.c, bf.cc, bf.hc, HC, Pc, nthr, C, &mtc);
+  fill_solve_dir(&sp.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mta);
+  for (int dd = 0; dd < 2; ++dd) {
+    std::vector<double>& mt = dd ? mta : mtc;
+    if (cudaMalloc((void**)&h->sd_Mt[dd], sizeof(double) * std::max<size_t>(9, mt.size())) != cudaSuccess) {
+      cudaGetLastError();
+      return MGRIT_ERR_OOM;
+    }
+    if (!mt.empty() &&
+        cudaMemcpy(h->sd_Mt[dd], mt.data(), sizeof(double) * mt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MGRIT_ERR_CUDA;
+  }
+  sp.c.Mt = h->sd_Mt[0];
+  sp.a.Mt = h->sd_Mt[1];
+  h->sdirk = true;
+  if (P.precision == MGRIT_MIXED) {
+    h->sd0f.reset(new SdirkParams<float>());
+    SdirkParams<float>& f = *h->sd0f;
+    std::memset((void*)&f, 0, sizeof(f));
+    f.n = sp.n;
+    f.P = sp.P;
+    f.nthr = sp.nthr;
+    f.csize = sp.csize;
+    f.npc = sp.npc;
+    f.p1 = sp.p1;
+    f.llo = sp.llo;
+    for (int i = 0; i < 8; ++i) f.ltaps[i] = (float)sp.ltaps[i];
+    f.sscale = (float)sp.sscale;
+    f.nops = sp.nops;
+    f.nslots = sp.nslots;
+    f.result = sp.result;
+    for (int o = 0; o < kSdirkMaxOps; ++o) {
+      f.opk[o] = sp.opk[o];
+      f.opd[o] = sp.opd[o];
+      f.ops[o] = sp.ops[o];
+      f.opc[o] = (float)sp.opc[o];
+    }
+    std::vector<float> mtcf, mtaf;
+    fill_solve_dir(&f.c, bf.cc, bf.hc, HC, Pc, nthr, C, &mtcf);
+    fill_solve_dir(&f.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mtaf);
+    int rc = upload_table(mtcf, &h->sdf_Mt[0]);
+    if (!rc) rc = upload_table(mtaf, &h->sdf_Mt[1]);
+    if (rc) return rc;
+    f.c.Mt = h->sdf_Mt[0];
+    f.a.Mt = h->sdf_Mt[1];
+  }
+  return MGRIT_OK;
+}
+
+static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double* start, double* out,
+                        const double* sub, int nsteps, int64_t K, double* traj, int every, int cat_flops) {
+  SdirkParams<double> sp = *h->sd0;
+  sp.mode = mode;
+  sp.zero_start = zero_start;
+  sp.start = start;
+  sp.out = out;
+  sp.sub = sub;
+  sp.rhs = nullptr;
+  sp.nsteps = nsteps;
+  sp.K = K;
+  sp.traj = traj;
+  sp.every = every;
+  sp.partial = (mode == kModeFRES) ? h->partials : nullptr;
+  // multiply-adds per point-step: solves (2 recurrences + fixups) and L mat-vecs
+  int nsolve = 0, naxl = 0, nax = 0;
+  for (int o = 0; o < sp.nops; ++o) {
+    nsolve += sp.opk[o] == kOpSolve;
+    naxl += sp.opk[o] == kOpAxpyL;
+    nax += sp.opk[o] == kOpAxpy;
+  }
+  const int H2 = sp.c.h + sp.a.h;
+  const double per_pt = nsolve * (H2 + 1) + naxl * (sp.p1 + 1) + nax;
+  ProfScope ps(h, cat_flops, 2.0 * per_pt * (double)h->nx * (double)K * (double)nsteps);
+  if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  ++h->launches;
+  return check_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -329,6 +581,11 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
 // level 0: out rows 1..K = Phi^m in rows 0..K-1 (+ optional residual form)
 static int l0_cf(mgrit_handle* h) {
   LevelData& L0 = h->lev[0];
+  if (h->sdirk) {
+    int rc = sdirk_launch(h, kModeCF, 0, L0.uC[L0.cur], L0.uC[1 - L0.cur], nullptr, h->m, L0.K, nullptr, 0, 0);
+    L0.cur = 1 - L0.cur;
+    return rc;
+  }
   StencilParams<double>& sp = *h->fineM;
   sp.in = L0.uC[L0.cur];
   sp.out = L0.uC[1 - L0.cur] + h->nx;
@@ -347,6 +604,16 @@ static int l0_cf(mgrit_handle* h) {
 
 static int l0_fres(mgrit_handle* h) {
   LevelData& L0 = h->lev[0];
+  if (h->sdirk) {
+    int rc = sdirk_launch(h, kModeFRES, 0, L0.uC[L0.cur], h->lev[1].g, L0.uC[L0.cur], h->m, L0.K, nullptr, 0, 0);
+    if (rc) return rc;
+    {
+      ProfScope ps(h, 2, 0.0);
+      launch_reduce_sum(h->partials, L0.K * h->sd0->csize, h->dnorm, h->st);
+    }
+    ++h->launches;
+    return check_launch();
+  }
   StencilParams<double>& sp = *h->fineM;
   sp.in = L0.uC[L0.cur];
   sp.sub = L0.uC[L0.cur] + h->nx;
@@ -384,7 +651,9 @@ static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const
   cp.partial = (mode == kModeFRES) ? h->partials : nullptr;
   const int H = cp.p1 / 2;
   double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
-  ProfScope ps(h, 1, 2.0 * (double)h->nx * steps * (double)(cp.p1 + 2 * H));
+  const double fl = 2.0 * (double)h->nx * steps * (double)(cp.p1 + 2 * H);
+  ProfScope ps(h, 1, fl);
+  ProfScope psl(h, 4 + std::min(l, kProfCats - 5), fl);
   if (launch_coarse(cp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   ++h->launches;
   return check_launch();
@@ -449,6 +718,184 @@ static int level0_relax_residual(mgrit_handle* h, double* norm) {
   return MGRIT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// MIXED precision: FP32 inner cycles on the error equation
+//   e_{km} = Phi^m e_{(k-1)m} + r_k  (level 0, RHS r at C-points only)
+// with FP32 relaxation sweeps, FP64 correction solves on ill-conditioned
+// levels, and the coarsest level solved sequentially in FP64.
+// ---------------------------------------------------------------------------
+static int l0f_cf(mgrit_handle* h, bool zero_start) {
+  LevelData& L0 = h->lev[0];
+  const size_t row = sizeof(float) * (size_t)h->nx;
+  float* dst = L0.uCf[1 - L0.curf];
+  if (zero_start) {
+    // Phi^m 0 + r = r
+    CUDA_TRY(cudaMemcpyAsync(dst, L0.gf, row * (L0.K + 1), cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(cudaMemsetAsync(dst, 0, row, h->st));
+    L0.curf = 1 - L0.curf;
+    return MGRIT_OK;
+  }
+  if (h->sdirk) {
+    SdirkParams<float> sp = *h->sd0f;
+    sp.mode = kModeCF;
+    sp.zero_start = 0;
+    sp.start = L0.uCf[L0.curf];
+    sp.out = dst;
+    sp.rhs = L0.gf;
+    sp.sub = nullptr;
+    sp.partial = nullptr;
+    sp.nsteps = h->m;
+    sp.K = L0.K;
+    sp.traj = nullptr;
+    ProfScope ps(h, 0, 0.0);
+    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  } else {
+    StencilParams<float>& sp = *h->fineMf;
+    sp.in = L0.uCf[L0.curf];
+    sp.out = dst + h->nx;
+    sp.rhs = L0.gf + h->nx;
+    sp.sub = nullptr;
+    sp.partial = nullptr;
+    sp.rows = L0.K;
+    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    launch_stencil_rows(sp, h->st);
+  }
+  ++h->launches;
+  L0.curf = 1 - L0.curf;
+  return check_launch();
+}
+
+// rho_{k+1} = Phi^m e_k + r_{k+1} - e_{k+1}  ->  level-1 RHS (FP32)
+static int l0f_fres(mgrit_handle* h, bool zero_guess) {
+  LevelData& L0 = h->lev[0];
+  float* g1 = h->lev[1].gf;
+  const size_t row = sizeof(float) * (size_t)h->nx;
+  if (zero_guess) {  // e = 0: rho = r, and the coarse correction starts from e = 0
+    CUDA_TRY(cudaMemcpyAsync(g1, L0.gf, row * (L0.K + 1), cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(cudaMemsetAsync(L0.uCf[L0.curf], 0, row * (L0.K + 1), h->st));
+    return MGRIT_OK;
+  }
+  if (h->sdirk) {
+    SdirkParams<float> sp = *h->sd0f;
+    sp.mode = kModeFRES;
+    sp.zero_start = 0;
+    sp.start = L0.uCf[L0.curf];
+    sp.out = g1;
+    sp.rhs = L0.gf;
+    sp.sub = L0.uCf[L0.curf];
+    sp.partial = h->partials;
+    sp.nsteps = h->m;
+    sp.K = L0.K;
+    sp.traj = nullptr;
+    ProfScope ps(h, 0, 0.0);
+    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  } else {
+    StencilParams<float>& sp = *h->fineMf;
+    sp.in = L0.uCf[L0.curf];
+    sp.out = g1 + h->nx;
+    sp.rhs = L0.gf + h->nx;
+    sp.sub = L0.uCf[L0.curf] + h->nx;
+    sp.partial = h->partials;
+    sp.rows = L0.K;
+    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    launch_stencil_rows(sp, h->st);
+  }
+  ++h->launches;
+  return check_launch();
+}
+
+static int coarse_launch_f(mgrit_handle* h, int l, int mode, int zero_start, const float* start, float* out,
+                           const float* sub, float* parent, int nsteps, int64_t K, const float* g) {
+  LevelData& Lv = h->lev[l];
+  auto fill = [&](auto& cp) {
+    cp.mode = mode;
+    cp.zero_start = zero_start;
+    cp.start = start;
+    cp.out = out;
+    cp.sub = sub;
+    cp.parent = parent;
+    cp.nsteps = nsteps;
+    cp.K = K;
+    cp.g = g;
+    cp.partial = nullptr;
+  };
+  const int H = Lv.cp.p1 / 2;
+  double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
+  const double fl = 2.0 * (double)h->nx * steps * (double)(Lv.cp.p1 + 2 * H);
+  ProfScope ps(h, 1, fl);
+  ProfScope psl(h, 4 + std::min(l, kProfCats - 5), fl);
+  int r;
+  if (Lv.solve64) {
+    CoarseParams<float, double> cp = Lv.cpfd;
+    fill(cp);
+    r = launch_coarse(cp, h->st);
+  } else {
+    CoarseParams<float, float> cp = Lv.cpf;
+    fill(cp);
+    r = launch_coarse(cp, h->st);
+  }
+  if (r < 0) return MGRIT_ERR_UNSUPPORTED;
+  ++h->launches;
+  return check_launch();
+}
+
+static int coarse_correct_f(mgrit_handle* h, int l) {
+  LevelData& Lv = h->lev[l];
+  LevelData& Par = h->lev[l - 1];
+  float* parent = Par.uCf[Par.curf];
+  int rc;
+  const size_t rowd = sizeof(double) * (size_t)h->nx;
+  if (l == h->L - 1) {
+    // coarsest level in FP64: g (FP32) -> FP64, sequential solve into a
+    // zeroed FP64 buffer, then added to the FP32 parent
+    launch_convert(kCvtF2D, Lv.g, Lv.gf, (Lv.N + 1) * h->nx, h->st);
+    CUDA_TRY(cudaMemsetAsync(h->seq_tmp, 0, rowd * (Lv.N + 1), h->st));
+    rc = coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, h->seq_tmp, (int)Lv.N, 1, Lv.g);
+    if (rc) return rc;
+    launch_convert(kAddD2F, h->seq_tmp + h->nx, parent + h->nx, Lv.N * h->nx, h->st);
+    h->launches += 2;
+    return check_launch();
+  }
+  const int nu = h->prm.nu;
+  const size_t rowf = sizeof(float) * (size_t)h->nx;
+  if (nu == 0) {
+    CUDA_TRY(cudaMemsetAsync(Lv.uCf[Lv.curf], 0, rowf * (Lv.K + 1), h->st));
+    rc = coarse_launch_f(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].gf, nullptr, nullptr, h->m, Lv.K, Lv.gf);
+  } else {
+    for (int s = 0; s < nu; ++s) {
+      bool zs = s == 0;
+      rc = coarse_launch_f(h, l, kModeCF, zs ? 1 : 0, zs ? nullptr : Lv.uCf[Lv.curf], Lv.uCf[1 - Lv.curf],
+                           nullptr, nullptr, h->m, Lv.K, Lv.gf);
+      if (rc) return rc;
+      Lv.curf = 1 - Lv.curf;
+    }
+    rc = coarse_launch_f(h, l, kModeFRES, 0, Lv.uCf[Lv.curf], h->lev[l + 1].gf, Lv.uCf[Lv.curf], nullptr, h->m,
+                         Lv.K, Lv.gf);
+  }
+  if (rc) return rc;
+  rc = coarse_correct_f(h, l + 1);
+  if (rc) return rc;
+  return coarse_launch_f(h, l, kModeFOUT, 0, Lv.uCf[Lv.curf], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.gf);
+}
+
+// One FP32 inner cycle for the level-0 error equation with RHS lev[0].gf.
+static int inner_cycle(mgrit_handle* h, bool zero_guess) {
+  const int nu = h->prm.nu;
+  int rc;
+  if (zero_guess && nu == 0) {
+    rc = l0f_fres(h, true);
+  } else {
+    for (int s = 0; s < nu; ++s) {
+      rc = l0f_cf(h, zero_guess && s == 0);
+      if (rc) return rc;
+    }
+    rc = l0f_fres(h, false);
+  }
+  if (rc) return rc;
+  return coarse_correct_f(h, 1);
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -502,12 +949,24 @@ int mgrit_destroy(mgrit_handle* h) {
     cudaFree(Lv.Mt_dev[0]);
     cudaFree(Lv.Mt_dev[1]);
   }
-  for (int c = 0; c < 4; ++c)
+  for (int c = 0; c < kProfCats; ++c)
     for (auto& pr : h->prof.ev[c]) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
     }
   for (auto e : h->prof.pool) cudaEventDestroy(e);
+  cudaFree(h->sd_Mt[0]);
+  cudaFree(h->sd_Mt[1]);
+  cudaFree(h->sdf_Mt[0]);
+  cudaFree(h->sdf_Mt[1]);
+  cudaFree(h->seq_tmp);
+  for (auto& Lv : h->lev) {
+    cudaFree(Lv.uCf[0]);
+    cudaFree(Lv.uCf[1]);
+    cudaFree(Lv.gf);
+    cudaFree(Lv.Mtf_dev[0]);
+    cudaFree(Lv.Mtf_dev[1]);
+  }
   cudaFree(h->partials);
   cudaFree(h->dnorm);
   cudaFree(h->du0);
@@ -531,7 +990,10 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.rk_kind == MGRIT_ERK && P.rk_order_q != P.order_p) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
   if (P.precision != MGRIT_FP64 && P.precision != MGRIT_MIXED) return MGRIT_ERR_INVALID_ARG;
-  if (P.rk_kind == MGRIT_SDIRK || P.precision == MGRIT_MIXED) return MGRIT_ERR_UNSUPPORTED;
+  // SDIRKq with q != p adds a phi_q D^{(q+1)}_2 correction term: q must be
+  // odd (a symmetric even-order difference) and q <= p (inside the SL band)
+  if (P.rk_kind == MGRIT_SDIRK && (P.rk_order_q > P.order_p || P.rk_order_q % 2 == 0))
+    return MGRIT_ERR_UNSUPPORTED;
   if (P.nt % P.m) return MGRIT_ERR_INVALID_ARG;
   int L = P.levels;
   if (L == 0) {  // coarsen until fewer than two time points would result
@@ -576,15 +1038,27 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     N /= P.m;
   }
   // level-0 operators
-  Stencil step = erk_step_stencil(P.order_p, P.rk_order_q, P.cfl);
+  int rc = MGRIT_OK;
   h->fine1.reset(new StencilParams<double>());
   h->fineM.reset(new StencilParams<double>());
-  int rc = set_stencil(h->fine1.get(), step, P.nx);
-  if (rc) return rc;
-  Stencil stepM = stencil_power(step, P.m);
-  h->fineM_taps_raw = stepM.width();
-  rc = set_stencil(h->fineM.get(), stepM, P.nx);
-  if (rc) return rc;
+  if (P.rk_kind == MGRIT_ERK) {
+    Stencil step = erk_step_stencil(P.order_p, P.rk_order_q, P.cfl);
+    rc = set_stencil(h->fine1.get(), step, P.nx);
+    if (rc) return rc;
+    Stencil stepM = stencil_power(step, P.m);
+    h->fineM_taps_raw = stepM.width();
+    rc = set_stencil(h->fineM.get(), stepM, P.nx);
+    if (rc) return rc;
+    if (P.precision == MGRIT_MIXED) {
+      h->fineMf.reset(new StencilParams<float>());
+      rc = set_stencil(h->fineMf.get(), stepM, P.nx);
+      if (rc) return rc;
+    }
+  } else {
+    std::string why0;
+    rc = build_sdirk(h.get(), &why0);
+    if (rc) return rc;
+  }
   // coarse operators
   std::vector<double> php, phq, es;
   std::vector<long long> ks;
@@ -616,7 +1090,28 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
       CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
     }
   }
-  h->npart = h->lev[0].K * stencil_tiles(P.nx) + 1;
+  if (P.precision == MGRIT_MIXED) {
+    h->mixed = true;
+    const size_t rowf = sizeof(float) * (size_t)P.nx;
+    auto allocf = [&](float** p, size_t bytes) -> int {
+      if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return MGRIT_ERR_OOM;
+      }
+      return cudaMemsetAsync(*p, 0, bytes, h->st) == cudaSuccess ? MGRIT_OK : MGRIT_ERR_CUDA;
+    };
+    for (int l = 0; l < L; ++l) {
+      LevelData& Lv = h->lev[l];
+      if (l < L - 1) {
+        for (int b = 0; b < 2; ++b)
+          if ((rc = allocf(&Lv.uCf[b], rowf * (Lv.K + 1)))) return rc;
+      }
+      int64_t grow = (l == 0) ? Lv.K + 1 : Lv.N + 1;
+      if ((rc = allocf(&Lv.gf, rowf * grow))) return rc;
+    }
+    if ((rc = alloc(&h->seq_tmp, row * (h->lev[L - 1].N + 1)))) return rc;
+  }
+  h->npart = h->lev[0].K * std::max<int64_t>(stencil_tiles(P.nx), h->sdirk ? h->sd0->csize : 1) + 1;
   for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * h->lev[l].cp.csize);
   if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
   if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
@@ -694,6 +1189,7 @@ int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
 int mgrit_coarse_apply(mgrit_handle* h, int level, const double* d_in, double* d_out, int64_t nvec) {
   if (!h || level < 0 || level >= h->L || !d_in || !d_out || nvec < 0) return MGRIT_ERR_INVALID_ARG;
   if (nvec == 0) return MGRIT_OK;
+  if (level == 0 && h->sdirk) return sdirk_launch(h, kModeAPPLY, 0, d_in, d_out, nullptr, 1, nvec, nullptr, 0, 0);
   if (level == 0) {
     StencilParams<double>& sp = *h->fine1;
     sp.in = d_in;
@@ -736,7 +1232,51 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
   double nrm = 0.0;
   int it = 0;
   int status = MGRIT_OK;
-  while (true) {
+  if (h->mixed) {
+    // FP64 iterative refinement around FP32 inner cycles: the first residual
+    // follows the FP64 pre-relaxation; every later one is the FP64 C-point
+    // residual of the corrected iterate (F-relaxation implied).
+    LevelData& L0 = h->lev[0];
+    const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
+    rc = level0_relax_residual(h, &nrm);
+    if (rc) return rc;
+    while (true) {
+      if (st.history_len < MGRIT_MAX_HISTORY) st.rnorm_history[st.history_len++] = nrm;
+      if (it == 0) st.rnorm0 = nrm;
+      st.rnorm = nrm;
+      if (!std::isfinite(nrm) || (it > 0 && nrm > 1e3 * st.rnorm0)) {
+        status = MGRIT_ERR_DIVERGED;
+        break;
+      }
+      if (nrm <= h->prm.tol * st.rnorm0) {
+        st.converged = 1;
+        break;
+      }
+      if (it >= h->prm.max_iter) {
+        status = MGRIT_ERR_NOT_CONVERGED;
+        break;
+      }
+      // r (FP64, rows 0..K of the level-1 RHS) -> FP32 RHS of the inner solve
+      launch_convert(kCvtD2F, h->lev[1].g, L0.gf, (L0.K + 1) * h->nx, h->st);
+      ++h->launches;
+      for (int j = 0; j < inner; ++j) {
+        rc = inner_cycle(h, j == 0);
+        if (rc) return rc;
+        ++st.inner_cycles;
+      }
+      // u += e at the C-points k = 1..K (FP64 master iterate)
+      launch_convert(kAddF2D, L0.uC[L0.cur] + h->nx, L0.uCf[L0.curf] + h->nx, L0.K * h->nx, h->st);
+      ++h->launches;
+      rc = l0_fres(h);
+      if (rc) return rc;
+      CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CUDA_TRY(cudaStreamSynchronize(h->st));
+      nrm = std::sqrt(std::max(0.0, *h->hnorm));
+      ++it;
+      ++st.outer_iterations;
+    }
+  }
+  while (!h->mixed) {
     rc = level0_relax_residual(h, &nrm);
     if (rc) return rc;
     if (st.history_len < MGRIT_MAX_HISTORY) st.rnorm_history[st.history_len++] = nrm;
@@ -806,8 +1346,21 @@ int mgrit_level_io(mgrit_handle* h, int level, int field, double* ptr, int to_de
 int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps, int64_t every,
                          double* traj) {
   if (!h || !u0 || !u_out || nsteps < 0 || every < 0) return MGRIT_ERR_INVALID_ARG;
-  if (h->prm.rk_kind != MGRIT_ERK) return MGRIT_ERR_UNSUPPORTED;
   const int64_t nx = h->nx;
+  if (h->sdirk) {
+    const size_t row = sizeof(double) * (size_t)nx;
+    int rc = copy_any(h->du0, u0, row, h->st);
+    if (rc) return rc;
+    bool out_dev = is_device_ptr(u_out);
+    double* dout = out_dev ? u_out : h->lev[0].uC[1 - h->lev[0].cur];
+    if (nsteps > INT32_MAX) return MGRIT_ERR_INVALID_ARG;
+    rc = sdirk_launch(h, kModeSEQ, 0, h->du0, dout, nullptr, (int)nsteps, 1, every > 0 ? traj : nullptr,
+                      (int)every, 3);
+    if (rc) return rc;
+    if (!out_dev && (rc = copy_any(u_out, dout, row, h->st))) return rc;
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    return MGRIT_OK;
+  }
   Stencil step = erk_step_stencil(h->prm.order_p, h->prm.rk_order_q, h->prm.cfl);
   // cluster size: power of two <= 16 dividing nx with >= 256 points per CTA
   int C = 1;
@@ -898,7 +1451,7 @@ int64_t mgrit_launch_count(const mgrit_handle* h) { return h ? h->launches : 0; 
 int mgrit_profile(mgrit_handle* h, int enable) {
   if (!h) return MGRIT_ERR_INVALID_ARG;
   CUDA_TRY(cudaStreamSynchronize(h->st));
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kProfCats; ++c) {
     for (auto& pr : h->prof.ev[c]) {
       h->prof.pool.push_back(pr.first);
       h->prof.pool.push_back(pr.second);
@@ -911,10 +1464,10 @@ int mgrit_profile(mgrit_handle* h, int enable) {
   return MGRIT_OK;
 }
 
-int mgrit_profile_read(mgrit_handle* h, double out[12]) {
+int mgrit_profile_read(mgrit_handle* h, double out[60]) {
   if (!h || !out) return MGRIT_ERR_INVALID_ARG;
   CUDA_TRY(cudaStreamSynchronize(h->st));
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < kProfCats; ++c) {
     double ms = 0.0;
     for (auto& pr : h->prof.ev[c]) {
       float t = 0.f;

@@ -61,8 +61,11 @@ struct SolveDir {
 // then the factored periodic solve (causal then anticausal recurrences).
 enum CoarseMode { kModeCF = 0, kModeFRES = 1, kModeFOUT = 2, kModeSEQ = 3, kModeAPPLY = 4 };
 
-template <typename T>
+// TS: storage / SL-gather precision; TC: precision of the banded correction
+// solve (and of its tables).
+template <typename TS, typename TC = TS>
 struct CoarseParams {
+  typedef TS T;
   int n, P, nthr;
   int csize;           // CTAs per vector (thread-block cluster size)
   int npc;             // points per CTA = nthr * P
@@ -71,7 +74,7 @@ struct CoarseParams {
   int kshift;          // SL shift k_l mod n
   int shift;           // y_i = v_{i+shift}
   T w[8];
-  SolveDir<T> c, a;
+  SolveDir<TC> c, a;
   int mode;
   int zero_start;
   int nsteps;
@@ -86,13 +89,57 @@ struct CoarseParams {
 };
 
 size_t coarse_smem_bytes(int npc, int P, int nthr, int elem);
+
+// ---------------------------------------------------------------------------
+// Level-0 SDIRK step kernel: m (or nsteps) steps of Phi = R_q(-c L_p) for an
+// SDIRK method, one CF-interval per thread-block cluster.  A step is a small
+// program over shared-memory vector slots (slot 0 holds the state):
+//   COPY  dst = src          ZERO  dst = 0          AXPY  dst += c src
+//   AXPYL dst += c L_p src   SOLVE dst = (I + gamma c L_p)^{-1} src
+// built on the host from the tableau (stiffly accurate stages) or from the
+// factored stability function (SDIRK5).
+// ---------------------------------------------------------------------------
+enum SdirkOpKind { kOpCopy = 0, kOpZero = 1, kOpAxpy = 2, kOpAxpyL = 3, kOpSolve = 4 };
+constexpr int kSdirkMaxOps = 40;
+constexpr int kSdirkMaxSlots = 5;
+
+template <typename T>
+struct SdirkParams {
+  int n, P, nthr, csize, npc;
+  int p1, llo;         // L_p taps at offsets llo .. llo + p1 - 1
+  T ltaps[8];
+  SolveDir<T> c, a;    // factored stage matrix (I + gamma c L_p)
+  T sscale;            // 1/kappa of the factorisation (applied before a solve)
+  int nops, nslots, result;
+  int opk[kSdirkMaxOps], opd[kSdirkMaxOps], ops[kSdirkMaxOps];
+  T opc[kSdirkMaxOps];
+  int mode;            // kModeCF, kModeFRES, kModeAPPLY, kModeSEQ
+  int zero_start, nsteps;
+  int64_t K;
+  const T* start;      // rows k
+  const T* rhs;        // optional C-point RHS, rows k+1 (CF / FRES)
+  T* out;              // CF / FRES: rows k+1; APPLY: rows k; SEQ: row 0
+  const T* sub;        // FRES: rows k+1
+  double* partial;     // FRES: one slot per CTA
+  T* traj;             // SEQ: state after every `every` steps, rows 0, 1, ...
+  int every;
+};
+size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem);
+int launch_sdirk(const SdirkParams<double>& p, cudaStream_t st);
+int launch_sdirk(const SdirkParams<float>& p, cudaStream_t st);
 int launch_coarse(const CoarseParams<double>& p, cudaStream_t st);
 int launch_coarse(const CoarseParams<float>& p, cudaStream_t st);
+int launch_coarse(const CoarseParams<float, double>& p, cudaStream_t st);
 int coarse_max_cluster(int want, size_t smem, int nthr);
 
 // ---------------------------------------------------------------------------
 // Utilities
 // ---------------------------------------------------------------------------
+// elementwise precision conversions over n values:
+//   kCvtD2F: f[i] = (float) d[i]     kCvtF2D: d[i] = f[i]
+//   kAddF2D: d[i] += f[i]            kAddD2F: f[i] += (float) d[i]
+enum CvtOp { kCvtD2F = 0, kCvtF2D = 1, kAddF2D = 2, kAddD2F = 3 };
+void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st);
 // sum of partial[0..n) in a fixed order, written to out[0] (FP64)
 void launch_reduce_sum(const double* partial, int64_t n, double* out, cudaStream_t st);
 // C-point iterate: row 0 = u0, rows k >= 1 uniform [0,1) at time index k*m

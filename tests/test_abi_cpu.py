@@ -64,6 +64,14 @@ def test_invalid_parameters_rejected_on_host(lib, kw):
     assert not h.value
 
 
+@pytest.mark.parametrize("q", [2, 4, 5])
+def test_sdirk_q_outside_the_correction_band_unsupported(lib, q):
+    """SDIRKq with q != p needs an odd q <= p (the phi_q D^{(q+1)} term)."""
+    prm = pkg.make_params(64, 128, 2.0, 3, kind=pkg.SDIRK, q=q)
+    h = ctypes.c_void_p()
+    assert lib.mgrit_setup(ctypes.byref(prm), None, ctypes.byref(h)) == -8
+
+
 def test_binding_refuses_wrong_dtypes():
     import numpy as np
     with pytest.raises(ValueError):

@@ -1,0 +1,63 @@
+"""MIXED precision (FP32 inner cycles inside FP64 iterative refinement): the
+converged solution must match the FP64 oracle's sequential time-stepping as
+closely as the FP64 solver does (the outer residual is FP64, so the FP32
+sweeps limit only the rate, not the accuracy)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2209_06916_gb300 as pkg
+from oracle import mgrit as omg
+from oracle import operators as oops
+from workloads import ic_fourier, ic_sin4, ic_sin4_noise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _seq(p, kind, q, c, u0, nt, m):
+    g = np.zeros((nt + 1, u0.shape[0]))
+    g[0] = u0
+    return omg.sequential(oops.FineOperator(p, kind, q, c), g)[::m]
+
+
+CASES = [  # kind, p, q, c, m, levels, nx, nt, inner
+    ("erk", 3, 3, 0.85, 8, 4, 512, 8 ** 3 * 2, 2),
+    ("erk", 1, 1, 0.85, 4, 2, 256, 1024, 1),
+    ("erk", 5, 5, 0.9, 4, 3, 256, 16 * 6, 3),
+    ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2, 2),
+    ("sdirk", 3, 3, 5.0, 4, 3, 256, 16 * 8, 2),
+]
+
+
+@pytest.mark.parametrize("kind,p,q,c,m,levels,nx,nt,inner", CASES)
+def test_mixed_solve_reaches_fp64_accuracy(kind, p, q, c, m, levels, nx, nt, inner):
+    u0 = ic_sin4_noise(nx, seed=1) if p < 5 else ic_fourier(nx, seed=1)
+    k = pkg.ERK if kind == "erk" else pkg.SDIRK
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for prec in (pkg.FP64, pkg.MIXED):
+        prm = pkg.make_params(nx, nt, c, p, kind=k, q=q, m=m, levels=levels, tol=1e-10, max_iter=40,
+                              precision=prec, seed=3, inner_cycles=inner)
+        s = pkg.Solver(prm, stream=stream)
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        st = s.solve(torch.tensor(u0, device="cuda"), out)
+        torch.cuda.synchronize()
+        res[prec] = (out.cpu().numpy(), st)
+        s.close()
+    seq = _seq(p, kind, q, c, u0, nt, m)
+    scale = np.max(np.abs(seq))
+    e64 = np.max(np.abs(res[pkg.FP64][0] - seq)) / scale
+    emx = np.max(np.abs(res[pkg.MIXED][0] - seq)) / scale
+    st = res[pkg.MIXED][1]
+    assert st["converged"] and st["inner_cycles"] >= st["outer_iterations"] * inner
+    # same accuracy class as FP64: within 10x of the FP64 solver's error and
+    # below the 1e-8 bound used for FP64 solves
+    assert emx < max(10 * e64, 1e-9) and emx < 1e-8, (e64, emx)
