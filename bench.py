@@ -26,8 +26,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="advection1d_erk3u3_vcycle_fp64", nx=4096, nt=16384, p=3, cfl=0.85, m=8,
-                levels=4, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4+N(0,1e-2)")
+WORKLOADS = {
+    # the headline: 4096 x 16384, ERK3+U3, FP64, 4-level V-cycle (m = 8)
+    "c2": dict(name="advection1d_erk3u3_vcycle_fp64", nx=4096, nt=16384, p=3, kind="erk", q=3, cfl=0.85,
+               m=8, levels=4, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4_noise", precision="fp64"),
+    # 256 x 1024, ERK1+U1, FP64, two-level m = 4
+    "c1": dict(name="advection1d_erk1u1_twolevel_fp64", nx=256, nt=1024, p=1, kind="erk", q=1, cfl=0.85,
+               m=4, levels=2, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4", precision="fp64"),
+    # 16384 x 65536, U5 + SDIRK3 (c = 4), FP32 relaxation in FP64 refinement, m = 16, 5 levels
+    "c3": dict(name="advection1d_sdirk3u5_vcycle_mixed", nx=16384, nt=65536, p=5, kind="sdirk", q=3,
+               cfl=4.0, m=16, levels=5, nu=1, tol=1e-10, max_iter=30, seed=0, ic="fourier20",
+               precision="mixed"),
+}
+WORKLOAD = WORKLOADS["c2"]
 METRIC = "space-time DOF/s to 1e-10 residual vs GPU seq. stepping; p50/p99 latency"
 UNIT = "DOF/s"
 # FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM (4 flop/clk/SM) x 2.07 GHz
@@ -83,21 +94,102 @@ def clocks_sampler_stop(p, f, path, device):
             "samples": len(sm)}
 
 
+def make_ic(w):
+    from workloads import ic_fourier, ic_sin4, ic_sin4_noise
+    if w["ic"] == "sin4_noise":
+        return ic_sin4_noise(w["nx"], seed=w["seed"])
+    if w["ic"] == "fourier20":
+        return ic_fourier(w["nx"], seed=w["seed"])
+    return ic_sin4(w["nx"])
+
+
 def cpu_baseline(sample_nt=2048):
     """The CPU oracle (plain numpy FP64 V-cycle MGRIT, as it stands) on a
     bounded sample of the workload: the same nx, scheme, m, levels and
     tolerance over the first sample_nt steps."""
     from oracle import mgrit as omg
-    from workloads import ic_sin4_noise
     w = WORKLOAD
-    h = omg.Hierarchy(w["p"], "erk", w["p"], w["cfl"], w["m"], w["levels"])
-    u0 = ic_sin4_noise(w["nx"], seed=w["seed"])
+    sample_nt = min(sample_nt, w["nt"])
+    levels = w["levels"]
+    while sample_nt % (w["m"] ** (levels - 1)):
+        levels -= 1
+    h = omg.Hierarchy(w["p"], w["kind"], w["q"], w["cfl"], w["m"], levels)
+    u0 = make_ic(w)
     t = time.perf_counter()
     r = omg.solve(h, u0, sample_nt, nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"])
     dt = time.perf_counter() - t
     return {"value": w["nx"] * sample_nt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "nx=%d, nt=%d (first %d of %d steps), same scheme/m/levels/tol, %d iterations, %.1f s"
-                      % (w["nx"], sample_nt, sample_nt, w["nt"], r["iterations"], dt)}
+            "sample": "nx=%d, nt=%d (first %d of %d steps), same scheme/m/tol, %d levels, %d iterations, %.1f s"
+                      % (w["nx"], sample_nt, sample_nt, w["nt"], levels, r["iterations"], dt)}
+
+
+def run_batched(args):
+    """512 independent solves (nx, nt, p, c, m mixed), FP32 relaxation in FP64
+    refinement, all launched together; value = total DOF / batch time."""
+    import torch
+    import paper_2209_06916_gb300 as pkg
+    from workloads import batch_mix, ic_sin4_noise
+    torch.cuda.set_device(0)
+    mix = batch_mix(args.count, seed=1000)
+    prms = [pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=1e-10,
+                            max_iter=60, precision=pkg.MIXED, seed=d["seed"]) for d in mix]
+    u0s = [torch.tensor(ic_sin4_noise(d["nx"], seed=d["seed"]), dtype=torch.float64, device="cuda") for d in mix]
+    b = pkg.Batch(prms, nstreams=32)
+    dof = b.dof()
+    for _ in range(args.warmup):
+        b.solve(u0s, allow_unconverged=True)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = b.solve(u0s, allow_unconverged=True)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    dt = float(np.median(ts))
+    its = [x["iterations"] for x in st]
+    conv = sum(1 for x in st if x["converged"])
+    b.close()
+    line = {"metric": METRIC, "value": dof / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
+            "config": {"workload": "advection1d_batched_%d_erk_mixed" % args.count, "solves": args.count,
+                       "dof_total": dof, "converged": conv, "iterations_median": float(np.median(its)),
+                       "iterations_max": int(max(its)), "nstreams": 32}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Poisson stream (2000 requests/s) of mixed solves through the native
+    continuous-batching server with an 80 GB HBM budget."""
+    import torch
+    import paper_2209_06916_gb300 as pkg
+    from workloads import ic_fourier, ic_sin4_noise, serving_stream
+    torch.cuda.set_device(0)
+    arrivals, reqs = serving_stream(rate=2000.0, duration=args.duration, seed=2000)
+    prms, u0s = [], []
+    for d in reqs:
+        kind = pkg.ERK if d["kind"] == "erk" else pkg.SDIRK
+        prms.append(pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=kind, q=d["q"], m=d["m"], levels=0,
+                                    nu=1, tol=1e-10, max_iter=60, precision=pkg.MIXED, seed=d["seed"]))
+        u0s.append(ic_sin4_noise(d["nx"], seed=d["seed"]) if d["kind"] == "erk" else ic_fourier(d["nx"], d["seed"]))
+    res, st = pkg.serve(prms, u0s, arrivals, 80 * 10 ** 9, max_inflight=args.inflight,
+                        time_limit_s=args.duration + args.drain)
+    lat = np.array([r["latency_ms"] for r in res if r["status"] == 0])
+    offered = float(sum(d["nx"] * d["nt"] for d in reqs))
+    line = {"metric": METRIC, "value": st["dof_completed"] / st["wall_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": st["wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
+            "config": {"workload": "advection1d_serving_poisson2000", "arrival_rate_per_s": 2000.0,
+                       "duration_s": args.duration, "requests": len(reqs), "offered_dof_per_s": offered / args.duration,
+                       "hbm_budget_gb": 80, "max_inflight": args.inflight},
+            "serving": {k: st[k] for k in ("arrived", "admitted", "completed", "failed", "rejected", "backlog_end",
+                                           "max_backlog", "max_mem_bytes", "max_inflight", "wall_s")},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
+                           "p99": float(np.percentile(lat, 99)) if lat.size else None,
+                           "completed": int(lat.size)}}
+    print(json.dumps(line))
+    return 0
 
 
 def run_reference(args):
@@ -130,7 +222,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5"])
+    ap.add_argument("--count", type=int, default=512, help="c4: number of solves")
+    ap.add_argument("--duration", type=float, default=5.0, help="c5: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=25.0, help="c5: extra seconds before the server stops")
+    ap.add_argument("--inflight", type=int, default=64, help="c5: concurrent solves")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision sub-measurement")
     args = ap.parse_args()
+    global WORKLOAD
+    if args.workload == "c4" and args.impl == "ours":
+        return run_batched(args)
+    if args.workload == "c5" and args.impl == "ours":
+        return run_serving(args)
+    WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c2"])
     if args.impl == "reference":
         return run_reference(args)
 
@@ -144,15 +248,20 @@ def main():
         dist.init_process_group("nccl")
 
     import paper_2209_06916_gb300 as pkg
-    from workloads import ic_sin4_noise
 
     w = WORKLOAD
     nx, nt, m = w["nx"], w["nt"], w["m"]
     stream = torch.cuda.current_stream()
-    prm = pkg.make_params(nx, nt, w["cfl"], w["p"], m=m, levels=w["levels"], nu=w["nu"], tol=w["tol"],
-                          max_iter=w["max_iter"], seed=w["seed"])
-    s = pkg.Solver(prm, stream=stream.cuda_stream)
-    u0_h = ic_sin4_noise(nx, seed=w["seed"])
+    kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
+    prec = pkg.FP64 if w["precision"] == "fp64" else pkg.MIXED
+
+    def make(precision):
+        prm = pkg.make_params(nx, nt, w["cfl"], w["p"], kind=kind, q=w["q"], m=m, levels=w["levels"], nu=w["nu"],
+                              tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=precision)
+        return pkg.Solver(prm, stream=stream.cuda_stream)
+
+    s = make(prec)
+    u0_h = make_ic(w)
     u0 = torch.tensor(u0_h, dtype=torch.float64, device="cuda")
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
 
@@ -220,6 +329,27 @@ def main():
     s.solve(u0, out)
     torch.cuda.synchronize()
     err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+    dof = nx * nt
+    variants = {}
+    if not args.no_variants and prec == pkg.FP64:
+        # the same workload with FP32 relaxation inside FP64 refinement
+        sm = make(pkg.MIXED)
+        outm = torch.empty_like(out)
+        for _ in range(max(1, args.warmup)):
+            stm = sm.solve(u0, outm)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            stm = sm.solve(u0, outm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1) / args.steps
+        errm = float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+        variants["mixed"] = {"value": dof / (mms / 1e3), "unit": UNIT, "ms": mms,
+                             "outer_iterations": stm["outer_iterations"], "inner_cycles": stm["inner_cycles"],
+                             "max_rel_err_vs_sequential": errm,
+                             "over_sequential": (dof / (mms / 1e3)) / (dof / (seq_ms / 1e3))}
+        sm.close()
     clocks = clocks_sampler_stop(cp, cf, clk_path, local)
     scnt, sms, sfl = sprof["sequential"]
 
@@ -228,7 +358,9 @@ def main():
     value = ws * dof * args.steps / (ms / 1e3)
     cnt, kms, kfl = prof["stencil0"]
     achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "stencil_rows_kernel<double,4> (level-0 composite Phi^m)",
+    kname = ("stencil_rows_kernel<double,4> (level-0 composite Phi^m)" if w["kind"] == "erk"
+             else "sdirk_kernel<double> (level-0 SDIRK stages: banded solves + L_p mat-vecs)")
+    roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
             "peak_source": "derived FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
@@ -236,8 +368,10 @@ def main():
             "share_of_step": kms / ms if ms > 0 else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "nx": nx, "nt": nt, "scheme": "ERK3+U3", "cfl": w["cfl"],
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == pkg.FP64 else "f32 relax / f64 residual", "data": "synthetic",
+            "config": {"workload": w["name"], "nx": nx, "nt": nt,
+                       "scheme": "%s%d+U%d" % (w["kind"].upper(), w["q"], w["p"]), "cfl": w["cfl"],
                        "m": m, "levels": w["levels"], "relax": "FCF", "tol": w["tol"],
                        "iterations": iters, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (
@@ -252,9 +386,10 @@ def main():
                            "frac": (sfl / (sms / 1e3)) / FP64_PEAK_FLOPS if sms > 0 else None},
             "mgrit_over_sequential": (dof / (ms / 1e3 / args.steps)) / (dof / (seq_ms / 1e3)),
             "max_rel_err_vs_sequential": err,
+            "variants": variants,
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(sample_nt=2048 if w["kind"] == "erk" else 256)
     if rank == 0:
         print(json.dumps(line))
     s.close()

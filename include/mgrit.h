@@ -120,6 +120,10 @@ int mgrit_destroy(mgrit_handle* h);
 /* Static text of an error code. */
 const char* mgrit_strerror(int code);
 
+/* Text of the last failing CUDA call of this host thread ("" if none); valid
+ * until the next failure on the same thread. */
+const char* mgrit_last_error(void);
+
 /*
  * mgrit_set_initial -- set the initial condition u0 (nx values, host or
  * device) and the initial C-point iterate of level 0.  init (host or device,
@@ -168,6 +172,25 @@ int mgrit_coarse_apply(mgrit_handle* h, int level, const double* d_in, double* d
  * Returns OK, NOT_CONVERGED or DIVERGED (u_out and stats are still written).
  */
 int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* stats);
+
+/*
+ * mgrit_solve_async -- the same solve as mgrit_solve, run as one CUDA graph
+ * launch without host round trips: the first pre-relaxation and residual,
+ * then a device-side loop (a conditional while node) whose body is one
+ * MGRIT iteration followed by the stop test (||r|| <= tol ||r_0||,
+ * max_iter, divergence) evaluated on the GPU.  The graph is built at the
+ * first call and reused.  u0 (host or device, nx; NULL keeps the current
+ * initial state) is copied and the random initial iterate generated on the
+ * handle's stream.  Returns immediately; at most one solve per handle is in
+ * flight.  Not thread safe.
+ * mgrit_solve_query -- MGRIT_OK when the solve finished, 1 while running.
+ * mgrit_solve_wait  -- wait, then copy the C-points to u_out (host or device,
+ * may be NULL) and fill stats (may be NULL); returns the solve's status (OK,
+ * NOT_CONVERGED, DIVERGED) like mgrit_solve.
+ */
+int mgrit_solve_async(mgrit_handle* h, const double* u0);
+int mgrit_solve_query(mgrit_handle* h);
+int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats);
 
 /*
  * mgrit_vcycle -- one MGRIT iteration without the stop test: coarse
@@ -220,8 +243,9 @@ int64_t mgrit_launch_count(const mgrit_handle* h);
  * out[3c+2] algorithmic flops (2 per multiply-add the kernel must do) for
  * category c = 0 level-0 composite stencil, 1 coarse step kernel (all
  * levels), 2 reductions, 3 sequential stepping, 4 + l coarse step kernel on
- * level l (l = 1..15, the last slot collects deeper levels); 20 categories,
- * out has 60 entries.  Synchronises the stream.
+ * level l (l = 1..14, the last of these slots collects deeper levels),
+ * 19 the FP32 level-0 kernels of MIXED inner cycles; 20 categories, out has
+ * 60 entries.  Synchronises the stream.
  */
 int mgrit_profile(mgrit_handle* h, int enable);
 int mgrit_profile_read(mgrit_handle* h, double out[60]);
@@ -258,6 +282,68 @@ int mgrit_profile_read(mgrit_handle* h, double out[60]);
  */
 int mgrit_residual_noalloc(const mgrit_params* params, const double* d_uC, int64_t rows, double* d_r,
                            double* norm_out, void* stream);
+
+/* ---- batched and served solves ----------------------------------------- */
+/*
+ * Many independent advection problems (the batched workload) run as
+ * graph-resident solves launched together over a pool of streams, so their
+ * kernels share the GPU and no solve waits on the host between iterations.
+ * The paper solves one problem at a time; batching is an interface layer.
+ */
+typedef struct mgrit_batch mgrit_batch;
+
+/* Device bytes mgrit_setup allocates for *p (admission estimate), or -1. */
+int64_t mgrit_estimate_bytes(const mgrit_params* p);
+
+/* count solves with per-solve parameters params[0..count) (host), on
+ * nstreams internal streams.  Allocates every hierarchy up front. */
+int mgrit_batch_create(const mgrit_params* params, int64_t count, int nstreams, mgrit_batch** out);
+/* Solve all: u0s[i] (host or device, params[i].nx values).  stats (host, count
+ * entries, may be NULL).  Returns OK, or the first NOT_CONVERGED / DIVERGED
+ * status among the solves (all solves still ran). */
+int mgrit_batch_solve(mgrit_batch* b, const double* const* u0s, mgrit_stats* stats);
+/* C-points of solve i ((nt/m + 1) * nx values, host or device). */
+int mgrit_batch_get(mgrit_batch* b, int64_t i, double* u_out);
+/* Sum of nx * nt over the batch. */
+int64_t mgrit_batch_dof(const mgrit_batch* b);
+int mgrit_batch_destroy(mgrit_batch* b);
+
+typedef struct mgrit_request_result {
+  double start_s;     /* admission time (s from the start of mgrit_serve)   */
+  double finish_s;    /* completion time                                   */
+  double latency_ms;  /* finish - arrival                                  */
+  int iterations;
+  int status;         /* MGRIT status; 1 = never admitted (time limit)     */
+} mgrit_request_result;
+
+typedef struct mgrit_serve_stats {
+  int64_t arrived, admitted, completed, failed, rejected;
+  int64_t backlog_end;   /* requests not admitted when the run ended         */
+  int64_t max_backlog;   /* largest queue of arrived, not admitted requests  */
+  int64_t max_mem_bytes; /* peak admitted device memory (estimate)           */
+  int max_inflight, pad;
+  double dof_completed;  /* sum of nx * nt over completed requests           */
+  double wall_s;
+} mgrit_serve_stats;
+
+/*
+ * mgrit_serve -- replay a stream of solve requests with continuous batching:
+ * request i (params[i], initial condition u0s[i] on the host) arrives at
+ * arrival_s[i] seconds (non-decreasing) after the call starts; arrived
+ * requests are admitted first come, first served while fewer than
+ * max_inflight solves run and the estimated device memory of the running
+ * solves stays within hbm_budget_bytes; each admitted request gets its own
+ * hierarchy (set up on admission, freed on completion) and runs as a
+ * graph-resident solve overlapping the others on the GPU.  Returns when all
+ * requests finished or after time_limit_s (running solves are drained,
+ * unadmitted ones keep status 1).  u_outs (may be NULL, as may each
+ * u_outs[i]) receives request i's C-points ((nt/m + 1) * nx values, host or
+ * device).  results (host, count entries) and st (host, may be NULL) are
+ * filled.
+ */
+int mgrit_serve(const mgrit_params* params, const double* const* u0s, double* const* u_outs,
+                const double* arrival_s, int64_t count, int64_t hbm_budget_bytes, int max_inflight,
+                double time_limit_s, mgrit_request_result* results, mgrit_serve_stats* st);
 
 #ifdef __cplusplus
 }

@@ -55,10 +55,26 @@ class Stats(ctypes.Structure):
         }
 
 
+class RequestResult(ctypes.Structure):
+    _fields_ = [("start_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("arrived", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("rejected", ctypes.c_int64), ("backlog_end", ctypes.c_int64),
+                ("max_backlog", ctypes.c_int64), ("max_mem_bytes", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int), ("pad", ctypes.c_int), ("dof_completed", ctypes.c_double),
+                ("wall_s", ctypes.c_double)]
+
+
 class MgritError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
-        super().__init__("%s: %s (%d)" % (what, ERRORS.get(code, "?"), code))
+        detail = ""
+        if code == -6 and _lib is not None:
+            detail = " [%s]" % _lib.mgrit_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%d)%s" % (what, ERRORS.get(code, "?"), code, detail))
 
 
 _lib = None
@@ -78,6 +94,8 @@ def load_library(path=LIB_PATH):
     lib.mgrit_destroy.argtypes = [P]
     lib.mgrit_strerror.argtypes = [ctypes.c_int]
     lib.mgrit_strerror.restype = ctypes.c_char_p
+    lib.mgrit_last_error.argtypes = []
+    lib.mgrit_last_error.restype = ctypes.c_char_p
     lib.mgrit_set_initial.argtypes = [P, P, P]
     lib.mgrit_relax.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.mgrit_residual.argtypes = [P, ctypes.c_int, dp]
@@ -90,6 +108,21 @@ def load_library(path=LIB_PATH):
     lib.mgrit_level_info.argtypes = [P, ctypes.c_int, dp]
     lib.mgrit_launch_count.argtypes = [P]
     lib.mgrit_launch_count.restype = ctypes.c_int64
+    lib.mgrit_estimate_bytes.argtypes = [ctypes.POINTER(Params)]
+    lib.mgrit_estimate_bytes.restype = ctypes.c_int64
+    lib.mgrit_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_int, ctypes.POINTER(P)]
+    lib.mgrit_batch_solve.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Stats)]
+    lib.mgrit_batch_get.argtypes = [P, ctypes.c_int64, P]
+    lib.mgrit_batch_dof.argtypes = [P]
+    lib.mgrit_batch_dof.restype = ctypes.c_int64
+    lib.mgrit_batch_destroy.argtypes = [P]
+    lib.mgrit_serve.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p),
+                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(RequestResult),
+                                ctypes.POINTER(ServeStats)]
+    lib.mgrit_solve_async.argtypes = [P, P]
+    lib.mgrit_solve_query.argtypes = [P]
+    lib.mgrit_solve_wait.argtypes = [P, P, ctypes.POINTER(Stats)]
     lib.mgrit_profile.argtypes = [P, ctypes.c_int]
     lib.mgrit_profile_read.argtypes = [P, dp]
     _lib = lib
@@ -176,6 +209,25 @@ class Solver:
         d["status"] = code
         return d
 
+    def solve_async(self, u0=None):
+        """Launch the graph-resident solve (returns at once)."""
+        _check(self.lib.mgrit_solve_async(self.h, _ptr(u0)), "mgrit_solve_async")
+
+    def done(self):
+        code = self.lib.mgrit_solve_query(self.h)
+        if code < 0:
+            raise MgritError(code, "mgrit_solve_query")
+        return code == 0
+
+    def wait(self, u_out=None, allow_unconverged=False):
+        st = Stats()
+        code = self.lib.mgrit_solve_wait(self.h, _ptr(u_out), ctypes.byref(st))
+        if code != MGRIT_OK and not (allow_unconverged and code in (-3, -4)):
+            raise MgritError(code, "mgrit_solve_wait")
+        d = st.to_dict()
+        d["status"] = code
+        return d
+
     def level_rows(self, level, field):
         """Rows of a level buffer: field 0 (C-point unknowns) N_l/m + 1,
         field 1 (RHS) N_l + 1."""
@@ -216,6 +268,81 @@ class Solver:
         'stencil0' (level-0 composite stencil), 'coarse', 'reduce'."""
         out = (ctypes.c_double * 60)()
         _check(self.lib.mgrit_profile_read(self.h, out), "mgrit_profile_read")
-        names = ["stencil0", "coarse", "reduce", "sequential"] + ["coarse_l%d" % l for l in range(16)]
+        names = ["stencil0", "coarse", "reduce", "sequential"] + ["coarse_l%d" % l for l in range(15)] + \
+            ["level0_fp32"]
         d = {n: (int(out[3 * i]), out[3 * i + 1], out[3 * i + 2]) for i, n in enumerate(names)}
         return {k: v for k, v in d.items() if not k.startswith("coarse_l") or v[0] > 0}
+
+
+def _ptr_array(arrs):
+    out = (ctypes.c_void_p * len(arrs))()
+    for i, a in enumerate(arrs):
+        out[i] = _ptr(a) if a is not None else None
+    return out
+
+
+class Batch:
+    """Independent solves launched together (graph-resident, stream pool)."""
+
+    def __init__(self, params, nstreams=16):
+        self.lib = load_library()
+        self.params = list(params)
+        arr = (Params * len(self.params))(*self.params)
+        b = ctypes.c_void_p()
+        _check(self.lib.mgrit_batch_create(arr, len(self.params), nstreams, ctypes.byref(b)), "mgrit_batch_create")
+        self.b = b
+
+    def solve(self, u0s, allow_unconverged=False):
+        """u0s: list of arrays (host numpy or device tensors).  Returns a list
+        of stats dicts."""
+        self._u0 = list(u0s)
+        ptrs = _ptr_array(self._u0)
+        stats = (Stats * len(self.params))()
+        code = self.lib.mgrit_batch_solve(self.b, ptrs, stats)
+        if code != MGRIT_OK and not (allow_unconverged and code in (-3, -4)):
+            raise MgritError(code, "mgrit_batch_solve")
+        return [s.to_dict() for s in stats]
+
+    def get(self, i):
+        p = self.params[i]
+        out = np.empty((p.nt // p.m + 1, p.nx), dtype=np.float64)
+        _check(self.lib.mgrit_batch_get(self.b, i, _ptr(out)), "mgrit_batch_get")
+        return out
+
+    def dof(self):
+        return int(self.lib.mgrit_batch_dof(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mgrit_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(params):
+    return int(load_library().mgrit_estimate_bytes(ctypes.byref(params)))
+
+
+def serve(params, u0s, arrivals, hbm_budget_bytes, max_inflight=32, time_limit_s=60.0, u_outs=None):
+    """Replay a request stream through the native continuous-batching server.
+    Returns (list of per-request result dicts, stats dict)."""
+    lib = load_library()
+    n = len(params)
+    parr = (Params * n)(*params)
+    u0p = _ptr_array(list(u0s))
+    outp = _ptr_array(list(u_outs)) if u_outs is not None else None
+    arr = (ctypes.c_double * n)(*[float(a) for a in arrivals])
+    res = (RequestResult * n)()
+    st = ServeStats()
+    code = lib.mgrit_serve(parr, u0p, outp, arr, n, int(hbm_budget_bytes), int(max_inflight), float(time_limit_s),
+                           res, ctypes.byref(st))
+    _check(code, "mgrit_serve")
+    results = [{"start_s": r.start_s, "finish_s": r.finish_s, "latency_ms": r.latency_ms,
+                "iterations": r.iterations, "status": r.status} for r in res]
+    stats = {f[0]: getattr(st, f[0]) for f in ServeStats._fields_ if f[0] != "pad"}
+    return results, stats

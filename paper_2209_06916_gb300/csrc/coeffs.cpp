@@ -561,6 +561,26 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
     ++d.jterms;
     mat3_mul(mcj, Mc, mcj);
   }
+  // warp-level tables: M^d (d <= 32) and powers of M^32 for the warp totals
+  {
+    double md[9];
+    for (int i = 0; i < 9; ++i) md[i] = M[i];
+    for (int dd = 1; dd <= 32; ++dd) {
+      d.Mlane.insert(d.Mlane.end(), md, md + 9);
+      mat3_mul(md, M, md);
+    }
+    double m32[9];
+    for (int i = 0; i < 9; ++i) m32[i] = d.Mlane[31 * 9 + i];
+    double pj[9];
+    for (int i = 0; i < 9; ++i) pj[i] = I3[i];
+    const int nw = (T + 31) / 32;
+    for (int j = 0; j < std::min(nw, 8); ++j) {
+      if (j > 0 && mat3_norm(pj) < 1e-18) break;
+      d.M32pow.insert(d.M32pow.end(), pj, pj + 9);
+      ++d.wterms;
+      mat3_mul(pj, m32, pj);
+    }
+  }
   if (d.jterms == C && mat3_norm(mcj) >= 1e-18) {
     // the sum wraps the ring: closure (I - Mc^C)^{-1}; mcj = Mc^C here
     double IM[9];

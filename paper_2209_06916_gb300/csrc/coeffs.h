@@ -87,6 +87,9 @@ struct DistScanTables {
   std::vector<double> McPow; // jterms * 9: (M^T)^j
   double Clc[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   int closure = 0;
+  std::vector<double> Mlane;   // 32 * 9: M^d, d = 1..32
+  std::vector<double> M32pow;  // wterms * 9: (M^32)^j
+  int wterms = 0;
 };
 DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C);
 

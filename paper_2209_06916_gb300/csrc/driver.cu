@@ -57,6 +57,7 @@ struct LevelData {
 // profiling categories: 0 level-0 stencil, 1 coarse kernel (all levels),
 // 2 reductions, 3 sequential stepping, 4 + l coarse kernel on level l
 constexpr int kProfCats = 20;
+constexpr int kProfL0F32 = 19;  // MIXED: level-0 FP32 inner-cycle kernels
 
 struct mgrit_handle {
   mgrit_params prm;
@@ -71,8 +72,20 @@ struct mgrit_handle {
   std::unique_ptr<StencilParams<float>> fineMf;  // MIXED: Phi^m in FP32 (ERK)
   std::unique_ptr<SdirkParams<float>> sd0f;      // MIXED: SDIRK programme in FP32
   float* sdf_Mt[2] = {nullptr, nullptr};
+  std::unique_ptr<SdirkParams<double>> sdseq;    // SDIRK sequential stepping (one vector)
+  double* sdseq_Mt[2] = {nullptr, nullptr};
   double* seq_tmp = nullptr;                     // MIXED: FP64 coarsest-level output
   bool mixed = false;
+  // graph-resident solve: prologue (first relaxation and residual) and a
+  // conditional while node whose body is one MGRIT iteration with the stop
+  // test on the device
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  DevSolveState* dstate = nullptr;
+  DevSolveState* hstate = nullptr;  // pinned
+  cudaEvent_t done = nullptr;
+  bool graph_pending = false;
+  int graph_cur = 0;  // level-0 C-point buffer holding the result of a graph solve
   double* sd_Mt[2] = {nullptr, nullptr};
   bool sdirk = false;
   int fineM_taps_raw = 0;
@@ -126,15 +139,27 @@ struct ProfScope {
   }
 };
 
-#define CUDA_TRY(expr)                           \
-  do {                                           \
-    cudaError_t e_ = (expr);                     \
-    if (e_ != cudaSuccess) return MGRIT_ERR_CUDA; \
+// Text of the last failing CUDA call on this host thread (mgrit_last_error).
+static thread_local char g_last_error[256] = "";
+
+static void note_cuda_error(const char* what, cudaError_t e) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                \
+  do {                                \
+    cudaError_t e_ = (expr);          \
+    if (e_ != cudaSuccess) {          \
+      note_cuda_error(#expr, e_);     \
+      return MGRIT_ERR_CUDA;          \
+    }                                 \
   } while (0)
 
 static int check_launch() {
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? MGRIT_OK : MGRIT_ERR_CUDA;
+  if (e == cudaSuccess) return MGRIT_OK;
+  note_cuda_error("kernel launch", e);
+  return MGRIT_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
@@ -208,6 +233,11 @@ static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int H
     for (int i = 0; i < 9; ++i) d->Mpow[r][i] = (T)tb.Mpow[r * 9 + i];
   for (int j = 0; j < d->jterms; ++j)
     for (int i = 0; i < 9; ++i) d->McPow[j][i] = (T)tb.McPow[j * 9 + i];
+  d->wterms = std::min(tb.wterms, 8);
+  for (int dd = 0; dd < 32; ++dd)
+    for (int i = 0; i < 9; ++i) d->Mlane[dd][i] = (T)tb.Mlane[dd * 9 + i];
+  for (int j = 0; j < d->wterms; ++j)
+    for (int i = 0; i < 9; ++i) d->M32pow[j][i] = (T)tb.M32pow[j * 9 + i];
   for (int i = 0; i < 9; ++i) d->Clc[i] = (T)tb.Clc[i];
   for (int j = 0; j < P && j < kPMax; ++j)
     for (int q = 0; q < 3; ++q) d->G[j * 3 + q] = (T)tb.G[(size_t)j * 3 + q];
@@ -452,11 +482,16 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
   return true;
 }
 
-static int build_sdirk(mgrit_handle* h, std::string* why) {
+// Build the SDIRK step parameters for K vectors per launch (K = number of
+// CF-intervals on level 0, or 1 for sequential stepping); the cluster size
+// follows from K and from the shared-memory need of the stage slots.
+static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
+                              double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
+                              std::string* why) {
   const mgrit_params& P = h->prm;
   const int p = P.order_p;
-  h->sd0.reset(new SdirkParams<double>());
-  SdirkParams<double>& sp = *h->sd0;
+  out->reset(new SdirkParams<double>());
+  SdirkParams<double>& sp = **out;
   std::memset((void*)&sp, 0, sizeof(sp));
   double gamma = 0.0;
   if (!sdirk_program(P.rk_order_q, P.cfl, &sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
@@ -476,7 +511,7 @@ static int build_sdirk(mgrit_handle* h, std::string* why) {
   // geometry: like a coarse level with K0 intervals, then more CTAs per
   // vector until the slots fit in shared memory
   int C, Pc, nthr;
-  if (!pick_coarse_geometry(h->nx, h->lev[0].K, &C, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
+  if (!pick_coarse_geometry(h->nx, K, &C, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
   while (sdirk_smem_bytes((int)(h->nx / C), Pc, nthr, sp.nslots, 8) > 227 * 1024) {
     if (C >= 16 || h->nx % (2 * C)) return MGRIT_ERR_UNSUPPORTED;
     C *= 2;
@@ -500,20 +535,14 @@ static int build_sdirk(mgrit_handle* h, std::string* why) {
   fill_solve_dir(&sp.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mta);
   for (int dd = 0; dd < 2; ++dd) {
     std::vector<double>& mt = dd ? mta : mtc;
-    if (cudaMalloc((void**)&h->sd_Mt[dd], sizeof(double) * std::max<size_t>(9, mt.size())) != cudaSuccess) {
-      cudaGetLastError();
-      return MGRIT_ERR_OOM;
-    }
-    if (!mt.empty() &&
-        cudaMemcpy(h->sd_Mt[dd], mt.data(), sizeof(double) * mt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-      return MGRIT_ERR_CUDA;
+    int rc = upload_table(mt, &mt_dev[dd]);
+    if (rc) return rc;
   }
-  sp.c.Mt = h->sd_Mt[0];
-  sp.a.Mt = h->sd_Mt[1];
-  h->sdirk = true;
-  if (P.precision == MGRIT_MIXED) {
-    h->sd0f.reset(new SdirkParams<float>());
-    SdirkParams<float>& f = *h->sd0f;
+  sp.c.Mt = mt_dev[0];
+  sp.a.Mt = mt_dev[1];
+  if (outf) {
+    outf->reset(new SdirkParams<float>());
+    SdirkParams<float>& f = **outf;
     std::memset((void*)&f, 0, sizeof(f));
     f.n = sp.n;
     f.P = sp.P;
@@ -536,18 +565,44 @@ static int build_sdirk(mgrit_handle* h, std::string* why) {
     std::vector<float> mtcf, mtaf;
     fill_solve_dir(&f.c, bf.cc, bf.hc, HC, Pc, nthr, C, &mtcf);
     fill_solve_dir(&f.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mtaf);
-    int rc = upload_table(mtcf, &h->sdf_Mt[0]);
-    if (!rc) rc = upload_table(mtaf, &h->sdf_Mt[1]);
+    int rc = upload_table(mtcf, &mtf_dev[0]);
+    if (!rc) rc = upload_table(mtaf, &mtf_dev[1]);
     if (rc) return rc;
-    f.c.Mt = h->sdf_Mt[0];
-    f.a.Mt = h->sdf_Mt[1];
+    f.c.Mt = mtf_dev[0];
+    f.a.Mt = mtf_dev[1];
   }
   return MGRIT_OK;
 }
 
+static int build_sdirk(mgrit_handle* h, std::string* why) {
+  int rc = build_sdirk_params(h, h->lev[0].K, &h->sd0, h->sd_Mt,
+                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why);
+  if (rc) return rc;
+  h->sdirk = true;
+  return MGRIT_OK;
+}
+
+
+
+// Algorithmic flops of `steps` SDIRK steps on K vectors: 2 per multiply-add
+// of the two recurrences of each solve (plus the 1/kappa scaling), of each
+// L_p mat-vec (plus its axpy) and of each axpy.
+template <typename T>
+static double sdirk_flops(const SdirkParams<T>& sp, int64_t nx, int64_t K, int64_t steps) {
+  int nsolve = 0, naxl = 0, nax = 0;
+  for (int o = 0; o < sp.nops; ++o) {
+    nsolve += sp.opk[o] == kOpSolve;
+    naxl += sp.opk[o] == kOpAxpyL;
+    nax += sp.opk[o] == kOpAxpy;
+  }
+  const double per_pt = nsolve * (sp.c.h + sp.a.h + 1) + naxl * (sp.p1 + 1) + nax;
+  return 2.0 * per_pt * (double)nx * (double)K * (double)steps;
+}
+
 static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double* start, double* out,
-                        const double* sub, int nsteps, int64_t K, double* traj, int every, int cat_flops) {
-  SdirkParams<double> sp = *h->sd0;
+                        const double* sub, int nsteps, int64_t K, double* traj, int every, int cat_flops,
+                        const SdirkParams<double>* base = nullptr) {
+  SdirkParams<double> sp = base ? *base : *h->sd0;
   sp.mode = mode;
   sp.zero_start = zero_start;
   sp.start = start;
@@ -559,16 +614,7 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
   sp.traj = traj;
   sp.every = every;
   sp.partial = (mode == kModeFRES) ? h->partials : nullptr;
-  // multiply-adds per point-step: solves (2 recurrences + fixups) and L mat-vecs
-  int nsolve = 0, naxl = 0, nax = 0;
-  for (int o = 0; o < sp.nops; ++o) {
-    nsolve += sp.opk[o] == kOpSolve;
-    naxl += sp.opk[o] == kOpAxpyL;
-    nax += sp.opk[o] == kOpAxpy;
-  }
-  const int H2 = sp.c.h + sp.a.h;
-  const double per_pt = nsolve * (H2 + 1) + naxl * (sp.p1 + 1) + nax;
-  ProfScope ps(h, cat_flops, 2.0 * per_pt * (double)h->nx * (double)K * (double)nsteps);
+  ProfScope ps(h, cat_flops, sdirk_flops(sp, h->nx, K, nsteps));
   if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   ++h->launches;
   return check_launch();
@@ -653,7 +699,7 @@ static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const
   double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
   const double fl = 2.0 * (double)h->nx * steps * (double)(cp.p1 + 2 * H);
   ProfScope ps(h, 1, fl);
-  ProfScope psl(h, 4 + std::min(l, kProfCats - 5), fl);
+  ProfScope psl(h, 4 + std::min(l, kProfCats - 6), fl);
   if (launch_coarse(cp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   ++h->launches;
   return check_launch();
@@ -748,7 +794,7 @@ static int l0f_cf(mgrit_handle* h, bool zero_start) {
     sp.nsteps = h->m;
     sp.K = L0.K;
     sp.traj = nullptr;
-    ProfScope ps(h, 0, 0.0);
+    ProfScope ps(h, kProfL0F32, sdirk_flops(sp, h->nx, L0.K, h->m));
     if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   } else {
     StencilParams<float>& sp = *h->fineMf;
@@ -758,7 +804,7 @@ static int l0f_cf(mgrit_handle* h, bool zero_start) {
     sp.sub = nullptr;
     sp.partial = nullptr;
     sp.rows = L0.K;
-    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    ProfScope ps(h, kProfL0F32, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
     launch_stencil_rows(sp, h->st);
   }
   ++h->launches;
@@ -788,7 +834,7 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess) {
     sp.nsteps = h->m;
     sp.K = L0.K;
     sp.traj = nullptr;
-    ProfScope ps(h, 0, 0.0);
+    ProfScope ps(h, kProfL0F32, sdirk_flops(sp, h->nx, L0.K, h->m));
     if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   } else {
     StencilParams<float>& sp = *h->fineMf;
@@ -798,7 +844,7 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess) {
     sp.sub = L0.uCf[L0.curf] + h->nx;
     sp.partial = h->partials;
     sp.rows = L0.K;
-    ProfScope ps(h, 0, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+    ProfScope ps(h, kProfL0F32, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
     launch_stencil_rows(sp, h->st);
   }
   ++h->launches;
@@ -824,7 +870,7 @@ static int coarse_launch_f(mgrit_handle* h, int l, int mode, int zero_start, con
   double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
   const double fl = 2.0 * (double)h->nx * steps * (double)(Lv.cp.p1 + 2 * H);
   ProfScope ps(h, 1, fl);
-  ProfScope psl(h, 4 + std::min(l, kProfCats - 5), fl);
+  ProfScope psl(h, 4 + std::min(l, kProfCats - 6), fl);
   int r;
   if (Lv.solve64) {
     CoarseParams<float, double> cp = Lv.cpfd;
@@ -896,6 +942,134 @@ static int inner_cycle(mgrit_handle* h, bool zero_guess) {
   return coarse_correct_f(h, 1);
 }
 
+
+static int level0_relax_residual_async_mixed(mgrit_handle* h) {
+  int rc;
+  for (int s = 0; s < h->prm.nu; ++s)
+    if ((rc = l0_cf(h))) return rc;
+  return l0_fres(h);
+}
+
+// ---------------------------------------------------------------------------
+// Graph-resident solve
+// ---------------------------------------------------------------------------
+// Level-0 pre-relaxation and residual, asynchronous, leaving the C-point
+// iterate in buffer 0 so that a replayed graph finds it where it was
+// captured (FP64 mode; MIXED keeps the FP64 iterate in place).
+static int l0_relax_residual_async(mgrit_handle* h) {
+  LevelData& L0 = h->lev[0];
+  int rc;
+  for (int s = 0; s < h->prm.nu; ++s)
+    if ((rc = l0_cf(h))) return rc;
+  if (L0.cur != 0) {
+    CUDA_TRY(cudaMemcpyAsync(L0.uC[0], L0.uC[1], sizeof(double) * (size_t)h->nx * (L0.K + 1),
+                             cudaMemcpyDeviceToDevice, h->st));
+    L0.cur = 0;
+  }
+  return l0_fres(h);
+}
+
+static int mixed_outer_body(mgrit_handle* h) {
+  LevelData& L0 = h->lev[0];
+  const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
+  int rc;
+  launch_convert(kCvtD2F, h->lev[1].g, L0.gf, (L0.K + 1) * h->nx, h->st);
+  ++h->launches;
+  for (int j = 0; j < inner; ++j)
+    if ((rc = inner_cycle(h, j == 0))) return rc;
+  launch_convert(kAddF2D, L0.uC[L0.cur] + h->nx, L0.uCf[L0.curf] + h->nx, L0.K * h->nx, h->st);
+  ++h->launches;
+  return l0_fres(h);
+}
+
+static int build_solve_graph(mgrit_handle* h) {
+  if (h->gexec) return MGRIT_OK;
+  const bool prof = h->prof.on;
+  h->prof.on = false;  // no event records inside the graph
+  int rc = MGRIT_OK;
+  cudaGraph_t pro = nullptr;
+  // capture on a private stream (the legacy default stream cannot capture);
+  // the graph is later launched on the handle's stream
+  cudaStream_t user = h->st, cap = nullptr;
+  if (cudaStreamSynchronize(user) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    h->prof.on = prof;
+    note_cuda_error("capture stream", cudaGetLastError());
+    return MGRIT_ERR_CUDA;
+  }
+  h->st = cap;
+  do {
+    if (!h->dstate) {
+      if (cudaMalloc((void**)&h->dstate, sizeof(DevSolveState)) != cudaSuccess) { rc = MGRIT_ERR_OOM; break; }
+      if (cudaMallocHost((void**)&h->hstate, sizeof(DevSolveState)) != cudaSuccess) { rc = MGRIT_ERR_OOM; break; }
+      if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) { rc = MGRIT_ERR_CUDA; break; }
+    }
+    if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) { note_cuda_error("cudaGraphCreate", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    cudaGraphConditionalHandle hnd;
+    if (cudaGraphConditionalHandleCreate(&hnd, h->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      note_cuda_error("cudaGraphConditionalHandleCreate", cudaGetLastError());
+      rc = MGRIT_ERR_CUDA;
+      break;
+    }
+    // prologue: first (pre-relaxation and) residual, captured from buffer 0
+    h->lev[0].cur = 0;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) { note_cuda_error("cudaStreamBeginCapture", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    rc = h->mixed ? level0_relax_residual_async_mixed(h) : l0_relax_residual_async(h);
+    if (cudaStreamEndCapture(h->st, &pro) != cudaSuccess && !rc) rc = MGRIT_ERR_CUDA;
+    if (rc) break;
+    cudaGraphNode_t npro, ninit, ncond;
+    if (cudaGraphAddChildGraphNode(&npro, h->graph, nullptr, 0, pro) != cudaSuccess) { note_cuda_error("cudaGraphAddChildGraphNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    void* args[3] = {(void*)&h->dstate, (void*)&h->dnorm, (void*)&hnd};
+    cudaKernelNodeParams kp = {};
+    kp.func = solve_init_kernel_fn();
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    if (cudaGraphAddKernelNode(&ninit, h->graph, &npro, 1, &kp) != cudaSuccess) { note_cuda_error("cudaGraphAddKernelNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&ncond, h->graph, &ninit, nullptr, 1, &cp) != cudaSuccess) { note_cuda_error("cudaGraphAddNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+      note_cuda_error("cudaStreamBeginCaptureToGraph", cudaGetLastError());
+      rc = MGRIT_ERR_CUDA;
+      break;
+    }
+    if (h->mixed) {
+      rc = mixed_outer_body(h);
+    } else {
+      rc = coarse_correct(h, 1);
+      if (!rc) rc = l0_relax_residual_async(h);
+    }
+    if (!rc) {
+      launch_solve_check(h->dstate, h->dnorm, hnd, h->st);
+      ++h->launches;
+    }
+    cudaGraph_t body_out = nullptr;
+    if (cudaStreamEndCapture(h->st, &body_out) != cudaSuccess && !rc) rc = MGRIT_ERR_CUDA;
+    if (rc) break;
+    h->graph_cur = h->lev[0].cur;
+    if (cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) { note_cuda_error("cudaGraphInstantiate", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+  } while (0);
+  if (pro) cudaGraphDestroy(pro);
+  h->st = user;
+  cudaStreamDestroy(cap);
+  h->prof.on = prof;
+  if (rc) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) note_cuda_error("graph build", e);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph = nullptr;
+    h->gexec = nullptr;
+  }
+  return rc;
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -914,6 +1088,8 @@ static int copy_any(void* dst, const void* src, size_t bytes, cudaStream_t st) {
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
+
+const char* mgrit_last_error(void) { return g_last_error; }
 
 const char* mgrit_strerror(int code) {
   switch (code) {
@@ -959,6 +1135,13 @@ int mgrit_destroy(mgrit_handle* h) {
   cudaFree(h->sd_Mt[1]);
   cudaFree(h->sdf_Mt[0]);
   cudaFree(h->sdf_Mt[1]);
+  cudaFree(h->sdseq_Mt[0]);
+  cudaFree(h->sdseq_Mt[1]);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->done) cudaEventDestroy(h->done);
+  cudaFree(h->dstate);
+  if (h->hstate) cudaFreeHost(h->hstate);
   cudaFree(h->seq_tmp);
   for (auto& Lv : h->lev) {
     cudaFree(Lv.uCf[0]);
@@ -1354,8 +1537,13 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
     bool out_dev = is_device_ptr(u_out);
     double* dout = out_dev ? u_out : h->lev[0].uC[1 - h->lev[0].cur];
     if (nsteps > INT32_MAX) return MGRIT_ERR_INVALID_ARG;
+    if (!h->sdseq) {
+      std::string why;
+      rc = build_sdirk_params(h, 1, &h->sdseq, h->sdseq_Mt, nullptr, nullptr, &why);
+      if (rc) return rc;
+    }
     rc = sdirk_launch(h, kModeSEQ, 0, h->du0, dout, nullptr, (int)nsteps, 1, every > 0 ? traj : nullptr,
-                      (int)every, 3);
+                      (int)every, 3, h->sdseq.get());
     if (rc) return rc;
     if (!out_dev && (rc = copy_any(u_out, dout, row, h->st))) return rc;
     CUDA_TRY(cudaStreamSynchronize(h->st));
@@ -1444,6 +1632,76 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   out[6] = (double)Lv.cp.P;
   out[7] = (double)Lv.cp.csize;
   return MGRIT_OK;
+}
+
+
+int mgrit_solve_async(mgrit_handle* h, const double* u0) {
+  if (!h || h->graph_pending) return MGRIT_ERR_INVALID_ARG;
+  int rc = build_solve_graph(h);
+  if (rc) return rc;
+  if (u0) {
+    LevelData& L0 = h->lev[0];
+    const size_t row = sizeof(double) * (size_t)h->nx;
+    if ((rc = copy_any(h->du0, u0, row, h->st))) return rc;
+    launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, h->st);
+    ++h->launches;
+    CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, h->st));
+    L0.cur = 0;
+    h->have_initial = true;
+  } else if (!h->have_initial) {
+    return MGRIT_ERR_INVALID_ARG;
+  }
+  DevSolveState init;
+  std::memset(&init, 0, sizeof(init));
+  init.tol = h->prm.tol;
+  init.max_iter = h->prm.max_iter;
+  *h->hstate = init;
+  CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(DevSolveState), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaGraphLaunch(h->gexec, h->st));
+  CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(DevSolveState), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaEventRecord(h->done, h->st));
+  h->graph_pending = true;
+  h->lev[0].cur = h->graph_cur;
+  return MGRIT_OK;
+}
+
+int mgrit_solve_query(mgrit_handle* h) {
+  if (!h || !h->graph_pending) return MGRIT_ERR_INVALID_ARG;
+  cudaError_t e = cudaEventQuery(h->done);
+  if (e == cudaSuccess) return MGRIT_OK;
+  if (e == cudaErrorNotReady) return 1;
+  return MGRIT_ERR_CUDA;
+}
+
+int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats) {
+  if (!h || !h->graph_pending) return MGRIT_ERR_INVALID_ARG;
+  CUDA_TRY(cudaEventSynchronize(h->done));
+  h->graph_pending = false;
+  const DevSolveState& s = *h->hstate;
+  int rc;
+  if (u_out) {
+    LevelData& L0 = h->lev[0];
+    if ((rc = copy_any(u_out, L0.uC[L0.cur], sizeof(double) * (size_t)h->nx * (L0.K + 1), h->st))) return rc;
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = s.it;
+    stats->converged = s.converged;
+    stats->levels = h->L;
+    stats->history_len = std::min(s.hist_len, MGRIT_MAX_HISTORY);
+    for (int i = 0; i < stats->history_len; ++i) stats->rnorm_history[i] = s.hist[i];
+    stats->rnorm0 = s.r0;
+    stats->rnorm = s.rnorm;
+    if (stats->history_len >= 2 && s.hist[stats->history_len - 2] > 0)
+      stats->conv_factor = s.hist[stats->history_len - 1] / s.hist[stats->history_len - 2];
+    if (h->mixed) {
+      const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
+      stats->outer_iterations = s.it;
+      stats->inner_cycles = s.it * inner;
+    }
+  }
+  return s.status;
 }
 
 int64_t mgrit_launch_count(const mgrit_handle* h) { return h ? h->launches : 0; }

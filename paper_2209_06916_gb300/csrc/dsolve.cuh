@@ -37,42 +37,90 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 
-// Non-circular inclusive Hillis-Steele scan of chunk states inside the CTA in
-// direction dir (-1: from lower chunks, +1: from higher chunks).  On return
-// the final states are in sq (buffer index returned) and Q holds this
-// chunk's prefix.
+// Inclusive prefix of chunk states inside the CTA in direction dir (-1: from
+// lower chunks, +1: from higher chunks).  Rounds at distances < 32 run on
+// warp shuffles; the carry from other warps comes from one exchange of warp
+// totals through shared memory (sw), combined with the host tables
+// (M^32)^j and M^d.  On return Q is this chunk's prefix and the CTA-end lane
+// of every warp has written its prefix to sq[w*3 + a] (read by chunk_carry
+// after the caller's cluster barrier).
 template <int H, typename T>
-__device__ __forceinline__ int hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, int t, int NT, int dir) {
-  int buf = 0;
-  for (int r = 0; r < D.rounds; ++r) {
+__device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, T* sw, int t, int NT, int dir) {
+  const int lane = t & 31, w = t >> 5, nw = (NT + 31) >> 5;
+  const int wlen = min(32, NT - (w << 5));
+  const unsigned mask = (wlen == 32) ? 0xffffffffu : ((1u << wlen) - 1u);
+  for (int r = 0; r < D.rounds && r < 5; ++r) {
+    const int d = 1 << r;
+    T Qo[H];
 #pragma unroll
-    for (int a = 0; a < H; ++a) sq[(buf * 3 + a) * NT + t] = Q[a];
-    __syncthreads();
-    const int src = t + dir * (1 << r);
-    if (src >= 0 && src < NT) {
-      T Qo[H];
-#pragma unroll
-      for (int a = 0; a < H; ++a) Qo[a] = sq[(buf * 3 + a) * NT + src];
+    for (int a = 0; a < H; ++a) Qo[a] = dir < 0 ? __shfl_up_sync(mask, Q[a], d) : __shfl_down_sync(mask, Q[a], d);
+    const bool ok = dir < 0 ? (lane >= d) : (lane + d < wlen);
+    if (ok) {
 #pragma unroll
       for (int a = 0; a < H; ++a)
 #pragma unroll
         for (int q = 0; q < H; ++q) Q[a] = fma(D.Mpow[r][a * 3 + q], Qo[q], Q[a]);
     }
-    buf ^= 1;
   }
+  const int end_lane = dir < 0 ? wlen - 1 : 0;
+  if (nw > 1 && D.rounds > 0) {
+    if (lane == end_lane) {
 #pragma unroll
-  for (int a = 0; a < H; ++a) sq[(buf * 3 + a) * NT + t] = Q[a];
-  return buf;
+      for (int a = 0; a < H; ++a) sw[w * 3 + a] = Q[a];
+    }
+    __syncthreads();
+    T X[H];
+#pragma unroll
+    for (int a = 0; a < H; ++a) X[a] = T(0);
+    for (int j = 1; j <= D.wterms; ++j) {
+      const int v = w + dir * j;
+      if (v < 0 || v >= nw) break;
+#pragma unroll
+      for (int a = 0; a < H; ++a)
+#pragma unroll
+        for (int q = 0; q < H; ++q) X[a] = fma(D.M32pow[j - 1][a * 3 + q], sw[v * 3 + q], X[a]);
+    }
+    const int dd = dir < 0 ? lane + 1 : wlen - lane;  // chunks from the warp edge, 1..32
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+#pragma unroll
+      for (int q = 0; q < H; ++q) Q[a] = fma(D.Mlane[dd - 1][a * 3 + q], X[q], Q[a]);
+  }
+  if (lane == end_lane) {
+#pragma unroll
+    for (int a = 0; a < H; ++a) sq[w * 3 + a] = Q[a];
+  }
 }
 
-// Carry S entering this thread's chunk in direction dir, from the final
-// intra-CTA prefixes (sq[buf]) and the cluster-level carry.  `agg` is this
-// CTA's cluster-visible aggregate slot (H values), already published and
-// synchronised across the cluster by the caller.
+// Carry S entering this thread's chunk in direction dir: the neighbouring
+// chunk's prefix (a shuffle inside the warp, sq across warps) plus
+// M^{tdist} X, X the cluster-level carry into the CTA.  `agg` is this CTA's
+// cluster-visible aggregate slot (H values), published and synchronised by
+// the caller; Mt holds M^{tdist} (zero when negligible) for this thread.
 template <int H, typename T>
-__device__ __forceinline__ void chunk_carry(T (&S)[H], const SolveDir<T>& D, const T* sq, int buf, T* agg,
-                                            int t, int NT, int dir, int rank, int C) {
+__device__ __forceinline__ void chunk_carry(T (&S)[H], const T (&Q)[H], const SolveDir<T>& D, const T* sq,
+                                            T* agg, const T (&Mt)[9], int t, int NT, int dir, int rank, int C) {
   cgc::cluster_group cl = cgc::this_cluster();
+  const int lane = t & 31, w = t >> 5;
+  const int wlen = min(32, NT - (w << 5));
+  const unsigned mask = (wlen == 32) ? 0xffffffffu : ((1u << wlen) - 1u);
+  T Qs[H];
+#pragma unroll
+  for (int a = 0; a < H; ++a) Qs[a] = dir < 0 ? __shfl_up_sync(mask, Q[a], 1) : __shfl_down_sync(mask, Q[a], 1);
+  const bool edge = dir < 0 ? (lane == 0) : (lane == wlen - 1);
+  const int tdist = (dir < 0) ? t : (NT - 1 - t);
+#pragma unroll
+  for (int a = 0; a < H; ++a) S[a] = T(0);
+  if (tdist > 0) {
+    if (edge) {
+      const int v = w + dir;
+#pragma unroll
+      for (int a = 0; a < H; ++a) S[a] = sq[v * 3 + a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < H; ++a) S[a] = Qs[a];
+    }
+  }
   T X[H];
 #pragma unroll
   for (int a = 0; a < H; ++a) X[a] = T(0);
@@ -101,21 +149,23 @@ __device__ __forceinline__ void chunk_carry(T (&S)[H], const SolveDir<T>& D, con
 #pragma unroll
     for (int a = 0; a < H; ++a) X[a] = Y[a];
   }
-  // distance (in chunks) from the CTA edge the carry enters through
+#pragma unroll
+  for (int a = 0; a < H; ++a)
+#pragma unroll
+    for (int q = 0; q < H; ++q) S[a] = fma(Mt[a * 3 + q], X[q], S[a]);
+}
+
+// M^{tdist} of this thread for direction dir (zero when below the cut).
+template <typename T>
+__device__ __forceinline__ void load_carry_power(T (&Mt)[9], const SolveDir<T>& D, int t, int NT, int dir) {
   const int tdist = (dir < 0) ? t : (NT - 1 - t);
-#pragma unroll
-  for (int a = 0; a < H; ++a) S[a] = T(0);
-  if (tdist > 0) {
-    const int src = t + dir;
-#pragma unroll
-    for (int a = 0; a < H; ++a) S[a] = sq[(buf * 3 + a) * NT + src];
-  }
   if (tdist < D.tcut) {
-    const T* Mt = D.Mt + (size_t)tdist * 9;
+    const T* p = D.Mt + (size_t)tdist * 9;
 #pragma unroll
-    for (int a = 0; a < H; ++a)
+    for (int i = 0; i < 9; ++i) Mt[i] = __ldg(p + i);
+  } else {
 #pragma unroll
-      for (int q = 0; q < H; ++q) S[a] = fma(__ldg(Mt + a * 3 + q), X[q], S[a]);
+    for (int i = 0; i < 9; ++i) Mt[i] = T(0);
   }
 }
 
@@ -124,7 +174,7 @@ __device__ __forceinline__ void chunk_carry(T (&S)[H], const SolveDir<T>& D, con
 // fixup.  Every thread of every CTA of the cluster must call it.
 template <int HC, int HA, typename T, int PM, typename Prm>
 __device__ __forceinline__ void banded_solve(T (&x)[PM], const Prm& A, T* sqc, T* sqa, T* aggc, T* agga,
-                                             int t, int rank) {
+                                             const T (&Mtc)[9], const T (&Mta)[9], int t, int rank) {
   cgc::cluster_group cl = cgc::this_cluster();
   const int P = A.P, NT = A.nthr, C = A.csize;
   if constexpr (HC > 0) {
@@ -144,14 +194,14 @@ __device__ __forceinline__ void banded_solve(T (&x)[PM], const Prm& A, T* sqc, T
           if (j == P - 1 - a) Q[a] = v;
       }
     }
-    int buf = hs_scan<HC>(Q, A.c, sqc, t, NT, -1);
+    hs_scan<HC>(Q, A.c, sqc, sqc + 24, t, NT, -1);
     if (t == NT - 1) {
 #pragma unroll
       for (int a = 0; a < HC; ++a) aggc[a] = Q[a];
     }
     cl.sync();
     T S[HC > 0 ? HC : 1];
-    chunk_carry<HC>(S, A.c, sqc, buf, aggc, t, NT, -1, rank, C);
+    chunk_carry<HC>(S, Q, A.c, sqc, aggc, Mtc, t, NT, -1, rank, C);
 #pragma unroll
     for (int j = 0; j < PM; ++j) {
       if (j < P) {
@@ -180,14 +230,14 @@ __device__ __forceinline__ void banded_solve(T (&x)[PM], const Prm& A, T* sqc, T
     }
 #pragma unroll
     for (int a = 0; a < HA; ++a) Q[a] = x[a];
-    int buf = hs_scan<HA>(Q, A.a, sqa, t, NT, +1);
+    hs_scan<HA>(Q, A.a, sqa, sqa + 24, t, NT, +1);
     if (t == 0) {
 #pragma unroll
       for (int a = 0; a < HA; ++a) agga[a] = Q[a];
     }
     cl.sync();
     T S[HA > 0 ? HA : 1];
-    chunk_carry<HA>(S, A.a, sqa, buf, agga, t, NT, +1, rank, C);
+    chunk_carry<HA>(S, Q, A.a, sqa, agga, Mta, t, NT, +1, rank, C);
 #pragma unroll
     for (int j = 0; j < PM; ++j) {
       if (j < P) {

@@ -155,6 +155,55 @@ void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st) {
   convert_kernel<<<blocks, 256, 0, st>>>(op, d, f, n);
 }
 
+__global__ void solve_init_kernel(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd) {
+  const double nrm = sqrt(fmax(0.0, dnorm_sq[0]));
+  s->r0 = nrm;
+  s->rnorm = nrm;
+  s->it = 0;
+  s->hist[0] = nrm;
+  s->hist_len = 1;
+  s->status = 0;
+  s->converged = (nrm <= s->tol * nrm) ? 1 : 0;
+  int go = 1;
+  if (!isfinite(nrm)) {
+    s->status = -4;
+    go = 0;
+  } else if (s->converged) {
+    go = 0;
+  } else if (s->max_iter <= 0) {
+    s->status = -3;
+    go = 0;
+  }
+  cudaGraphSetConditional(hnd, go);
+}
+
+__global__ void solve_check_kernel(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd) {
+  const double nrm = sqrt(fmax(0.0, dnorm_sq[0]));
+  s->it += 1;
+  s->rnorm = nrm;
+  if (s->hist_len < 128) s->hist[s->hist_len++] = nrm;
+  int go = 1;
+  if (!isfinite(nrm) || nrm > 1e3 * s->r0) {
+    s->status = -4;
+    go = 0;
+  } else if (nrm <= s->tol * s->r0) {
+    s->converged = 1;
+    go = 0;
+  } else if (s->it >= s->max_iter) {
+    s->status = -3;
+    go = 0;
+  }
+  cudaGraphSetConditional(hnd, go);
+}
+
+void* solve_init_kernel_fn() { return (void*)solve_init_kernel; }
+void* solve_check_kernel_fn() { return (void*)solve_check_kernel; }
+
+void launch_solve_check(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd,
+                        cudaStream_t st) {
+  solve_check_kernel<<<1, 1, 0, st>>>(s, dnorm_sq, hnd);
+}
+
 void launch_reduce_sum(const double* partial, int64_t n, double* out, cudaStream_t st) {
   reduce_sum_kernel<<<1, 1024, 0, st>>>(partial, n, out);
 }

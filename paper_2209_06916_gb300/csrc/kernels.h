@@ -49,8 +49,11 @@ struct SolveDir {
   int tcut;
   int jterms;
   int closure;
+  int wterms;          // cross-warp terms (warp totals combined per chunk)
   T ncoef[3];          // negated recurrence coefficients
   T Mpow[kMaxRounds][9];
+  T Mlane[32][9];      // M^d, d = 1..32 (index d - 1)
+  T M32pow[8][9];      // (M^32)^j, j = 0..wterms-1
   T McPow[16][9];
   T Clc[9];
   T G[kPMax * 3];      // impulse responses G[j*3+q]
@@ -140,6 +143,19 @@ int coarse_max_cluster(int want, size_t smem, int nthr);
 //   kAddF2D: d[i] += f[i]            kAddD2F: f[i] += (float) d[i]
 enum CvtOp { kCvtD2F = 0, kCvtF2D = 1, kAddF2D = 2, kAddD2F = 3 };
 void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st);
+// Device-side state of a graph-resident MGRIT solve (stop test on the GPU).
+struct DevSolveState {
+  double r0, rnorm, tol;
+  int it, max_iter, converged, status, hist_len, pad;
+  double hist[128];
+};
+// First residual: r0, history[0]; sets the loop condition (0 when already
+// converged).  Check: after each iteration, appends the norm and sets the
+// condition to continue, or records converged / diverged / not converged.
+void* solve_init_kernel_fn();
+void* solve_check_kernel_fn();
+void launch_solve_check(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd,
+                        cudaStream_t st);
 // sum of partial[0..n) in a fixed order, written to out[0] (FP64)
 void launch_reduce_sum(const double* partial, int64_t n, double* out, cudaStream_t st);
 // C-point iterate: row 0 = u0, rows k >= 1 uniform [0,1) at time index k*m

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "dsolve.cuh"
 #include "kernels.h"
 
@@ -26,9 +28,10 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   T* sg = sv1 + npad;
   // scan buffers of the solve precision, 16-byte aligned after the slots
   size_t slot_bytes = (((size_t)3 * npad * sizeof(T)) + 15) & ~(size_t)15;
+  const int SQ = max(6 * NT, 48);
   TC* sqc = reinterpret_cast<TC*>(smem_raw + slot_bytes);
-  TC* sqa = sqc + 6 * NT;
-  TC* aggc = sqa + 6 * NT;
+  TC* sqa = sqc + SQ;
+  TC* aggc = sqa + SQ;
   TC* agga = aggc + 4;
   double* red = reinterpret_cast<double*>(agga + 4);
   const int64_t k = blockIdx.x / C;
@@ -55,6 +58,9 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   }
   cl.sync();
 
+  TC mtc[9], mta[9];
+  load_carry_power(mtc, A.c, t, NT, -1);
+  load_carry_power(mta, A.a, t, NT, +1);
   // SL gather window of this thread: global indices gw0 + w, w < P + P1 - 1
   int gw0 = (int)((off + (int64_t)t * P - A.kshift + A.jlo) % nn);
   if (gw0 < 0) gw0 += n;
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
         }
       }
       __syncthreads();
-      banded_solve<H, H, TC, PM>(x, A, sqc, sqa, aggc, agga, t, rank);
+      banded_solve<H, H, TC, PM>(x, A, sqc, sqa, aggc, agga, mtc, mta, t, rank);
     }
     // new state v_{i - shift} = x_i + g (the shift stays inside this CTA's
     // range for the symmetric factorisation: shift = 0)
@@ -150,7 +156,8 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
 size_t coarse_smem_bytes(int npc, int P, int nthr, int elem) {
   // slots of `elem` bytes; scan buffers budgeted at 8 bytes (FP64 solve)
   size_t npad = (size_t)npc + (size_t)((npc + P - 1) / P);
-  return ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + (12 * (size_t)nthr + 8) * 8 + 32 * sizeof(double) + 16;
+  const size_t sq = std::max<size_t>(6 * (size_t)nthr, 48);
+  return ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + (2 * sq + 8) * 8 + 32 * sizeof(double) + 16;
 }
 
 template <typename T, typename TC, int PM, int P1>

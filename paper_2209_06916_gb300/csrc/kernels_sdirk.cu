@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "dsolve.cuh"
 #include "kernels.h"
 
@@ -23,11 +25,13 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
   const int rank = (int)cl.block_rank();
   const int npad = npc + (npc + P - 1) / P;
   T* slots = reinterpret_cast<T*>(smem_raw);
+  const int SQ = max(6 * NT, 48);
   T* sqc = slots + (size_t)A.nslots * npad;
-  T* sqa = sqc + 6 * NT;
-  T* aggc = sqa + 6 * NT;
+  T* sqa = sqc + SQ;
+  T* aggc = sqa + SQ;
   T* agga = aggc + 4;
-  double* red = reinterpret_cast<double*>(agga + 4);
+  // 16-byte aligned FP64 reduction scratch after the (possibly FP32) slots
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(agga + 4) + 15) & ~(uintptr_t)15);
   const int64_t k = blockIdx.x / C;
   const int64_t nn = n;
   const int64_t off = (int64_t)rank * npc;
@@ -39,6 +43,9 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
     const T* src = A.start + k * nn + off;
     for (int j = 0; j < P; ++j) slots[c0 + j + (c0 + j) / P] = src[c0 + j];
   }
+  T mtc[9], mta[9];
+  load_carry_power(mtc, A.c, t, NT, -1);
+  load_carry_power(mta, A.a, t, NT, +1);
   // L_p window of this thread: global points gw0 + w, w < P + P1 - 1
   int gw0 = (int)((off + c0 + A.llo) % nn);
   if (gw0 < 0) gw0 += n;
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
 #pragma unroll
         for (int j = 0; j < PM; ++j)
           if (j < P) x[j] = A.sscale * src[c0 + j + (c0 + j) / P];
-        banded_solve<HC, HA, T, PM>(x, A, sqc, sqa, aggc, agga, t, rank);
+        banded_solve<HC, HA, T, PM>(x, A, sqc, sqa, aggc, agga, mtc, mta, t, rank);
 #pragma unroll
         for (int j = 0; j < PM; ++j)
           if (j < P) dst[c0 + j + (c0 + j) / P] = x[j];
@@ -146,7 +153,8 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
 
 size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem) {
   size_t npad = (size_t)npc + (size_t)((npc + P - 1) / P);
-  return ((size_t)nslots * npad + 12 * (size_t)nthr + 8) * (size_t)elem + 32 * sizeof(double) + 16;
+  const size_t sq = std::max<size_t>(6 * (size_t)nthr, 48);
+  return ((size_t)nslots * npad + 2 * sq + 8) * (size_t)elem + 32 * sizeof(double) + 16;
 }
 
 template <typename T, int PM, int P1>

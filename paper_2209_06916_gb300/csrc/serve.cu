@@ -1,0 +1,254 @@
+// Batched and served MGRIT solves (host-side scheduling in C++).
+//
+// Every solve is a graph-resident MGRIT solve (mgrit_solve_async: one CUDA
+// graph launch, iteration loop and stop test on the device).  A batch
+// launches all its solves at once over a pool of streams, so kernels of
+// different solves share the GPU; the server admits requests of a Poisson
+// stream as device memory (an HBM budget) and in-flight slots free up, and
+// records arrival-to-completion latency per request.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include "../../include/mgrit.h"
+
+namespace {
+
+int64_t levels_of(const mgrit_params& p) {
+  if (p.levels > 0) return p.levels;
+  int64_t L = 1, N = p.nt;
+  while (N % p.m == 0 && N / p.m >= 2) {
+    N /= p.m;
+    ++L;
+  }
+  return std::max<int64_t>(L, 2);
+}
+
+}  // namespace
+
+// Device bytes a solve with these parameters allocates (C-point and RHS
+// buffers of every level, FP64 plus the FP32 copies of MIXED), used for
+// admission against the HBM budget.
+extern "C" int64_t mgrit_estimate_bytes(const mgrit_params* p) {
+  if (!p || p->nx <= 0 || p->nt <= 0 || p->m < 2) return -1;
+  const int64_t L = levels_of(*p);
+  int64_t rows = 0, N = p->nt;
+  for (int64_t l = 0; l < L; ++l) {
+    int64_t K = (l < L - 1) ? N / p->m : 0;
+    if (l < L - 1) rows += 2 * (K + 1);  // C-point double buffer
+    if (l >= 1) rows += N + 1;           // RHS
+    N /= p->m;
+  }
+  int64_t bytes = rows * p->nx * 8;
+  if (p->precision == MGRIT_MIXED) bytes += rows * p->nx * 4 + (N + 2) * p->nx * 8;
+  return bytes + (4 << 20);
+}
+
+struct mgrit_batch {
+  std::vector<mgrit_handle*> hs;
+  std::vector<cudaStream_t> streams;
+  std::vector<mgrit_params> prm;
+};
+
+extern "C" int mgrit_batch_destroy(mgrit_batch* b) {
+  if (!b) return MGRIT_OK;
+  for (auto h : b->hs) mgrit_destroy(h);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  delete b;
+  return MGRIT_OK;
+}
+
+extern "C" int mgrit_batch_create(const mgrit_params* params, int64_t count, int nstreams, mgrit_batch** out) {
+  if (!params || count <= 0 || !out || nstreams <= 0) return MGRIT_ERR_INVALID_ARG;
+  *out = nullptr;
+  mgrit_batch* b = new mgrit_batch();
+  for (int i = 0; i < nstreams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      mgrit_batch_destroy(b);
+      return MGRIT_ERR_CUDA;
+    }
+    b->streams.push_back(s);
+  }
+  for (int64_t i = 0; i < count; ++i) {
+    mgrit_handle* h = nullptr;
+    int rc = mgrit_setup(&params[i], (void*)b->streams[i % nstreams], &h);
+    if (rc) {
+      mgrit_batch_destroy(b);
+      return rc;
+    }
+    b->hs.push_back(h);
+    b->prm.push_back(params[i]);
+  }
+  *out = b;
+  return MGRIT_OK;
+}
+
+extern "C" int mgrit_batch_solve(mgrit_batch* b, const double* const* u0s, mgrit_stats* stats) {
+  if (!b || !u0s) return MGRIT_ERR_INVALID_ARG;
+  const int64_t n = (int64_t)b->hs.size();
+  for (int64_t i = 0; i < n; ++i) {
+    int rc = mgrit_solve_async(b->hs[i], u0s[i]);
+    if (rc) return rc;
+  }
+  int worst = MGRIT_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    int rc = mgrit_solve_wait(b->hs[i], nullptr, stats ? &stats[i] : nullptr);
+    if (rc == MGRIT_ERR_CUDA || rc == MGRIT_ERR_INVALID_ARG) return rc;
+    if (rc && !worst) worst = rc;
+  }
+  return worst;
+}
+
+extern "C" int mgrit_batch_get(mgrit_batch* b, int64_t i, double* u_out) {
+  if (!b || i < 0 || i >= (int64_t)b->hs.size() || !u_out) return MGRIT_ERR_INVALID_ARG;
+  const mgrit_params& p = b->prm[i];
+  // the C-point iterate of level 0
+  return mgrit_level_io(b->hs[i], 0, 0, u_out, 0, nullptr);
+}
+
+extern "C" int64_t mgrit_batch_dof(const mgrit_batch* b) {
+  if (!b) return 0;
+  int64_t s = 0;
+  for (auto& p : b->prm) s += p.nx * p.nt;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// server
+// ---------------------------------------------------------------------------
+extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s, double* const* u_outs,
+                           const double* arrival_s, int64_t count, int64_t hbm_budget_bytes, int max_inflight,
+                           double time_limit_s, mgrit_request_result* results, mgrit_serve_stats* st) {
+  if (!params || !u0s || !arrival_s || count < 0 || max_inflight <= 0 || !results) return MGRIT_ERR_INVALID_ARG;
+  for (int64_t i = 1; i < count; ++i)
+    if (arrival_s[i] < arrival_s[i - 1]) return MGRIT_ERR_INVALID_ARG;
+  std::vector<cudaStream_t> pool;
+  for (int i = 0; i < max_inflight; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto q : pool) cudaStreamDestroy(q);
+      return MGRIT_ERR_CUDA;
+    }
+    pool.push_back(s);
+  }
+  struct Slot {
+    mgrit_handle* h = nullptr;
+    int64_t req = -1;
+    int64_t bytes = 0;
+  };
+  std::vector<Slot> slots(max_inflight);
+  std::deque<int64_t> pending;
+  for (int64_t i = 0; i < count; ++i) {
+    std::memset(&results[i], 0, sizeof(results[i]));
+    results[i].status = 1;  // not started
+  }
+  mgrit_serve_stats S;
+  std::memset(&S, 0, sizeof(S));
+  const auto t0 = std::chrono::steady_clock::now();
+  auto now = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  int64_t next = 0, finished = 0, mem = 0;
+  int rc_fatal = MGRIT_OK;
+  while (finished < count) {
+    const double t = now();
+    if (t > time_limit_s) break;
+    while (next < count && arrival_s[next] <= t) pending.push_back(next++);
+    S.max_backlog = std::max<int64_t>(S.max_backlog, (int64_t)pending.size());
+    bool progress = false;
+    // completions
+    for (auto& sl : slots) {
+      if (!sl.h) continue;
+      int q = mgrit_solve_query(sl.h);
+      if (q == 1) continue;
+      mgrit_stats ms;
+      int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
+      mgrit_request_result& r = results[sl.req];
+      r.finish_s = now();
+      r.latency_ms = (r.finish_s - arrival_s[sl.req]) * 1e3;
+      r.iterations = ms.iterations;
+      r.status = rc;
+      if (rc == MGRIT_OK) {
+        ++S.completed;
+        S.dof_completed += (double)params[sl.req].nx * (double)params[sl.req].nt;
+      } else {
+        ++S.failed;
+      }
+      mgrit_destroy(sl.h);
+      mem -= sl.bytes;
+      sl = Slot();
+      ++finished;
+      progress = true;
+      if (rc == MGRIT_ERR_CUDA) rc_fatal = rc;
+    }
+    if (rc_fatal) break;
+    // admissions (FIFO; a request larger than the whole budget is rejected)
+    while (!pending.empty()) {
+      const int64_t req = pending.front();
+      const int64_t need = mgrit_estimate_bytes(&params[req]);
+      if (need > hbm_budget_bytes) {
+        results[req].status = MGRIT_ERR_OOM;
+        ++S.rejected;
+        ++finished;
+        pending.pop_front();
+        continue;
+      }
+      auto it = std::find_if(slots.begin(), slots.end(), [](const Slot& s) { return s.h == nullptr; });
+      if (it == slots.end() || mem + need > hbm_budget_bytes) break;
+      const int si = (int)(it - slots.begin());
+      mgrit_handle* h = nullptr;
+      int rc = mgrit_setup(&params[req], (void*)pool[si], &h);
+      if (rc == MGRIT_OK) rc = mgrit_solve_async(h, u0s[req]);
+      results[req].start_s = now();
+      pending.pop_front();
+      if (rc) {
+        if (h) mgrit_destroy(h);
+        results[req].status = rc;
+        ++S.failed;
+        ++finished;
+        continue;
+      }
+      it->h = h;
+      it->req = req;
+      it->bytes = need;
+      mem += need;
+      S.max_mem_bytes = std::max(S.max_mem_bytes, mem);
+      ++S.admitted;
+      progress = true;
+    }
+    int inflight = 0;
+    for (auto& sl : slots) inflight += sl.h != nullptr;
+    S.max_inflight = std::max(S.max_inflight, inflight);
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  // drain whatever is still running at the time limit
+  for (auto& sl : slots) {
+    if (!sl.h) continue;
+    mgrit_stats ms;
+    int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
+    mgrit_request_result& r = results[sl.req];
+    r.finish_s = now();
+    r.latency_ms = (r.finish_s - arrival_s[sl.req]) * 1e3;
+    r.iterations = ms.iterations;
+    r.status = rc;
+    if (rc == MGRIT_OK) {
+      ++S.completed;
+      S.dof_completed += (double)params[sl.req].nx * (double)params[sl.req].nt;
+    } else {
+      ++S.failed;
+    }
+    mgrit_destroy(sl.h);
+    sl = Slot();
+  }
+  S.arrived = next;
+  S.backlog_end = (int64_t)pending.size() + (count - next);
+  S.wall_s = now();
+  for (auto q : pool) cudaStreamDestroy(q);
+  if (st) *st = S;
+  return rc_fatal;
+}

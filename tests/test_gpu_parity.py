@@ -288,3 +288,36 @@ def test_sequential_stepping_matches_oracle(p, c, nx, nsteps, every):
     host_out = np.zeros(nx)
     s.fine_propagate(u0, host_out, nsteps)  # host pointers
     assert _rel(host_out, u) < 1e-13 * nsteps
+
+
+# ---------------------------------------------------------------------------
+# graph-resident solve (conditional while node, stop test on the device)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,p,c,m,levels,nu,prec,nx,nt", [
+    (pkg.ERK, 3, 0.85, 8, 4, 1, pkg.FP64, 128, 8 ** 3 * 2),
+    (pkg.ERK, 1, 0.85, 4, 2, 1, pkg.FP64, 256, 1024),
+    (pkg.ERK, 3, 0.85, 4, 3, 2, pkg.FP64, 64, 16 * 6),
+    (pkg.SDIRK, 3, 5.0, 4, 3, 1, pkg.FP64, 64, 16 * 8),
+    (pkg.ERK, 3, 0.85, 8, 4, 1, pkg.MIXED, 256, 8 ** 3 * 2),
+])
+def test_graph_solve_equals_eager_solve(kind, p, c, m, levels, nu, prec, nx, nt):
+    u0 = ic_sin4(nx)
+    res = []
+    for graph in (False, True):
+        prm = pkg.make_params(nx, nt, c, p, kind=kind, m=m, levels=levels, nu=nu, tol=1e-10, max_iter=40,
+                              precision=prec, seed=4)
+        s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        if graph:
+            for _ in range(2):  # the second launch replays the built graph
+                s.solve_async(dev(u0))
+                st = s.wait(out)
+        else:
+            st = s.solve(dev(u0), out)
+        res.append((host(out), st))
+        s.close()
+    (a, sa), (b, sb) = res
+    assert sa["iterations"] == sb["iterations"] and sb["converged"]
+    assert np.array_equal(a, b)
+    assert np.allclose(sa["history"], sb["history"], rtol=0, atol=0)

@@ -55,3 +55,33 @@ def batch_mix(count, seed, nx_choices=(256, 512, 1024, 2048, 4096, 8192),
             "m": int(r.choice(m_choices)), "seed": seed + i,
         })
     return out
+
+
+def serving_stream(rate, duration, seed, sdirk_fraction=0.1, nx_max_sdirk=65536, nt_max_sdirk=131072,
+                   nx_choices=(256, 512, 1024, 2048, 4096, 8192),
+                   nt_choices=(512, 1024, 2048, 4096, 8192, 16384)):
+    """Poisson arrivals (rate per second over `duration` s) of solve requests:
+    a fraction `sdirk_fraction` are SDIRK5+U5 with CFL uniform in [2, 8] and
+    nx, nt powers of two up to nx_max_sdirk / nt_max_sdirk; the rest follow
+    batch_mix.  Returns (arrival times, list of parameter dicts)."""
+    r = np.random.default_rng(seed)
+    t, arrivals, reqs = 0.0, [], []
+    i = 0
+    while True:
+        t += r.exponential(1.0 / rate)
+        if t > duration:
+            break
+        if r.uniform() < sdirk_fraction:
+            nxs = [n for n in (256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536) if n <= nx_max_sdirk]
+            nts = [n for n in (512, 1024, 2048, 4096, 8192, 16384, 32768, 65536, 131072) if n <= nt_max_sdirk]
+            req = {"nx": int(r.choice(nxs)), "nt": int(r.choice(nts)), "p": 5, "kind": "sdirk", "q": 5,
+                   "cfl": float(r.uniform(2.0, 8.0)), "m": 4, "seed": seed + i}
+        else:
+            req = {"nx": int(r.choice(nx_choices)), "nt": int(r.choice(nt_choices)),
+                   "p": int(r.choice((1, 3, 5))), "kind": "erk", "cfl": float(r.uniform(0.5, 0.95)),
+                   "m": int(r.choice((4, 8, 16))), "seed": seed + i}
+            req["q"] = req["p"]
+        arrivals.append(t)
+        reqs.append(req)
+        i += 1
+    return np.array(arrivals), reqs
