@@ -567,6 +567,7 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
     for (int i = 0; i < 9; ++i) md[i] = M[i];
     for (int dd = 1; dd <= 32; ++dd) {
       d.Mlane.insert(d.Mlane.end(), md, md + 9);
+      if (mat3_norm(md) >= 1e-18) d.dcut = dd;
       mat3_mul(md, M, md);
     }
     double m32[9];

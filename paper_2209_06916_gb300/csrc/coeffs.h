@@ -90,6 +90,7 @@ struct DistScanTables {
   std::vector<double> Mlane;   // 32 * 9: M^d, d = 1..32
   std::vector<double> M32pow;  // wterms * 9: (M^32)^j
   int wterms = 0;
+  int dcut = 0;                // largest d <= 32 with M^d not negligible
 };
 DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C);
 

@@ -15,8 +15,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -57,6 +60,7 @@ struct LevelData {
 // profiling categories: 0 level-0 stencil, 1 coarse kernel (all levels),
 // 2 reductions, 3 sequential stepping, 4 + l coarse kernel on level l
 constexpr int kProfCats = 20;
+constexpr int kStencilThreadsHost = 256;  // threads of stencil_rows_kernel
 constexpr int kProfL0F32 = 19;  // MIXED: level-0 FP32 inner-cycle kernels
 
 struct mgrit_handle {
@@ -234,6 +238,7 @@ static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int H
   for (int j = 0; j < d->jterms; ++j)
     for (int i = 0; i < 9; ++i) d->McPow[j][i] = (T)tb.McPow[j * 9 + i];
   d->wterms = std::min(tb.wterms, 8);
+  d->dcut = tb.dcut;
   for (int dd = 0; dd < 32; ++dd)
     for (int i = 0; i < 9; ++i) d->Mlane[dd][i] = (T)tb.Mlane[dd * 9 + i];
   for (int j = 0; j < d->wterms; ++j)
@@ -620,6 +625,96 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
   return check_launch();
 }
 
+
+// ---------------------------------------------------------------------------
+// Autotuner of the level-0 stencil tile (outputs per thread R: a CTA covers
+// 256 R points of one CF-interval).  Each candidate is timed with CUDA
+// events on the handle's own buffers; decisions are cached per (n_x, taps,
+// element size, rows) for the process and, if MGRIT_AUTOTUNE_CACHE names a
+// file, across processes.  MGRIT_AUTOTUNE=0 keeps the n_x-based default.
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  char key[128];
+  int r;
+  while (std::fscanf(fp, "%127s %d", key, &r) == 2) g_tune[key] = r;
+  std::fclose(fp);
+}
+
+static void tune_store(const std::string& key, int r) {
+  g_tune[key] = r;
+  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d\n", key.c_str(), r);
+  std::fclose(fp);
+}
+
+template <typename T>
+static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out, int64_t rows) {
+  const char* on = std::getenv("MGRIT_AUTOTUNE");
+  if ((on && on[0] == '0') || rows <= 0) return MGRIT_OK;
+  char keyb[128];
+  std::snprintf(keyb, sizeof(keyb), "stencil:nx=%lld:taps=%d:b=%d:rows=%lld", (long long)sp->nx, sp->ntaps,
+                (int)sizeof(T), (long long)rows);
+  const std::string key(keyb);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      sp->tile_r = it->second;
+      return MGRIT_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  StencilParams<T> p = *sp;
+  p.in = in;
+  p.out = out;
+  p.rhs = nullptr;
+  p.sub = nullptr;
+  p.partial = nullptr;
+  p.rows = rows;
+  float best = 1e30f;
+  int bestR = 0;
+  for (int R : {1, 2, 4, 8}) {
+    if ((int64_t)kStencilThreadsHost * R > 2 * sp->nx && R > 1) continue;
+    p.tile_r = R;
+    launch_stencil_rows(p, h->st);  // warm-up
+    cudaEventRecord(e0, h->st);
+    for (int i = 0; i < 3; ++i) launch_stencil_rows(p, h->st);
+    cudaEventRecord(e1, h->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestR = R;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (check_launch()) return MGRIT_ERR_CUDA;
+  if (bestR > 0) {
+    sp->tile_r = bestR;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store(key, bestR);
+  }
+  return MGRIT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // kernels on levels
 // ---------------------------------------------------------------------------
@@ -682,8 +777,7 @@ static int l0_fres(mgrit_handle* h) {
 }
 
 static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const double* start,
-                         double* out, const double* sub, double* parent, int nsteps, int64_t K,
-                         const double* g) {
+                         double* out, const double* sub, double* parent, int nsteps, int64_t K, double* g) {
   CoarseParams<double> cp = h->lev[l].cp;
   cp.mode = mode;
   cp.zero_start = zero_start;
@@ -741,13 +835,23 @@ static int coarse_correct(mgrit_handle* h, int l) {
   double* parent = Par.uC[Par.cur];
   int rc;
   if (l == h->L - 1) {
-    return coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, parent, (int)Lv.N, 1, Lv.g);
+    rc = coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, parent, (int)Lv.N, 1, Lv.g);
+  } else {
+    rc = level_pre_and_residual(h, l, true);
+    if (rc) return rc;
+    rc = coarse_correct(h, l + 1);
+    if (rc) return rc;
+    rc = coarse_launch(h, l, kModeFOUT, 0, Lv.uC[Lv.cur], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.g);
   }
-  rc = level_pre_and_residual(h, l, true);
   if (rc) return rc;
-  rc = coarse_correct(h, l + 1);
-  if (rc) return rc;
-  return coarse_launch(h, l, kModeFOUT, 0, Lv.uC[Lv.cur], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.g);
+  // the kernel left this level's values at all its points in its RHS rows:
+  // add them into the parent's C-points (rows 1..N; row 0 stays exact)
+  {
+    ProfScope ps(h, 2, 0.0);
+    launch_convert(kAddD2D, parent + h->nx, nullptr, Lv.N * h->nx, h->st, Lv.g + h->nx);
+  }
+  ++h->launches;
+  return check_launch();
 }
 
 static int level0_relax_residual(mgrit_handle* h, double* norm) {
@@ -852,7 +956,7 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess) {
 }
 
 static int coarse_launch_f(mgrit_handle* h, int l, int mode, int zero_start, const float* start, float* out,
-                           const float* sub, float* parent, int nsteps, int64_t K, const float* g) {
+                           const float* sub, float* parent, int nsteps, int64_t K, float* g) {
   LevelData& Lv = h->lev[l];
   auto fill = [&](auto& cp) {
     cp.mode = mode;
@@ -893,13 +997,13 @@ static int coarse_correct_f(mgrit_handle* h, int l) {
   int rc;
   const size_t rowd = sizeof(double) * (size_t)h->nx;
   if (l == h->L - 1) {
-    // coarsest level in FP64: g (FP32) -> FP64, sequential solve into a
-    // zeroed FP64 buffer, then added to the FP32 parent
+    // coarsest level in FP64: g (FP32) -> FP64, sequential solve (its
+    // values replace the RHS rows), then added to the FP32 parent
+    (void)rowd;
     launch_convert(kCvtF2D, Lv.g, Lv.gf, (Lv.N + 1) * h->nx, h->st);
-    CUDA_TRY(cudaMemsetAsync(h->seq_tmp, 0, rowd * (Lv.N + 1), h->st));
-    rc = coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, h->seq_tmp, (int)Lv.N, 1, Lv.g);
+    rc = coarse_launch(h, l, kModeSEQ, 1, nullptr, nullptr, nullptr, nullptr, (int)Lv.N, 1, Lv.g);
     if (rc) return rc;
-    launch_convert(kAddD2F, h->seq_tmp + h->nx, parent + h->nx, Lv.N * h->nx, h->st);
+    launch_convert(kAddD2F, Lv.g + h->nx, parent + h->nx, Lv.N * h->nx, h->st);
     h->launches += 2;
     return check_launch();
   }
@@ -922,7 +1026,11 @@ static int coarse_correct_f(mgrit_handle* h, int l) {
   if (rc) return rc;
   rc = coarse_correct_f(h, l + 1);
   if (rc) return rc;
-  return coarse_launch_f(h, l, kModeFOUT, 0, Lv.uCf[Lv.curf], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.gf);
+  rc = coarse_launch_f(h, l, kModeFOUT, 0, Lv.uCf[Lv.curf], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.gf);
+  if (rc) return rc;
+  launch_convert(kAddF2F, nullptr, parent + h->nx, Lv.N * h->nx, h->st, nullptr, Lv.gf + h->nx);
+  ++h->launches;
+  return check_launch();
 }
 
 // One FP32 inner cycle for the level-0 error equation with RHS lev[0].gf.
@@ -1294,13 +1402,18 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     }
     if ((rc = alloc(&h->seq_tmp, row * (h->lev[L - 1].N + 1)))) return rc;
   }
-  h->npart = h->lev[0].K * std::max<int64_t>(stencil_tiles(P.nx), h->sdirk ? h->sd0->csize : 1) + 1;
+  h->npart = h->lev[0].K * std::max<int64_t>(stencil_tiles(P.nx, 1), h->sdirk ? h->sd0->csize : 1) + 1;
   for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * h->lev[l].cp.csize);
   if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
   if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
   if ((rc = alloc(&h->du0, row))) return rc;
   CUDA_TRY(cudaMemsetAsync(h->du0, 0, row, h->st));
   if (cudaMallocHost((void**)&h->hnorm, sizeof(double)) != cudaSuccess) return MGRIT_ERR_OOM;
+  if (!h->sdirk) {  // tile of the level-0 composite stencil (on the C-point buffers)
+    LevelData& L0 = h->lev[0];
+    if ((rc = autotune_stencil(h.get(), h->fineM.get(), L0.uC[0], L0.uC[1], L0.K))) return rc;
+    if (h->mixed && (rc = autotune_stencil(h.get(), h->fineMf.get(), L0.uCf[0], L0.uCf[1], L0.K))) return rc;
+  }
   CUDA_TRY(cudaStreamSynchronize(h->st));
   *out = h.release();
   return MGRIT_OK;

@@ -63,12 +63,14 @@ __device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, 
     }
   }
   const int end_lane = dir < 0 ? wlen - 1 : 0;
-  if (nw > 1 && D.rounds > 0) {
+  if (nw > 1 && D.rounds > 0 && D.dcut > 0) {
     if (lane == end_lane) {
 #pragma unroll
       for (int a = 0; a < H; ++a) sw[w * 3 + a] = Q[a];
     }
     __syncthreads();
+    const int dd = dir < 0 ? lane + 1 : wlen - lane;  // chunks from the warp edge, 1..32
+    if (dd <= D.dcut) {
     T X[H];
 #pragma unroll
     for (int a = 0; a < H; ++a) X[a] = T(0);
@@ -80,11 +82,11 @@ __device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, 
 #pragma unroll
         for (int q = 0; q < H; ++q) X[a] = fma(D.M32pow[j - 1][a * 3 + q], sw[v * 3 + q], X[a]);
     }
-    const int dd = dir < 0 ? lane + 1 : wlen - lane;  // chunks from the warp edge, 1..32
 #pragma unroll
     for (int a = 0; a < H; ++a)
 #pragma unroll
       for (int q = 0; q < H; ++q) Q[a] = fma(D.Mlane[dd - 1][a * 3 + q], X[q], Q[a]);
+    }
   }
   if (lane == end_lane) {
 #pragma unroll

@@ -78,8 +78,8 @@ static int stencil_r(int64_t nx) {
   return 1;
 }
 
-int stencil_tiles(int64_t nx) {
-  int R = stencil_r(nx);
+int stencil_tiles(int64_t nx, int tile_r) {
+  int R = tile_r > 0 ? tile_r : stencil_r(nx);
   return (int)((nx + (int64_t)kStencilThreads * R - 1) / ((int64_t)kStencilThreads * R));
 }
 
@@ -93,7 +93,7 @@ static int64_t launch_stencil_r(const StencilParams<T>& p, cudaStream_t st) {
                          64 * 1024);
     configured = true;
   }
-  dim3 grid((unsigned)p.rows, (unsigned)stencil_tiles(p.nx));
+  dim3 grid((unsigned)p.rows, (unsigned)stencil_tiles(p.nx, R));
   stencil_rows_kernel<T, R><<<grid, kStencilThreads, smem, st>>>(p);
   return (int64_t)grid.x * grid.y;
 }
@@ -101,7 +101,9 @@ static int64_t launch_stencil_r(const StencilParams<T>& p, cudaStream_t st) {
 template <typename T>
 static int64_t launch_stencil_any(const StencilParams<T>& p, cudaStream_t st) {
   if (p.rows <= 0) return 0;
-  switch (stencil_r(p.nx)) {
+  switch (p.tile_r > 0 ? p.tile_r : stencil_r(p.nx)) {
+    case 8:
+      return launch_stencil_r<T, 8>(p, st);
     case 4:
       return launch_stencil_r<T, 4>(p, st);
     case 2:
@@ -130,9 +132,16 @@ __global__ void __launch_bounds__(1024) reduce_sum_kernel(const double* __restri
   if (threadIdx.x == 0) out[0] = tot;
 }
 
-__global__ void convert_kernel(int op, double* __restrict__ d, float* __restrict__ f, int64_t n) {
+__global__ void convert_kernel(int op, double* __restrict__ d, float* __restrict__ f, int64_t n,
+                               const double* __restrict__ d2, const float* __restrict__ f2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     switch (op) {
+      case kAddD2D:
+        d[i] += d2[i];
+        break;
+      case kAddF2F:
+        f[i] += f2[i];
+        break;
       case kCvtD2F:
         f[i] = (float)d[i];
         break;
@@ -149,10 +158,10 @@ __global__ void convert_kernel(int op, double* __restrict__ d, float* __restrict
   }
 }
 
-void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st) {
+void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st, const double* d2, const float* f2) {
   if (n <= 0) return;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  convert_kernel<<<blocks, 256, 0, st>>>(op, d, f, n);
+  convert_kernel<<<blocks, 256, 0, st>>>(op, d, f, n, d2, f2);
 }
 
 __global__ void solve_init_kernel(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd) {

@@ -25,10 +25,11 @@ struct StencilParams {
   int64_t rows;
   int lo;
   int ntaps;
+  int tile_r;          // outputs per thread (tile = 256 * tile_r points); 0 = by n_x
   T taps[kMaxTaps];
 };
 
-int stencil_tiles(int64_t nx);
+int stencil_tiles(int64_t nx, int tile_r = 0);
 // Launch; returns the number of CTAs (= partial slots written).
 int64_t launch_stencil_rows(const StencilParams<double>& p, cudaStream_t st);
 int64_t launch_stencil_rows(const StencilParams<float>& p, cudaStream_t st);
@@ -50,6 +51,7 @@ struct SolveDir {
   int jterms;
   int closure;
   int wterms;          // cross-warp terms (warp totals combined per chunk)
+  int dcut;            // lanes with distance d <= dcut from the warp edge need M^d
   T ncoef[3];          // negated recurrence coefficients
   T Mpow[kMaxRounds][9];
   T Mlane[32][9];      // M^d, d = 1..32 (index d - 1)
@@ -84,10 +86,12 @@ struct CoarseParams {
   int m;
   int64_t K;
   const T* start;
-  const T* g;
+  T* g;                // RHS rows; FOUT / SEQ overwrite the rows they consumed with the
+                       // level's values there (C-points and F-relaxed points), which the
+                       // host then adds into the parent level
   T* out;
   const T* sub;
-  T* parent;
+  T* parent;           // unused by the kernel (kept for the host's bookkeeping)
   double* partial;     // FRES: one slot per CTA (K * csize)
 };
 
@@ -141,8 +145,10 @@ int coarse_max_cluster(int want, size_t smem, int nthr);
 // elementwise precision conversions over n values:
 //   kCvtD2F: f[i] = (float) d[i]     kCvtF2D: d[i] = f[i]
 //   kAddF2D: d[i] += f[i]            kAddD2F: f[i] += (float) d[i]
-enum CvtOp { kCvtD2F = 0, kCvtF2D = 1, kAddF2D = 2, kAddD2F = 3 };
-void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st);
+enum CvtOp { kCvtD2F = 0, kCvtF2D = 1, kAddF2D = 2, kAddD2F = 3, kAddD2D = 4, kAddF2F = 5 };
+//   kAddD2D: d[i] += d2[i]          kAddF2F: f[i] += f2[i]   (d2 / f2: src)
+void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st, const double* d2 = nullptr,
+                    const float* f2 = nullptr);
 // Device-side state of a graph-resident MGRIT solve (stop test on the GPU).
 struct DevSolveState {
   double r0, rnorm, tol;

@@ -5,6 +5,7 @@
 // post-relaxation added into the parent level (FOUT, the coarse-grid
 // correction), sequential coarsest solve (SEQ) and plain apply (APPLY).
 #include <cooperative_groups.h>
+#include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +26,9 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   const int npad = npc + (npc + P - 1) / P;
   T* sv0 = reinterpret_cast<T*>(smem_raw);
   T* sv1 = sv0 + npad;
+  // RHS row: row s+1 is fetched (cp.async) into it as soon as the cluster
+  // barrier after step s has retired its last reader, and lands while step
+  // s+1 gathers and solves
   T* sg = sv1 + npad;
   // scan buffers of the solve precision, 16-byte aligned after the slots
   size_t slot_bytes = (((size_t)3 * npad * sizeof(T)) + 15) & ~(size_t)15;
@@ -47,15 +51,24 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
     for (int i = t; i < npc; i += NT) cur[i + i / P] = src[i];
   }
   if (A.mode == kModeFOUT) {
+    // the C-points themselves go to RHS row k m (and the last CTA's
+    // start[K] to row K m): rows the F post-relaxation does not read
     const T* src = A.start + k * nn + off;
-    T* par = A.parent + k * A.m * nn + off;
-    for (int i = t; i < npc; i += NT) par[i] += src[i];
+    T* gr = A.g + k * A.m * nn + off;
+    for (int i = t; i < npc; i += NT) gr[i] = src[i];
     if (k == A.K - 1) {
       const T* s2 = A.start + A.K * nn + off;
-      T* p2 = A.parent + A.K * A.m * nn + off;
-      for (int i = t; i < npc; i += NT) p2[i] += s2[i];
+      T* g2 = A.g + A.K * A.m * nn + off;
+      for (int i = t; i < npc; i += NT) g2[i] = s2[i];
     }
   }
+  const int64_t gbase = (A.mode == kModeSEQ) ? 0 : k * A.m;
+  auto prefetch = [&](int s, T* dst) {
+    const T* gr = A.g + (gbase + s) * nn + off;
+    for (int i = t; i < npc; i += NT) __pipeline_memcpy_async(&dst[i + i / P], &gr[i], sizeof(T));
+    __pipeline_commit();
+  };
+  if (A.g && A.nsteps >= 1) prefetch(1, sg);
   cl.sync();
 
   TC mtc[9], mta[9];
@@ -65,12 +78,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   int gw0 = (int)((off + (int64_t)t * P - A.kshift + A.jlo) % nn);
   if (gw0 < 0) gw0 += n;
 
-  const int64_t gbase = (A.mode == kModeSEQ) ? 0 : k * A.m;
   for (int s = 1; s <= A.nsteps; ++s) {
-    if (A.g) {
-      const T* gr = A.g + (gbase + s) * nn + off;
-      for (int i = t; i < npc; i += NT) sg[i + i / P] = gr[i];
-    }
     TC x[PM];
     if (s == 1 && A.zero_start) {
 #pragma unroll
@@ -105,6 +113,10 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
       __syncthreads();
       banded_solve<H, H, TC, PM>(x, A, sqc, sqa, aggc, agga, mtc, mta, t, rank);
     }
+    if (A.g) {  // this step's RHS row has landed (for every thread)
+      __pipeline_wait_prior(0);
+      __syncthreads();
+    }
     // new state v_{i - shift} = x_i + g (the shift stays inside this CTA's
     // range for the symmetric factorisation: shift = 0)
 #pragma unroll
@@ -118,12 +130,13 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
       }
     }
     cl.sync();
+    if (A.g && s + 1 <= A.nsteps) prefetch(s + 1, sg);
     T* tmp = cur;
     cur = nxt;
     nxt = tmp;
-    if (A.mode == kModeFOUT || A.mode == kModeSEQ) {
-      T* par = A.parent + (gbase + s) * nn + off;
-      for (int i = t; i < npc; i += NT) par[i] += cur[i + i / P];
+    if (A.mode == kModeFOUT || A.mode == kModeSEQ) {  // store only: no read on the critical path
+      T* gr = A.g + (gbase + s) * nn + off;
+      for (int i = t; i < npc; i += NT) gr[i] = cur[i + i / P];
     }
   }
 

@@ -198,7 +198,7 @@ extern "C" int mgrit_residual_noalloc(const mgrit_params* params, const double* 
       P.nx % 8)
     return MGRIT_ERR_INVALID_ARG;
   const int64_t K = rows - 1;
-  if (K * (int64_t)mg::stencil_tiles(P.nx) > kNoAllocSlots) return MGRIT_ERR_INVALID_ARG;
+  if (K * (int64_t)mg::stencil_tiles(P.nx, 0) > kNoAllocSlots) return MGRIT_ERR_INVALID_ARG;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;
