@@ -175,7 +175,14 @@ def run_serving(args):
         u0s.append(ic_sin4_noise(d["nx"], seed=d["seed"]) if d["kind"] == "erk" else ic_fourier(d["nx"], d["seed"]))
     res, st = pkg.serve(prms, u0s, arrivals, 80 * 10 ** 9, max_inflight=args.inflight,
                         time_limit_s=args.duration + args.drain)
-    lat = np.array([r["latency_ms"] for r in res if r["status"] == 0])
+    ok = [r for r in res if r["status"] == 0]
+    lat = np.array([r["latency_ms"] for r in ok])
+    svc = np.array([(r["finish_s"] - r["start_s"]) * 1e3 for r in ok])
+    statuses = {}
+    for r in res:
+        if r["status"] not in (0, 1):
+            statuses[pkg.ERRORS.get(r["status"], str(r["status"]))] = statuses.get(
+                pkg.ERRORS.get(r["status"], str(r["status"])), 0) + 1
     offered = float(sum(d["nx"] * d["nt"] for d in reqs))
     line = {"metric": METRIC, "value": st["dof_completed"] / st["wall_s"], "unit": UNIT, "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": st["wall_s"] * 1e3, "higher_is_better": True,
@@ -187,7 +194,11 @@ def run_serving(args):
                                            "max_backlog", "max_mem_bytes", "max_inflight", "wall_s")},
             "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                            "p99": float(np.percentile(lat, 99)) if lat.size else None,
-                           "completed": int(lat.size)}}
+                           "completed": int(lat.size)},
+            "service_ms": {"p50": float(np.percentile(svc, 50)) if svc.size else None,
+                           "p99": float(np.percentile(svc, 99)) if svc.size else None,
+                           "note": "admission to completion (latency_ms adds the queueing under overload)"},
+            "failures": statuses}
     print(json.dumps(line))
     return 0
 
@@ -228,6 +239,8 @@ def main():
     ap.add_argument("--drain", type=float, default=25.0, help="c5: extra seconds before the server stops")
     ap.add_argument("--inflight", type=int, default=64, help="c5: concurrent solves")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision sub-measurement")
+    ap.add_argument("--nt", type=int, default=0, help="override n_t of c1-c3 (small profiling cases)")
+    ap.add_argument("--no-sequential", action="store_true", help="skip the sequential-stepping baseline")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload == "c4" and args.impl == "ours":
@@ -249,7 +262,12 @@ def main():
 
     import paper_2209_06916_gb300 as pkg
 
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.nt > 0:
+        w["nt"] = args.nt
+        w["name"] += "_nt%d" % args.nt
+        while w["levels"] > 2 and args.nt % (w["m"] ** (w["levels"] - 1)):
+            w["levels"] -= 1
     nx, nt, m = w["nx"], w["nt"], w["m"]
     stream = torch.cuda.current_stream()
     kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
@@ -315,20 +333,22 @@ def main():
     # GPU sequential time-stepping of the same problem (the baseline), and the
     # accuracy of the MGRIT solution against it at the final time
     seq_out = torch.empty(nx, dtype=torch.float64, device="cuda")
-    s.fine_propagate(u0, seq_out, nt)
-    s.profile(True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
+    seq_ms, err, sprof = None, None, {"sequential": (0, 0.0, 0.0)}
+    if not args.no_sequential:
         s.fine_propagate(u0, seq_out, nt)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1) / args.steps
-    sprof = s.profile_read()
-    s.profile(False)
-    s.solve(u0, out)
-    torch.cuda.synchronize()
-    err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+        s.profile(True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.fine_propagate(u0, seq_out, nt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1) / args.steps
+        sprof = s.profile_read()
+        s.profile(False)
+        s.solve(u0, out)
+        torch.cuda.synchronize()
+        err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
     dof = nx * nt
     variants = {}
     if not args.no_variants and prec == pkg.FP64:
@@ -344,11 +364,12 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         mms = e0.elapsed_time(e1) / args.steps
-        errm = float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+        errm = (float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+                if seq_ms is not None else None)
         variants["mixed"] = {"value": dof / (mms / 1e3), "unit": UNIT, "ms": mms,
                              "outer_iterations": stm["outer_iterations"], "inner_cycles": stm["inner_cycles"],
                              "max_rel_err_vs_sequential": errm,
-                             "over_sequential": (dof / (mms / 1e3)) / (dof / (seq_ms / 1e3))}
+                             "over_sequential": seq_ms / mms if seq_ms is not None else None}
         sm.close()
     clocks = clocks_sampler_stop(cp, cf, clk_path, local)
     scnt, sms, sfl = sprof["sequential"]
@@ -380,11 +401,13 @@ def main():
             "e2e": {"value": ws * dof * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8},
             "gpu_launches": launches, "clocks": clocks,
-            "sequential": {"value": dof / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
-                           "kernel": "seq_kernel (thread-block cluster, DSMEM halos, composite Phi^B)",
-                           "achieved_tflops": sfl / (sms / 1e3) / 1e12 if sms > 0 else None,
-                           "frac": (sfl / (sms / 1e3)) / FP64_PEAK_FLOPS if sms > 0 else None},
-            "mgrit_over_sequential": (dof / (ms / 1e3 / args.steps)) / (dof / (seq_ms / 1e3)),
+            "sequential": None if seq_ms is None else {
+                "value": dof / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
+                "kernel": ("seq_kernel (thread-block cluster, DSMEM halos, composite Phi^B)" if w["kind"] == "erk"
+                           else "sdirk_kernel<double> on one cluster (K = 1)"),
+                "achieved_tflops": sfl / (sms / 1e3) / 1e12 if sms > 0 else None,
+                "frac": (sfl / (sms / 1e3)) / FP64_PEAK_FLOPS if sms > 0 else None},
+            "mgrit_over_sequential": seq_ms / (ms / args.steps) if seq_ms is not None else None,
             "max_rel_err_vs_sequential": err,
             "variants": variants,
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()}}

@@ -50,6 +50,10 @@ struct LevelData {
   CoarseParams<float, double> cpfd;
   float* Mtf_dev[2] = {nullptr, nullptr};
   bool solve64 = false;
+  // geometry-free coarse operator data: factorised correction, SL weights
+  // (scaled by 1/kappa of the factorisation)
+  BandFactor bf;
+  double slw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double kappa = 1.0;
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
@@ -189,36 +193,6 @@ static bool pick_chunks(int64_t n, int* P, int* nthr) {
   return best >= 0;
 }
 
-// Geometry of a coarse level with K vectors (CF-intervals) of n points:
-// C CTAs per vector (a thread-block cluster, power of two <= 16), nthr
-// threads per CTA, P points per thread.  Grow C until the level has about
-// two CTAs per SM (keeping >= 256 points per CTA), then shrink P towards 8
-// while the level has fewer than ~4 warps per SM.
-static bool pick_coarse_geometry(int64_t n, int64_t K, int* C, int* P, int* nthr) {
-  int c = 1;
-  while (c < 16 && K * c < 2 * 152 && n % (2 * c) == 0 && n / (2 * c) >= 256) c *= 2;
-  int64_t npc = n / c;
-  int bestP = -1;
-  double bestScore = 0.0;
-  for (int p = 8; p <= 64; ++p) {
-    if (npc % p) continue;
-    int64_t t = npc / p;
-    if (t > 256) continue;
-    // prefer P = 32, but P = 16 / 8 when the level is short of warps
-    double warps_per_sm = (double)K * c * ((t + 31) / 32) / 152.0;
-    double target = warps_per_sm * 32.0 / p < 4.0 ? 8.0 : 32.0;
-    double score = std::fabs(std::log((double)p / target));
-    if (bestP < 0 || score < bestScore - 1e-12) {
-      bestP = p;
-      bestScore = score;
-    }
-  }
-  if (bestP < 0) return false;
-  *C = c;
-  *P = bestP;
-  *nthr = (int)(npc / bestP);
-  return true;
-}
 
 template <typename T>
 static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int Hpad, int P, int nthr, int C,
@@ -274,13 +248,89 @@ static int set_stencil(StencilParams<T>* sp, const Stencil& s0, int64_t nx) {
   return MGRIT_OK;
 }
 
-template <typename T>
-static int upload_table(const std::vector<T>& v, T** dev) {
-  if (cudaMalloc((void**)dev, sizeof(T) * std::max<size_t>(9, v.size())) != cudaSuccess) {
+
+// ---------------------------------------------------------------------------
+// Memory of a handle.  Device buffers come from one stream-ordered pool per
+// device (cudaMallocFromPoolAsync / cudaFreeAsync on the handle's stream):
+// freeing never synchronises the device, so solves that finish while others
+// run (batches, the server) do not stall them, and freed hierarchies stay
+// reserved in the pool for the next setup instead of going back to the
+// driver.  Small pinned host blocks (the device-state mirror, the norm) are
+// recycled through a free list for the same reason (cudaFreeHost
+// synchronises).
+// ---------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t device_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
     cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = UINT64_MAX;  // keep freed memory reserved in the pool
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  g_pools[dev] = pool;
+  return pool;
+}
+
+static int dev_alloc(mgrit_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaMemPool_t pool = device_pool(h->device);
+  if (!pool || cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, h->st) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
     return MGRIT_ERR_OOM;
   }
-  if (!v.empty() && cudaMemcpy(*dev, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+  return MGRIT_OK;
+}
+
+static void dev_free(mgrit_handle* h, void* p) {
+  if (p) cudaFreeAsync(p, h->st);  // ordered after the handle's last work on its stream
+}
+
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;  // 4 KiB pinned host blocks
+constexpr size_t kPinBlock = 4096;
+
+static void* pinned_get() {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      void* p = g_pin_free.back();
+      g_pin_free.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, kPinBlock) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pinned_put(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+template <typename T>
+static int upload_table(mgrit_handle* h, const std::vector<T>& v, T** dev) {
+  int rc = dev_alloc(h, (void**)dev, sizeof(T) * std::max<size_t>(9, v.size()));
+  if (rc) return rc;
+  // pageable source: staged before the call returns
+  if (!v.empty() && cudaMemcpyAsync(*dev, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->st) !=
+                        cudaSuccess)
     return MGRIT_ERR_CUDA;
   return MGRIT_OK;
 }
@@ -339,71 +389,55 @@ static void phi_recursion(const mgrit_params& P, int L, std::vector<double>* php
   }
 }
 
-static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long long k, double eps,
-                        std::string* why) {
+// MGRIT_GEOM="C:P" restricts the step kernels' geometries to C CTAs per
+// vector and chunk length P where that geometry fits (testing every
+// geometry against the oracle); tuning and its cache are then bypassed.
+static bool geom_forced(int* C, int* P) {
+  const char* f = std::getenv("MGRIT_GEOM");
+  return f && std::sscanf(f, "%d:%d", C, P) == 2;
+}
+
+// Coarse-level parameters of level l for geometry g: FP64, and in MIXED the
+// FP32-storage forms with an FP32 or FP64 correction solve; chunk-scan
+// tables built on the host, per-chunk carry tables uploaded.
+struct GeomC {
+  int C = 0, P = 0, nthr = 0;
+};
+static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   const mgrit_params& P = h->prm;
   LevelData& Lv = h->lev[l];
-  int p = P.order_p, q = P.rk_order_q;
-  Stencil A = stencil_identity();
-  A = stencil_add(A, central_diff(p + 1), -phi_p);
-  if (q != p && phi_q != 0.0) A = stencil_add(A, central_diff(q + 1), -phi_q);
-  BandFactor bf;
-  if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
+  const int p = P.order_p;
   const int H = (p + 1) / 2;
-  if (bf.hc > H || bf.ha > H) {
-    if (why) *why = "correction band wider than the SL stencil order supports";
-    return MGRIT_ERR_UNSUPPORTED;
-  }
-  if (bf.shift != 0) {
-    if (why) *why = "correction factorisation needs an index shift";
-    return MGRIT_ERR_UNSUPPORTED;
-  }
-  int Cc, Pc, nthr;
-  int64_t Kl = (l == h->L - 1) ? 1 : Lv.K;
-  if (!pick_coarse_geometry(h->nx, Kl, &Cc, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
-  size_t smem = coarse_smem_bytes((int)(h->nx / Cc), Pc, nthr, 8);
-  if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
-  while (Cc > 1 && coarse_max_cluster(Cc, smem, nthr) < Cc) {
-    // fall back to a smaller cluster with the same chunk length
-    Cc /= 2;
-    nthr *= 2;
-    if (nthr > 256) return MGRIT_ERR_UNSUPPORTED;
-    smem = coarse_smem_bytes((int)(h->nx / Cc), Pc, nthr, 8);
-    if (smem > 227 * 1024) return MGRIT_ERR_UNSUPPORTED;
-  }
+  const BandFactor& bf = Lv.bf;
   CoarseParams<double>& cp = Lv.cp;
   std::memset((void*)&cp, 0, sizeof(cp));
   cp.n = (int)h->nx;
-  cp.P = Pc;
-  cp.nthr = nthr;
-  cp.csize = Cc;
-  cp.npc = (int)(h->nx / Cc);
+  cp.P = g.P;
+  cp.nthr = g.nthr;
+  cp.csize = g.C;
+  cp.npc = (int)(h->nx / g.C);
   cp.p1 = p + 1;
   cp.jlo = -(p + 1) / 2;
-  cp.kshift = (int)(((k % h->nx) + h->nx) % h->nx);
+  cp.kshift = (int)(((Lv.kshift % h->nx) + h->nx) % h->nx);
   cp.shift = 0;
-  std::vector<double> w = sl_weights(p, eps);
-  for (int a = 0; a <= p; ++a) cp.w[a] = w[a] * bf.inv_kappa;
-  std::vector<double> mtc, mta;
-  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, Pc, nthr, Cc, &mtc);
-  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, Pc, nthr, Cc, &mta);
+  for (int a = 0; a <= p; ++a) cp.w[a] = Lv.slw[a];
   for (int d = 0; d < 2; ++d) {
-    std::vector<double>& mt = d ? mta : mtc;
-    if (cudaMalloc((void**)&Lv.Mt_dev[d], sizeof(double) * std::max<size_t>(9, mt.size())) != cudaSuccess) {
-      cudaGetLastError();
-      return MGRIT_ERR_OOM;
-    }
-    if (cudaMemcpy(Lv.Mt_dev[d], mt.data(), sizeof(double) * mt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-      return MGRIT_ERR_CUDA;
+    dev_free(h, Lv.Mt_dev[d]);
+    Lv.Mt_dev[d] = nullptr;
+    dev_free(h, Lv.Mtf_dev[d]);
+    Lv.Mtf_dev[d] = nullptr;
+  }
+  std::vector<double> mtc, mta;
+  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, g.P, g.nthr, g.C, &mtc);
+  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, g.P, g.nthr, g.C, &mta);
+  for (int d = 0; d < 2; ++d) {
+    int rc = upload_table(h, d ? mta : mtc, &Lv.Mt_dev[d]);
+    if (rc) return rc;
   }
   cp.c.Mt = Lv.Mt_dev[0];
   cp.a.Mt = Lv.Mt_dev[1];
   cp.m = h->m;
-  Lv.kappa = band_condition(A);
   if (P.precision == MGRIT_MIXED) {
-    // FP32 storage and SL gather; the correction solve in FP64 where an FP32
-    // solve would lose more than about four of its seven digits
-    Lv.solve64 = Lv.kappa > 1e3;
     auto geom = [&](auto& q) {
       std::memset((void*)&q, 0, sizeof(q));
       q.n = cp.n;
@@ -423,21 +457,93 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
     Lv.cpfd.a = cp.a;
     geom(Lv.cpf);
     std::vector<float> mtcf, mtaf;
-    fill_solve_dir(&Lv.cpf.c, bf.cc, bf.hc, H, Pc, nthr, Cc, &mtcf);
-    fill_solve_dir(&Lv.cpf.a, bf.ca, bf.ha, H, Pc, nthr, Cc, &mtaf);
-    int rc = upload_table(mtcf, &Lv.Mtf_dev[0]);
-    if (!rc) rc = upload_table(mtaf, &Lv.Mtf_dev[1]);
+    fill_solve_dir(&Lv.cpf.c, bf.cc, bf.hc, H, g.P, g.nthr, g.C, &mtcf);
+    fill_solve_dir(&Lv.cpf.a, bf.ca, bf.ha, H, g.P, g.nthr, g.C, &mtaf);
+    int rc = upload_table(h, mtcf, &Lv.Mtf_dev[0]);
+    if (!rc) rc = upload_table(h, mtaf, &Lv.Mtf_dev[1]);
     if (rc) return rc;
     Lv.cpf.c.Mt = Lv.Mtf_dev[0];
     Lv.cpf.a.Mt = Lv.Mtf_dev[1];
   }
+  return MGRIT_OK;
+}
+
+// Candidate geometries of the coarse kernel on this handle's vectors: the
+// SL window (P + p + 1 points) must lie within two neighbouring CTAs.
+static std::vector<GeomC> coarse_geometries(mgrit_handle* h, int max_out) {
+  const int elem = h->prm.precision == MGRIT_MIXED ? 4 : 8;
+  std::vector<std::pair<double, GeomC>> all;
+  for (int C = 1; C <= 16; C *= 2) {
+    if (h->nx % C) continue;
+    const int64_t npc = h->nx / C;
+    for (int P : kChunkLens) {
+      if (npc % P || npc < P + h->prm.order_p + 2) continue;
+      const int64_t nthr = npc / P;
+      if (nthr < 1 || nthr > 256) continue;
+      const size_t sm = coarse_smem_bytes((int)npc, P, (int)nthr, 8);
+      if (sm > 227 * 1024) continue;
+      if (C > 1 && coarse_max_cluster(C, sm, (int)nthr) < C) continue;
+      const int warps = ((int)nthr + 31) / 32;
+      const int regs = elem == 8 ? (P <= 8 ? 80 : P <= 16 ? 112 : 192) : (P <= 8 ? 64 : P <= 16 ? 96 : 160);
+      int cps = std::min<int>((int)(228 * 1024 / (sm + 1024)), 64 / warps);
+      cps = std::min(cps, 65536 / (regs * warps * 32));
+      cps = std::min(cps, 32);
+      const double lanes = (double)nthr / (32.0 * warps);
+      all.push_back({std::min(16.0, (double)(cps * warps)) * lanes - 0.01 * C, GeomC{C, P, (int)nthr}});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<double, GeomC>& a, const std::pair<double, GeomC>& b) { return a.first > b.first; });
+  int fc, fp;
+  if (geom_forced(&fc, &fp)) {
+    std::vector<std::pair<double, GeomC>> keep;
+    for (auto& x : all)
+      if (x.second.C == fc && x.second.P == fp) keep.push_back(x);
+    if (!keep.empty()) all.swap(keep);
+  }
+  std::vector<GeomC> out;
+  for (auto& x : all)
+    if ((int)out.size() < max_out) out.push_back(x.second);
+  return out;
+}
+
+static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long long k, double eps,
+                        std::string* why) {
+  const mgrit_params& P = h->prm;
+  LevelData& Lv = h->lev[l];
+  int p = P.order_p, q = P.rk_order_q;
+  Stencil A = stencil_identity();
+  A = stencil_add(A, central_diff(p + 1), -phi_p);
+  if (q != p && phi_q != 0.0) A = stencil_add(A, central_diff(q + 1), -phi_q);
+  BandFactor bf;
+  if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
+  const int H = (p + 1) / 2;
+  if (bf.hc > H || bf.ha > H) {
+    if (why) *why = "correction band wider than the SL stencil order supports";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  if (bf.shift != 0) {
+    if (why) *why = "correction factorisation needs an index shift";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  Lv.bf = bf;
+  std::vector<double> w = sl_weights(p, eps);
+  for (int a = 0; a <= p; ++a) Lv.slw[a] = w[a] * bf.inv_kappa;
+  Lv.kappa = band_condition(A);
+  // MIXED: FP32 storage and SL gather; the correction solve in FP64 where an
+  // FP32 solve would lose more than about four of its seven digits
+  if (P.precision == MGRIT_MIXED) Lv.solve64 = Lv.kappa > 1e3;
   Lv.kshift = k;
   Lv.eps = eps;
   Lv.phi = phi_p;
   Lv.phi_q = phi_q;
-  return MGRIT_OK;
+  std::vector<GeomC> cand = coarse_geometries(h, 1);
+  if (cand.empty()) {
+    if (why) *why = "no coarse-kernel chunk geometry fits the vector";
+    return MGRIT_ERR_INVALID_ARG;
+  }
+  return coarse_with_geom(h, l, cand[0]);
 }
-
 
 // Level-0 SDIRK step programme: stiffly accurate stages (q <= 4),
 //   R_i = u (i >= 1);  Y_i = (I + gamma c L)^{-1} R_i;  R_j += -c a_ji L Y_i,
@@ -487,60 +593,270 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
   return true;
 }
 
-// Build the SDIRK step parameters for K vectors per launch (K = number of
-// CF-intervals on level 0, or 1 for sequential stepping); the cluster size
-// follows from K and from the shared-memory need of the stage slots.
-static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
-                              double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
-                              std::string* why) {
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  char key[128];
+  int r;
+  while (std::fscanf(fp, "%127s %d", key, &r) == 2) g_tune[key] = r;
+  std::fclose(fp);
+}
+
+static void tune_store(const std::string& key, int r) {
+  g_tune[key] = r;
+  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d\n", key.c_str(), r);
+  std::fclose(fp);
+}
+
+// Barrier schedule of an SDIRK step programme.  Every op reads and writes
+// only its own thread's chunk, except that an AXPYL reads L_p halos from the
+// neighbouring chunks; a SOLVE has barriers of its own between its read and
+// its write.  A barrier is needed before an AXPYL group whose source was
+// written since the last barrier (read after write), and before any write
+// to a slot whose halos were read since the last barrier (write after read).
+// Consecutive AXPYLs on one source form a group (one mat-vec).  The
+// schedule is iterated over steps until it is stable.
+static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
+  const int n = sp->nops;
+  for (int o = 0; o < n; ++o) {
+    sp->opg[o] = 1;
+    sp->opb[o] = 0;
+  }
+  sp->resb = 0;
+  for (int o = 0; o < n;) {
+    if (sp->opk[o] != kOpAxpyL) {
+      ++o;
+      continue;
+    }
+    int g = 1;
+    while (o + g < n && sp->opk[o + g] == kOpAxpyL && sp->ops[o + g] == sp->ops[o]) ++g;
+    for (int e = 0; e < g; ++e)
+      if (sp->opd[o + e] == sp->ops[o]) {
+        if (why) *why = "SDIRK programme: a mat-vec writes its own source";
+        return false;
+      }
+    sp->opg[o] = g;
+    for (int e = 1; e < g; ++e) sp->opg[o + e] = 0;
+    o += g;
+  }
+  for (int pass = 0; pass < 16; ++pass) {
+    bool changed = false;
+    unsigned W = 0, R = 0;  // slots written / halo-read since the last barrier
+    for (int step = 0; step < 4; ++step) {
+      for (int o = 0; o < n;) {
+        const int kind = sp->opk[o];
+        if (kind == kOpAxpyL) {
+          const int g = sp->opg[o];
+          unsigned dsts = 0;
+          for (int e = 0; e < g; ++e) dsts |= 1u << sp->opd[o + e];
+          const bool need = ((W >> sp->ops[o]) & 1u) || (R & dsts);
+          if (need && !sp->opb[o]) {
+            sp->opb[o] = 1;
+            changed = true;
+          }
+          if (sp->opb[o]) W = R = 0;
+          R |= 1u << sp->ops[o];
+          W |= dsts;
+          o += g;
+        } else if (kind == kOpSolve) {
+          if (sp->opb[o]) W = R = 0;
+          W = R = 0;  // the solve's own barriers precede its write
+          W |= 1u << sp->opd[o];
+          ++o;
+        } else {
+          const int dst = sp->opd[o];
+          if (((R >> dst) & 1u) && !sp->opb[o]) {
+            sp->opb[o] = 1;
+            changed = true;
+          }
+          if (sp->opb[o]) W = R = 0;
+          W |= 1u << dst;
+          ++o;
+        }
+      }
+      if (sp->result != 0) {
+        if ((R & 1u) && !sp->resb) {
+          sp->resb = 1;
+          changed = true;
+        }
+        if (sp->resb) W = R = 0;
+        W |= 1u;
+      }
+    }
+    if (!changed) return true;
+  }
+  if (why) *why = "SDIRK barrier schedule did not settle";
+  return false;
+}
+
+// Geometry of a vector split for the step kernels: C CTAs (one thread-block
+// cluster), nthr threads per CTA, a chunk of P points per thread.
+struct Geom {
+  int C = 0, P = 0, nthr = 0;
+};
+
+// Rough resident warps per SM of a geometry (shared memory, threads,
+// registers), used to order candidates and as the untuned choice.
+static double geom_score(const Geom& g, size_t smem, int elem) {
+  const int warps = (g.nthr + 31) / 32;
+  const int regs = elem == 8 ? (g.P <= 8 ? 96 : g.P <= 16 ? 128 : 224) : (g.P <= 8 ? 64 : g.P <= 16 ? 96 : 168);
+  int cps = (int)(228 * 1024 / (smem + 1024));
+  cps = std::min(cps, 64 / warps);
+  cps = std::min(cps, 65536 / (regs * warps * 32));
+  cps = std::min(cps, 32);
+  const double lanes = (double)g.nthr / (32.0 * warps);
+  return std::min(16.0, (double)(cps * warps)) * lanes - 0.01 * g.C;
+}
+
+// Candidate geometries of an n-point vector: P a compiled chunk length,
+// 1..256 threads, at least `minpts` points per CTA, shared memory within the
+// CTA limit and a co-schedulable cluster; best-scored first.
+template <typename F>
+static std::vector<Geom> chunk_geometries(int64_t n, int64_t minpts, int elem, F smem_of, int max_out) {
+  std::vector<std::pair<double, Geom>> all;
+  for (int C = 1; C <= 16; C *= 2) {
+    if (n % C) continue;
+    const int64_t npc = n / C;
+    if (npc < minpts) continue;
+    for (int P : kChunkLens) {
+      if (npc % P) continue;
+      const int64_t nthr = npc / P;
+      if (nthr < 1 || nthr > 256) continue;
+      Geom g{C, P, (int)nthr};
+      const size_t sm = smem_of(g);
+      if (sm > 227 * 1024) continue;
+      if (C > 1 && sdirk_max_cluster(C, sm, g.nthr) < C) continue;
+      all.push_back({geom_score(g, sm, elem), g});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const std::pair<double, Geom>& a, const std::pair<double, Geom>& b) {
+    return a.first > b.first;
+  });
+  int fc, fp;
+  if (geom_forced(&fc, &fp)) {
+    std::vector<std::pair<double, Geom>> keep;
+    for (auto& x : all)
+      if (x.second.C == fc && x.second.P == fp) keep.push_back(x);
+    if (!keep.empty()) all.swap(keep);
+  }
+  std::vector<Geom> out;
+  for (auto& x : all)
+    if ((int)out.size() < max_out) out.push_back(x.second);
+  return out;
+}
+
+static bool tuning_on() {
+  const char* on = std::getenv("MGRIT_AUTOTUNE");
+  return !(on && on[0] == '0');
+}
+
+// Cached geometry decision for a tuning key (process-wide, optionally in
+// the MGRIT_AUTOTUNE_CACHE file as C * 1000000 + P * 1000 + nthr).
+static bool geom_cached(const std::string& key, Geom* g) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load();
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  g->C = it->second / 1000000;
+  g->P = (it->second / 1000) % 1000;
+  g->nthr = it->second % 1000;
+  return true;
+}
+
+static void geom_store(const std::string& key, const Geom& g) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_store(key, g.C * 1000000 + g.P * 1000 + g.nthr);
+}
+
+// Time `launch` (one warm-up, two timed) on the handle's stream; ms per
+// launch, or a negative value on a launch error.
+template <typename F>
+static float time_launches(mgrit_handle* h, F launch) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  float ms = -1.f;
+  if (launch() >= 0) {
+    cudaEventRecord(e0, h->st);
+    bool ok = launch() >= 0 && launch() >= 0;
+    cudaEventRecord(e1, h->st);
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms *= 0.5f;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return -1.f;
+  return ms;
+}
+
+// Geometry-free part of the level-0 SDIRK operator: the step programme with
+// its barrier schedule, L_p taps, the factorised stage matrix.
+static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why) {
   const mgrit_params& P = h->prm;
   const int p = P.order_p;
-  out->reset(new SdirkParams<double>());
-  SdirkParams<double>& sp = **out;
-  std::memset((void*)&sp, 0, sizeof(sp));
+  std::memset((void*)sp, 0, sizeof(*sp));
   double gamma = 0.0;
-  if (!sdirk_program(P.rk_order_q, P.cfl, &sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
+  if (!sdirk_program(P.rk_order_q, P.cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
+  if (!schedule_sdirk(sp, why)) return MGRIT_ERR_UNSUPPORTED;
   Stencil L = upwind_taps(p);
-  sp.p1 = L.width();
-  sp.llo = L.lo;
-  for (int i = 0; i < L.width(); ++i) sp.ltaps[i] = L.a[i];
-  BandFactor bf;
+  sp->p1 = L.width();
+  sp->llo = L.lo;
+  if (L.lo != -(L.width() / 2)) {
+    if (why) *why = "upwind stencil offsets outside the kernel's layout";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  for (int i = 0; i < L.width(); ++i) sp->ltaps[i] = L.a[i];
   Stencil A = stencil_add(stencil_identity(), L, gamma * P.cfl);
-  if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
+  if (!band_factor(A, bf, why)) return MGRIT_ERR_UNSTABLE;
   const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
-  if (bf.hc > HC || bf.ha > HA || bf.shift != 0) {
+  if (bf->hc > HC || bf->ha > HA || bf->shift != 0) {
     if (why) *why = "stage matrix factorisation outside the kernel's orders";
     return MGRIT_ERR_UNSUPPORTED;
   }
-  sp.sscale = bf.inv_kappa;
-  // geometry: like a coarse level with K0 intervals, then more CTAs per
-  // vector until the slots fit in shared memory
-  int C, Pc, nthr;
-  if (!pick_coarse_geometry(h->nx, K, &C, &Pc, &nthr)) return MGRIT_ERR_INVALID_ARG;
-  while (sdirk_smem_bytes((int)(h->nx / C), Pc, nthr, sp.nslots, 8) > 227 * 1024) {
-    if (C >= 16 || h->nx % (2 * C)) return MGRIT_ERR_UNSUPPORTED;
-    C *= 2;
-    if ((h->nx / C) % Pc) return MGRIT_ERR_UNSUPPORTED;
-    nthr = (int)(h->nx / C / Pc);
-  }
-  while (nthr > 256) {
-    if ((h->nx / C) % (2 * Pc) || 2 * Pc > kPMax) return MGRIT_ERR_UNSUPPORTED;
-    Pc *= 2;
-    nthr /= 2;
-  }
-  size_t smem = sdirk_smem_bytes((int)(h->nx / C), Pc, nthr, sp.nslots, 8);
-  if (C > 1 && coarse_max_cluster(C, smem, nthr) < C) return MGRIT_ERR_UNSUPPORTED;
+  sp->sscale = bf->inv_kappa;
+  return MGRIT_OK;
+}
+
+// The SDIRK step parameters for geometry g (FP64, and FP32 when outf):
+// chunk-scan tables on the host, per-chunk carry tables uploaded.
+static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const BandFactor& bf, const Geom& g,
+                           std::unique_ptr<SdirkParams<double>>* out, double** mt_dev,
+                           std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev) {
+  const int p = h->prm.order_p;
+  const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
+  out->reset(new SdirkParams<double>(op));
+  SdirkParams<double>& sp = **out;
   sp.n = (int)h->nx;
-  sp.P = Pc;
-  sp.nthr = nthr;
-  sp.csize = C;
-  sp.npc = (int)(h->nx / C);
+  sp.P = g.P;
+  sp.nthr = g.nthr;
+  sp.csize = g.C;
+  sp.npc = (int)(h->nx / g.C);
+  for (int d = 0; d < 2; ++d) {
+    dev_free(h, mt_dev[d]);
+    mt_dev[d] = nullptr;
+  }
   std::vector<double> mtc, mta;
-  fill_solve_dir(&sp.c, bf.cc, bf.hc, HC, Pc, nthr, C, &mtc);
-  fill_solve_dir(&sp.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mta);
+  fill_solve_dir(&sp.c, bf.cc, bf.hc, HC, g.P, g.nthr, g.C, &mtc);
+  fill_solve_dir(&sp.a, bf.ca, bf.ha, HA, g.P, g.nthr, g.C, &mta);
   for (int dd = 0; dd < 2; ++dd) {
-    std::vector<double>& mt = dd ? mta : mtc;
-    int rc = upload_table(mt, &mt_dev[dd]);
+    int rc = upload_table(h, dd ? mta : mtc, &mt_dev[dd]);
     if (rc) return rc;
   }
   sp.c.Mt = mt_dev[0];
@@ -561,17 +877,24 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
     f.nops = sp.nops;
     f.nslots = sp.nslots;
     f.result = sp.result;
+    f.resb = sp.resb;
     for (int o = 0; o < kSdirkMaxOps; ++o) {
       f.opk[o] = sp.opk[o];
       f.opd[o] = sp.opd[o];
       f.ops[o] = sp.ops[o];
+      f.opg[o] = sp.opg[o];
+      f.opb[o] = sp.opb[o];
       f.opc[o] = (float)sp.opc[o];
     }
+    for (int d = 0; d < 2; ++d) {
+      dev_free(h, mtf_dev[d]);
+      mtf_dev[d] = nullptr;
+    }
     std::vector<float> mtcf, mtaf;
-    fill_solve_dir(&f.c, bf.cc, bf.hc, HC, Pc, nthr, C, &mtcf);
-    fill_solve_dir(&f.a, bf.ca, bf.ha, HA, Pc, nthr, C, &mtaf);
-    int rc = upload_table(mtcf, &mtf_dev[0]);
-    if (!rc) rc = upload_table(mtaf, &mtf_dev[1]);
+    fill_solve_dir(&f.c, bf.cc, bf.hc, HC, g.P, g.nthr, g.C, &mtcf);
+    fill_solve_dir(&f.a, bf.ca, bf.ha, HA, g.P, g.nthr, g.C, &mtaf);
+    int rc = upload_table(h, mtcf, &mtf_dev[0]);
+    if (!rc) rc = upload_table(h, mtaf, &mtf_dev[1]);
     if (rc) return rc;
     f.c.Mt = mtf_dev[0];
     f.a.Mt = mtf_dev[1];
@@ -579,13 +902,176 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
   return MGRIT_OK;
 }
 
-static int build_sdirk(mgrit_handle* h, std::string* why) {
+// Build the SDIRK step parameters for K vectors per launch (the level-0
+// CF-intervals, or K = 1 for sequential stepping).  The geometry is the
+// fastest candidate measured on this handle's buffers (a warm-up plus two
+// timed launches of one step on up to 608 vectors; two steps of one vector
+// for sequential stepping) when `buffers` is set and tuning is on, else the
+// best-scored candidate; decisions are cached per (n_x, K, p, q, precision).
+static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
+                              double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
+                              std::string* why, bool buffers = false) {
+  SdirkParams<double> op;
+  BandFactor bf;
+  int rc = sdirk_operator(h, &op, &bf, why);
+  if (rc) return rc;
+  const int elem = outf ? 4 : 8;
+  auto smem_of = [&](const Geom& g) {
+    return sdirk_smem_bytes((int)(h->nx / g.C), g.P, g.nthr, op.nslots, elem);
+  };
+  std::vector<Geom> cand = chunk_geometries(h->nx, 1, elem, smem_of, 6);
+  if (cand.empty()) {
+    if (why) *why = "no SDIRK chunk geometry fits the vector";
+    return MGRIT_ERR_UNSUPPORTED;
+  }
+  const bool seq = (K == 1);
+  char keyb[160];
+  std::snprintf(keyb, sizeof(keyb), "sdirk:n=%lld:K=%lld:p=%d:q=%d:b=%d", (long long)h->nx, (long long)K,
+                h->prm.order_p, h->prm.rk_order_q, elem);
+  const std::string key(keyb);
+  Geom best = cand[0];
+  Geom cached;
+  int fc, fp;
+  const bool forced = geom_forced(&fc, &fp);
+  bool have = forced || geom_cached(key, &cached);
+  if (forced) cached = best;
+  if (have) {
+    have = false;
+    for (auto& g : cand)
+      if (g.C == cached.C && g.P == cached.P && g.nthr == cached.nthr) have = true;
+    if (have) best = cached;
+  }
+  if (!have && buffers && tuning_on() && cand.size() > 1) {
+    LevelData& L0 = h->lev[0];
+    const int64_t Kt = seq ? 1 : std::min<int64_t>(K, 608);
+    float bms = 1e30f;
+    for (auto& g : cand) {
+      if ((rc = sdirk_with_geom(h, op, bf, g, out, mt_dev, outf, mtf_dev))) return rc;
+      float ms;
+      if (outf) {
+        SdirkParams<float> sp = **outf;
+        sp.mode = seq ? kModeSEQ : kModeCF;
+        sp.zero_start = 0;
+        sp.start = L0.uCf[0];
+        sp.out = L0.uCf[1];
+        sp.rhs = nullptr;
+        sp.sub = nullptr;
+        sp.partial = nullptr;
+        sp.traj = nullptr;
+        sp.nsteps = seq ? 2 : 1;
+        sp.K = Kt;
+        ms = time_launches(h, [&]() { return launch_sdirk(sp, h->st); });
+      } else {
+        SdirkParams<double> sp = **out;
+        sp.mode = seq ? kModeSEQ : kModeCF;
+        sp.zero_start = 0;
+        sp.start = seq ? h->du0 : L0.uC[0];
+        sp.out = seq ? L0.uC[1 - L0.cur] : L0.uC[1];  // sequential: the scratch buffer
+        sp.rhs = nullptr;
+        sp.sub = nullptr;
+        sp.partial = nullptr;
+        sp.traj = nullptr;
+        sp.nsteps = seq ? 2 : 1;
+        sp.K = Kt;
+        ms = time_launches(h, [&]() { return launch_sdirk(sp, h->st); });
+      }
+      if (ms < 0.f) return MGRIT_ERR_CUDA;
+      if (ms < bms) {
+        bms = ms;
+        best = g;
+      }
+    }
+    geom_store(key, best);
+  }
+  return sdirk_with_geom(h, op, bf, best, out, mt_dev, outf, mtf_dev);
+}
+
+static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) {
   int rc = build_sdirk_params(h, h->lev[0].K, &h->sd0, h->sd_Mt,
-                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why);
+                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers);
   if (rc) return rc;
   h->sdirk = true;
   return MGRIT_OK;
 }
+
+// Measured geometry of level l (after the buffers exist): the candidate
+// that runs the level's main launch fastest -- CF relaxation of up to 608
+// intervals (m - 1 steps) on an intermediate level, sequential stepping
+// (up to 8 steps) on the coarsest -- in the precision the solve runs it
+// in; cached per (n_x, intervals, m, p, precision, solve precision).
+static int tune_coarse(mgrit_handle* h, int l) {
+  LevelData& Lv = h->lev[l];
+  const bool coarsest = (l == h->L - 1);
+  const bool f32 = h->mixed && !coarsest;
+  std::vector<GeomC> cand = coarse_geometries(h, 6);
+  int fc, fp;
+  if (cand.size() <= 1 || geom_forced(&fc, &fp)) return MGRIT_OK;
+  char keyb[160];
+  std::snprintf(keyb, sizeof(keyb), "coarse:n=%lld:K=%lld:N=%lld:m=%d:p=%d:b=%d:s=%d", (long long)h->nx,
+                (long long)Lv.K, (long long)(coarsest ? Lv.N : 0), h->m, h->prm.order_p, f32 ? 4 : 8,
+                f32 ? (Lv.solve64 ? 8 : 4) : 8);
+  const std::string key(keyb);
+  Geom cg;
+  GeomC best = cand[0];
+  if (geom_cached(key, &cg)) {
+    for (auto& g : cand)
+      if (g.C == cg.C && g.P == cg.P && g.nthr == cg.nthr) return coarse_with_geom(h, l, g);
+  }
+  if (!tuning_on()) return MGRIT_OK;
+  float bms = 1e30f;
+  for (auto& g : cand) {
+    int rc = coarse_with_geom(h, l, g);
+    if (rc) return rc;
+    float ms;
+    if (coarsest) {
+      CoarseParams<double> cp = Lv.cp;
+      cp.mode = kModeSEQ;
+      cp.zero_start = 1;
+      cp.start = nullptr;
+      cp.out = nullptr;
+      cp.sub = nullptr;
+      cp.partial = nullptr;
+      cp.g = Lv.g;
+      cp.nsteps = (int)std::min<int64_t>(Lv.N, 8);
+      cp.K = 1;
+      ms = time_launches(h, [&]() { return launch_coarse(cp, h->st); });
+    } else {
+      const int64_t Kt = std::min<int64_t>(Lv.K, 608);
+      auto fill = [&](auto& cp, auto* start, auto* out, auto* gg) {
+        cp.mode = kModeCF;
+        cp.zero_start = 0;
+        cp.start = start;
+        cp.out = out;
+        cp.sub = nullptr;
+        cp.partial = nullptr;
+        cp.g = gg;
+        cp.nsteps = h->m - 1;
+        cp.K = Kt;
+      };
+      if (!f32) {
+        CoarseParams<double> cp = Lv.cp;
+        fill(cp, Lv.uC[0], Lv.uC[1], Lv.g);
+        ms = time_launches(h, [&]() { return launch_coarse(cp, h->st); });
+      } else if (Lv.solve64) {
+        CoarseParams<float, double> cp = Lv.cpfd;
+        fill(cp, Lv.uCf[0], Lv.uCf[1], Lv.gf);
+        ms = time_launches(h, [&]() { return launch_coarse(cp, h->st); });
+      } else {
+        CoarseParams<float, float> cp = Lv.cpf;
+        fill(cp, Lv.uCf[0], Lv.uCf[1], Lv.gf);
+        ms = time_launches(h, [&]() { return launch_coarse(cp, h->st); });
+      }
+    }
+    if (ms < 0.f) return MGRIT_ERR_CUDA;
+    if (ms < bms) {
+      bms = ms;
+      best = g;
+    }
+  }
+  geom_store(key, Geom{best.C, best.P, best.nthr});
+  return coarse_with_geom(h, l, best);
+}
+
 
 
 
@@ -633,40 +1119,16 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
 // element size, rows) for the process and, if MGRIT_AUTOTUNE_CACHE names a
 // file, across processes.  MGRIT_AUTOTUNE=0 keeps the n_x-based default.
 // ---------------------------------------------------------------------------
-static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tune;
-static bool g_tune_loaded = false;
-
-static void tune_load() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
-  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
-  if (!f) return;
-  FILE* fp = std::fopen(f, "r");
-  if (!fp) return;
-  char key[128];
-  int r;
-  while (std::fscanf(fp, "%127s %d", key, &r) == 2) g_tune[key] = r;
-  std::fclose(fp);
-}
-
-static void tune_store(const std::string& key, int r) {
-  g_tune[key] = r;
-  const char* f = std::getenv("MGRIT_AUTOTUNE_CACHE");
-  if (!f) return;
-  FILE* fp = std::fopen(f, "a");
-  if (!fp) return;
-  std::fprintf(fp, "%s %d\n", key.c_str(), r);
-  std::fclose(fp);
-}
-
 template <typename T>
 static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out, int64_t rows) {
   const char* on = std::getenv("MGRIT_AUTOTUNE");
   if ((on && on[0] == '0') || rows <= 0) return MGRIT_OK;
+  // rows enter only through the wave count: bucket them by powers of two
+  int64_t rb = 1;
+  while (rb < rows) rb <<= 1;
   char keyb[128];
-  std::snprintf(keyb, sizeof(keyb), "stencil:nx=%lld:taps=%d:b=%d:rows=%lld", (long long)sp->nx, sp->ntaps,
-                (int)sizeof(T), (long long)rows);
+  std::snprintf(keyb, sizeof(keyb), "stencil:nx=%lld:taps=%d:b=%d:rows<=%lld", (long long)sp->nx, sp->ntaps,
+                (int)sizeof(T), (long long)rb);
   const std::string key(keyb);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1098,6 +1560,18 @@ static int build_solve_graph(mgrit_handle* h) {
   cudaGraph_t pro = nullptr;
   // capture on a private stream (the legacy default stream cannot capture);
   // the graph is later launched on the handle's stream
+  if (!h->dstate) {  // on the handle's stream, ordered before the sync below
+    static_assert(sizeof(DevSolveState) <= kPinBlock, "device state exceeds a pinned block");
+    if (dev_alloc(h, (void**)&h->dstate, sizeof(DevSolveState)) || !(h->hstate = (DevSolveState*)pinned_get())) {
+      h->prof.on = prof;
+      return MGRIT_ERR_OOM;
+    }
+    if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+      h->prof.on = prof;
+      note_cuda_error("cudaEventCreate", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+  }
   cudaStream_t user = h->st, cap = nullptr;
   if (cudaStreamSynchronize(user) != cudaSuccess ||
       cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1107,11 +1581,6 @@ static int build_solve_graph(mgrit_handle* h) {
   }
   h->st = cap;
   do {
-    if (!h->dstate) {
-      if (cudaMalloc((void**)&h->dstate, sizeof(DevSolveState)) != cudaSuccess) { rc = MGRIT_ERR_OOM; break; }
-      if (cudaMallocHost((void**)&h->hstate, sizeof(DevSolveState)) != cudaSuccess) { rc = MGRIT_ERR_OOM; break; }
-      if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) { rc = MGRIT_ERR_CUDA; break; }
-    }
     if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) { note_cuda_error("cudaGraphCreate", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     cudaGraphConditionalHandle hnd;
     if (cudaGraphConditionalHandleCreate(&hnd, h->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
@@ -1226,12 +1695,15 @@ const char* mgrit_strerror(int code) {
 
 int mgrit_destroy(mgrit_handle* h) {
   if (!h) return MGRIT_OK;
+  // a solve still in flight writes the pinned state block: let it land
+  // before the block is recycled
+  if (h->done) cudaEventSynchronize(h->done);
   for (auto& Lv : h->lev) {
-    cudaFree(Lv.uC[0]);
-    cudaFree(Lv.uC[1]);
-    cudaFree(Lv.g);
-    cudaFree(Lv.Mt_dev[0]);
-    cudaFree(Lv.Mt_dev[1]);
+    dev_free(h, Lv.uC[0]);
+    dev_free(h, Lv.uC[1]);
+    dev_free(h, Lv.g);
+    dev_free(h, Lv.Mt_dev[0]);
+    dev_free(h, Lv.Mt_dev[1]);
   }
   for (int c = 0; c < kProfCats; ++c)
     for (auto& pr : h->prof.ev[c]) {
@@ -1239,29 +1711,29 @@ int mgrit_destroy(mgrit_handle* h) {
       cudaEventDestroy(pr.second);
     }
   for (auto e : h->prof.pool) cudaEventDestroy(e);
-  cudaFree(h->sd_Mt[0]);
-  cudaFree(h->sd_Mt[1]);
-  cudaFree(h->sdf_Mt[0]);
-  cudaFree(h->sdf_Mt[1]);
-  cudaFree(h->sdseq_Mt[0]);
-  cudaFree(h->sdseq_Mt[1]);
+  dev_free(h, h->sd_Mt[0]);
+  dev_free(h, h->sd_Mt[1]);
+  dev_free(h, h->sdf_Mt[0]);
+  dev_free(h, h->sdf_Mt[1]);
+  dev_free(h, h->sdseq_Mt[0]);
+  dev_free(h, h->sdseq_Mt[1]);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->done) cudaEventDestroy(h->done);
-  cudaFree(h->dstate);
-  if (h->hstate) cudaFreeHost(h->hstate);
-  cudaFree(h->seq_tmp);
+  dev_free(h, h->dstate);
+  pinned_put(h->hstate);
+  dev_free(h, h->seq_tmp);
   for (auto& Lv : h->lev) {
-    cudaFree(Lv.uCf[0]);
-    cudaFree(Lv.uCf[1]);
-    cudaFree(Lv.gf);
-    cudaFree(Lv.Mtf_dev[0]);
-    cudaFree(Lv.Mtf_dev[1]);
+    dev_free(h, Lv.uCf[0]);
+    dev_free(h, Lv.uCf[1]);
+    dev_free(h, Lv.gf);
+    dev_free(h, Lv.Mtf_dev[0]);
+    dev_free(h, Lv.Mtf_dev[1]);
   }
-  cudaFree(h->partials);
-  cudaFree(h->dnorm);
-  cudaFree(h->du0);
-  if (h->hnorm) cudaFreeHost(h->hnorm);
+  dev_free(h, h->partials);
+  dev_free(h, h->dnorm);
+  dev_free(h, h->du0);
+  pinned_put(h->hnorm);
   delete h;
   return MGRIT_OK;
 }
@@ -1361,13 +1833,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   }
   // buffers
   const size_t row = sizeof(double) * (size_t)P.nx;
-  auto alloc = [&](double** p, size_t bytes) -> int {
-    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return MGRIT_ERR_OOM;
-    }
-    return MGRIT_OK;
-  };
+  auto alloc = [&](double** p, size_t bytes) -> int { return dev_alloc(h.get(), (void**)p, bytes); };
   for (int l = 0; l < L; ++l) {
     LevelData& Lv = h->lev[l];
     if (l < L - 1) {
@@ -1385,10 +1851,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     h->mixed = true;
     const size_t rowf = sizeof(float) * (size_t)P.nx;
     auto allocf = [&](float** p, size_t bytes) -> int {
-      if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return MGRIT_ERR_OOM;
-      }
+      if (dev_alloc(h.get(), (void**)p, bytes)) return MGRIT_ERR_OOM;
       return cudaMemsetAsync(*p, 0, bytes, h->st) == cudaSuccess ? MGRIT_OK : MGRIT_ERR_CUDA;
     };
     for (int l = 0; l < L; ++l) {
@@ -1402,17 +1865,36 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     }
     if ((rc = alloc(&h->seq_tmp, row * (h->lev[L - 1].N + 1)))) return rc;
   }
-  h->npart = h->lev[0].K * std::max<int64_t>(stencil_tiles(P.nx, 1), h->sdirk ? h->sd0->csize : 1) + 1;
-  for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * h->lev[l].cp.csize);
+  // partial sums: one per CTA of any launch (tile count of the stencil at
+  // its smallest tile, clusters of up to 16 CTAs for the step kernels)
+  h->npart = h->lev[0].K * std::max<int64_t>(stencil_tiles(P.nx, 1), 16) + 1;
+  for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * 16);
   if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
   if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
   if ((rc = alloc(&h->du0, row))) return rc;
   CUDA_TRY(cudaMemsetAsync(h->du0, 0, row, h->st));
-  if (cudaMallocHost((void**)&h->hnorm, sizeof(double)) != cudaSuccess) return MGRIT_ERR_OOM;
-  if (!h->sdirk) {  // tile of the level-0 composite stencil (on the C-point buffers)
-    LevelData& L0 = h->lev[0];
+  if (!(h->hnorm = (double*)pinned_get())) return MGRIT_ERR_OOM;
+  // measured launch geometries on this handle's buffers (cached per shape):
+  // the level-0 stencil tile or SDIRK chunk geometry, each coarse level's
+  LevelData& L0 = h->lev[0];
+  if (!h->sdirk) {
     if ((rc = autotune_stencil(h.get(), h->fineM.get(), L0.uC[0], L0.uC[1], L0.K))) return rc;
     if (h->mixed && (rc = autotune_stencil(h.get(), h->fineMf.get(), L0.uCf[0], L0.uCf[1], L0.K))) return rc;
+  } else {
+    std::string why0;
+    if ((rc = build_sdirk(h.get(), &why0, true))) return rc;
+  }
+  for (int l = 1; l < L; ++l)
+    if ((rc = tune_coarse(h.get(), l))) return rc;
+  // the timing launches wrote into the level buffers: back to zero
+  for (int l = 0; l < L; ++l) {
+    LevelData& Lv = h->lev[l];
+    for (int b = 0; b < 2; ++b) {
+      if (Lv.uC[b]) CUDA_TRY(cudaMemsetAsync(Lv.uC[b], 0, row * (Lv.K + 1), h->st));
+      if (Lv.uCf[b]) CUDA_TRY(cudaMemsetAsync(Lv.uCf[b], 0, sizeof(float) * P.nx * (Lv.K + 1), h->st));
+    }
+    if (Lv.g) CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
+    if (Lv.gf) CUDA_TRY(cudaMemsetAsync(Lv.gf, 0, sizeof(float) * P.nx * ((l == 0 ? Lv.K : Lv.N) + 1), h->st));
   }
   CUDA_TRY(cudaStreamSynchronize(h->st));
   *out = h.release();
@@ -1652,7 +2134,7 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
     if (nsteps > INT32_MAX) return MGRIT_ERR_INVALID_ARG;
     if (!h->sdseq) {
       std::string why;
-      rc = build_sdirk_params(h, 1, &h->sdseq, h->sdseq_Mt, nullptr, nullptr, &why);
+      rc = build_sdirk_params(h, 1, &h->sdseq, h->sdseq_Mt, nullptr, nullptr, &why, true);
       if (rc) return rc;
     }
     rc = sdirk_launch(h, kModeSEQ, 0, h->du0, dout, nullptr, (int)nsteps, 1, every > 0 ? traj : nullptr,
@@ -1735,7 +2217,12 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   const LevelData& Lv = h->lev[level];
   out[0] = (double)Lv.N;
   if (level == 0) {
-    out[5] = (double)h->fineM->ntaps;
+    if (h->sdirk) {
+      out[6] = (double)h->sd0->P;
+      out[7] = (double)h->sd0->csize;
+    } else {
+      out[5] = (double)h->fineM->ntaps;
+    }
     return MGRIT_OK;
   }
   out[1] = (double)Lv.kshift;

@@ -37,29 +37,43 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 
+// Barrier over every thread that shares the vector: the CTA, or the whole
+// thread-block cluster when the vector is split over C > 1 CTAs (also makes
+// the shared-memory writes before it visible to the cluster).
+__device__ __forceinline__ void vec_sync(int C) {
+  if (C == 1)
+    __syncthreads();
+  else
+    cgc::this_cluster().sync();
+}
+
 // Inclusive prefix of chunk states inside the CTA in direction dir (-1: from
 // lower chunks, +1: from higher chunks).  Rounds at distances < 32 run on
 // warp shuffles; the carry from other warps comes from one exchange of warp
 // totals through shared memory (sw), combined with the host tables
 // (M^32)^j and M^d.  On return Q is this chunk's prefix and the CTA-end lane
 // of every warp has written its prefix to sq[w*3 + a] (read by chunk_carry
-// after the caller's cluster barrier).
+// after the caller's barrier).
 template <int H, typename T>
 __device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, T* sw, int t, int NT, int dir) {
   const int lane = t & 31, w = t >> 5, nw = (NT + 31) >> 5;
   const int wlen = min(32, NT - (w << 5));
   const unsigned mask = (wlen == 32) ? 0xffffffffu : ((1u << wlen) - 1u);
-  for (int r = 0; r < D.rounds && r < 5; ++r) {
-    const int d = 1 << r;
-    T Qo[H];
 #pragma unroll
-    for (int a = 0; a < H; ++a) Qo[a] = dir < 0 ? __shfl_up_sync(mask, Q[a], d) : __shfl_down_sync(mask, Q[a], d);
-    const bool ok = dir < 0 ? (lane >= d) : (lane + d < wlen);
-    if (ok) {
+  for (int r = 0; r < 5; ++r) {
+    if (r < D.rounds) {
+      const int d = 1 << r;
+      T Qo[H];
 #pragma unroll
       for (int a = 0; a < H; ++a)
+        Qo[a] = dir < 0 ? __shfl_up_sync(mask, Q[a], d) : __shfl_down_sync(mask, Q[a], d);
+      const bool ok = dir < 0 ? (lane >= d) : (lane + d < wlen);
+      if (ok) {
 #pragma unroll
-        for (int q = 0; q < H; ++q) Q[a] = fma(D.Mpow[r][a * 3 + q], Qo[q], Q[a]);
+        for (int a = 0; a < H; ++a)
+#pragma unroll
+          for (int q = 0; q < H; ++q) Q[a] = fma(D.Mpow[r][a * 3 + q], Qo[q], Q[a]);
+      }
     }
   }
   const int end_lane = dir < 0 ? wlen - 1 : 0;
@@ -71,21 +85,21 @@ __device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, 
     __syncthreads();
     const int dd = dir < 0 ? lane + 1 : wlen - lane;  // chunks from the warp edge, 1..32
     if (dd <= D.dcut) {
-    T X[H];
+      T X[H];
 #pragma unroll
-    for (int a = 0; a < H; ++a) X[a] = T(0);
-    for (int j = 1; j <= D.wterms; ++j) {
-      const int v = w + dir * j;
-      if (v < 0 || v >= nw) break;
+      for (int a = 0; a < H; ++a) X[a] = T(0);
+      for (int j = 1; j <= D.wterms; ++j) {
+        const int v = w + dir * j;
+        if (v < 0 || v >= nw) break;
+#pragma unroll
+        for (int a = 0; a < H; ++a)
+#pragma unroll
+          for (int q = 0; q < H; ++q) X[a] = fma(D.M32pow[j - 1][a * 3 + q], sw[v * 3 + q], X[a]);
+      }
 #pragma unroll
       for (int a = 0; a < H; ++a)
 #pragma unroll
-        for (int q = 0; q < H; ++q) X[a] = fma(D.M32pow[j - 1][a * 3 + q], sw[v * 3 + q], X[a]);
-    }
-#pragma unroll
-    for (int a = 0; a < H; ++a)
-#pragma unroll
-      for (int q = 0; q < H; ++q) Q[a] = fma(D.Mlane[dd - 1][a * 3 + q], X[q], Q[a]);
+        for (int q = 0; q < H; ++q) Q[a] = fma(D.Mlane[dd - 1][a * 3 + q], X[q], Q[a]);
     }
   }
   if (lane == end_lane) {
@@ -98,11 +112,10 @@ __device__ __forceinline__ void hs_scan(T (&Q)[H], const SolveDir<T>& D, T* sq, 
 // chunk's prefix (a shuffle inside the warp, sq across warps) plus
 // M^{tdist} X, X the cluster-level carry into the CTA.  `agg` is this CTA's
 // cluster-visible aggregate slot (H values), published and synchronised by
-// the caller; Mt holds M^{tdist} (zero when negligible) for this thread.
+// the caller; M^{tdist} comes from the device table D.Mt (zero beyond tcut).
 template <int H, typename T>
 __device__ __forceinline__ void chunk_carry(T (&S)[H], const T (&Q)[H], const SolveDir<T>& D, const T* sq,
-                                            T* agg, const T (&Mt)[9], int t, int NT, int dir, int rank, int C) {
-  cgc::cluster_group cl = cgc::this_cluster();
+                                            T* agg, int t, int NT, int dir, int rank, int C) {
   const int lane = t & 31, w = t >> 5;
   const int wlen = min(32, NT - (w << 5));
   const unsigned mask = (wlen == 32) ? 0xffffffffu : ((1u << wlen) - 1u);
@@ -123,9 +136,11 @@ __device__ __forceinline__ void chunk_carry(T (&S)[H], const T (&Q)[H], const So
       for (int a = 0; a < H; ++a) S[a] = Qs[a];
     }
   }
+  if (tdist >= D.tcut) return;  // the cluster-level carry has decayed below 1e-18 here
   T X[H];
 #pragma unroll
   for (int a = 0; a < H; ++a) X[a] = T(0);
+  cgc::cluster_group cl = cgc::this_cluster();
   for (int j = 0; j < D.jterms; ++j) {
     int src = rank + dir * (1 + j);
     src %= C;
@@ -151,85 +166,61 @@ __device__ __forceinline__ void chunk_carry(T (&S)[H], const T (&Q)[H], const So
 #pragma unroll
     for (int a = 0; a < H; ++a) X[a] = Y[a];
   }
+  const T* Mt = D.Mt + (size_t)tdist * 9;
 #pragma unroll
   for (int a = 0; a < H; ++a)
 #pragma unroll
-    for (int q = 0; q < H; ++q) S[a] = fma(Mt[a * 3 + q], X[q], S[a]);
+    for (int q = 0; q < H; ++q) S[a] = fma(__ldg(Mt + a * 3 + q), X[q], S[a]);
 }
 
-// M^{tdist} of this thread for direction dir (zero when below the cut).
-template <typename T>
-__device__ __forceinline__ void load_carry_power(T (&Mt)[9], const SolveDir<T>& D, int t, int NT, int dir) {
-  const int tdist = (dir < 0) ? t : (NT - 1 - t);
-  if (tdist < D.tcut) {
-    const T* p = D.Mt + (size_t)tdist * 9;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Mt[i] = __ldg(p + i);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Mt[i] = T(0);
-  }
-}
-
-// Periodic banded solve of the thread's chunk x (registers) in place: causal
-// recurrence, carry, fixup fused with the anticausal local pass, carry,
-// fixup.  Every thread of every CTA of the cluster must call it.
-template <int HC, int HA, typename T, int PM, typename Prm>
-__device__ __forceinline__ void banded_solve(T (&x)[PM], const Prm& A, T* sqc, T* sqa, T* aggc, T* agga,
-                                             const T (&Mtc)[9], const T (&Mta)[9], int t, int rank) {
-  cgc::cluster_group cl = cgc::this_cluster();
-  const int P = A.P, NT = A.nthr, C = A.csize;
+// Periodic banded solve of the thread's chunk x (P values in registers, P a
+// compile-time chunk length) in place: causal local recurrence, carry,
+// fix-up; anticausal local recurrence, carry, fix-up.  Every thread of every
+// CTA sharing the vector must call it (C = CTAs per vector).
+template <int HC, int HA, typename T, int P, typename Prm>
+__device__ __forceinline__ void banded_solve(T (&x)[P], const Prm& A, T* sqc, T* sqa, T* aggc, T* agga, int t,
+                                             int rank, int C) {
+  const int NT = A.nthr;
   if constexpr (HC > 0) {
-    T Q[HC > 0 ? HC : 1];
+    // x_j -= sum_q c_q x_{j-q}, oldest term first: the newest value enters
+    // through the last FMA only
 #pragma unroll
-    for (int a = 0; a < HC; ++a) Q[a] = T(0);
+    for (int j = 0; j < P; ++j) {
+      T v = x[j];
 #pragma unroll
-    for (int j = 0; j < PM; ++j) {
-      if (j < P) {
-        T v = x[j];
-#pragma unroll
-        for (int q = 1; q <= HC; ++q)
-          if (j - q >= 0) v = fma(A.c.ncoef[q - 1], x[j - q], v);
-        x[j] = v;
-#pragma unroll
-        for (int a = 0; a < HC; ++a)
-          if (j == P - 1 - a) Q[a] = v;
-      }
+      for (int q = HC; q >= 1; --q)
+        if (j - q >= 0) v = fma(A.c.ncoef[q - 1], x[j - q], v);
+      x[j] = v;
     }
+    T Q[HC];
+#pragma unroll
+    for (int a = 0; a < HC; ++a) Q[a] = x[P - 1 - a];
     hs_scan<HC>(Q, A.c, sqc, sqc + 24, t, NT, -1);
     if (t == NT - 1) {
 #pragma unroll
       for (int a = 0; a < HC; ++a) aggc[a] = Q[a];
     }
-    cl.sync();
-    T S[HC > 0 ? HC : 1];
-    chunk_carry<HC>(S, Q, A.c, sqc, aggc, Mtc, t, NT, -1, rank, C);
+    vec_sync(C);
+    T S[HC];
+    chunk_carry<HC>(S, Q, A.c, sqc, aggc, t, NT, -1, rank, C);
 #pragma unroll
-    for (int j = 0; j < PM; ++j) {
-      if (j < P) {
-        T v = x[j];
+    for (int j = 0; j < P; ++j) {
+      T v = x[j];
 #pragma unroll
-        for (int q = 0; q < HC; ++q) v = fma(A.c.G[j * 3 + q], S[q], v);
-        x[j] = v;
-      }
+      for (int q = 0; q < HC; ++q) v = fma(A.c.G[j * 3 + q], S[q], v);
+      x[j] = v;
     }
   }
   if constexpr (HA > 0) {
-    T Q[HA > 0 ? HA : 1];
 #pragma unroll
-    for (int a = 0; a < HA; ++a) Q[a] = T(0);
+    for (int j = P - 1; j >= 0; --j) {
+      T v = x[j];
 #pragma unroll
-    for (int j = PM - 1; j >= 0; --j) {
-      if (j < P) {
-        T v = x[j];
-#pragma unroll
-        for (int q = 1; q <= HA; ++q)
-          if (j + q < PM) {
-            if (j + q < P) v = fma(A.a.ncoef[q - 1], x[j + q], v);
-          }
-        x[j] = v;
-      }
+      for (int q = HA; q >= 1; --q)
+        if (j + q < P) v = fma(A.a.ncoef[q - 1], x[j + q], v);
+      x[j] = v;
     }
+    T Q[HA];
 #pragma unroll
     for (int a = 0; a < HA; ++a) Q[a] = x[a];
     hs_scan<HA>(Q, A.a, sqa, sqa + 24, t, NT, +1);
@@ -237,21 +228,17 @@ __device__ __forceinline__ void banded_solve(T (&x)[PM], const Prm& A, T* sqc, T
 #pragma unroll
       for (int a = 0; a < HA; ++a) agga[a] = Q[a];
     }
-    cl.sync();
-    T S[HA > 0 ? HA : 1];
-    chunk_carry<HA>(S, Q, A.a, sqa, agga, Mta, t, NT, +1, rank, C);
+    vec_sync(C);
+    T S[HA];
+    chunk_carry<HA>(S, Q, A.a, sqa, agga, t, NT, +1, rank, C);
 #pragma unroll
-    for (int j = 0; j < PM; ++j) {
-      if (j < P) {
-        const int d = P - 1 - j;
-        T v = x[j];
+    for (int j = 0; j < P; ++j) {
+      T v = x[j];
 #pragma unroll
-        for (int q = 0; q < HA; ++q) v = fma(A.a.G[d * 3 + q], S[q], v);
-        x[j] = v;
-      }
+      for (int q = 0; q < HA; ++q) v = fma(A.a.G[(P - 1 - j) * 3 + q], S[q], v);
+      x[j] = v;
     }
   }
 }
-
 
 }  // namespace mg

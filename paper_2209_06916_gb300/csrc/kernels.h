@@ -113,12 +113,15 @@ constexpr int kSdirkMaxSlots = 5;
 template <typename T>
 struct SdirkParams {
   int n, P, nthr, csize, npc;
-  int p1, llo;         // L_p taps at offsets llo .. llo + p1 - 1
+  int p1, llo;         // L_p taps at offsets llo = -p1/2 .. llo + p1 - 1
   T ltaps[8];
   SolveDir<T> c, a;    // factored stage matrix (I + gamma c L_p)
   T sscale;            // 1/kappa of the factorisation (applied before a solve)
   int nops, nslots, result;
   int opk[kSdirkMaxOps], opd[kSdirkMaxOps], ops[kSdirkMaxOps];
+  int opg[kSdirkMaxOps];   // AXPYL group head: number of consecutive AXPYL ops on the same src (else 1)
+  int opb[kSdirkMaxOps];   // 1: barrier over the vector's threads before the op (halo hazards)
+  int resb;                // barrier before the end-of-step copy result -> slot 0
   T opc[kSdirkMaxOps];
   int mode;            // kModeCF, kModeFRES, kModeAPPLY, kModeSEQ
   int zero_start, nsteps;
@@ -132,6 +135,11 @@ struct SdirkParams {
   int every;
 };
 size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem);
+// Chunk lengths the step kernels are compiled for (one chunk per thread).
+constexpr int kChunkLens[3] = {8, 16, 32};
+// Largest co-schedulable cluster size <= want (power of two) for a CTA of
+// nthr threads and smem bytes of dynamic shared memory.
+int sdirk_max_cluster(int want, size_t smem, int nthr);
 int launch_sdirk(const SdirkParams<double>& p, cudaStream_t st);
 int launch_sdirk(const SdirkParams<float>& p, cudaStream_t st);
 int launch_coarse(const CoarseParams<double>& p, cudaStream_t st);

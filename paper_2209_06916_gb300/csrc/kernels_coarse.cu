@@ -16,39 +16,74 @@
 
 namespace mg {
 
-template <typename T, typename TC, int PM, int P1>
+template <int P>
+struct Log2c {
+  static constexpr int v = (P <= 1) ? 0 : 1 + Log2c<P / 2>::v;
+};
+template <>
+struct Log2c<1> {
+  static constexpr int v = 0;
+};
+
+// One step's SL gather for the thread's chunk: x_j = sum_a w_a v(g0 + j + a),
+// the window g0 .. g0 + P + P1 - 2 starting at local index l0 of CTA `b0`
+// and running into CTA `b1` past npc (b0 == b1 and a wrap for one CTA).
+template <typename T, typename TC, int P, int P1, int LP>
+__device__ __forceinline__ void sl_gather(TC (&x)[P], const T* b0, const T* b1, int l0, int npc, const T* w) {
+  auto val = [&](int l) -> T {
+    if (l < npc) return b0[l + (l >> LP)];
+    l -= npc;
+    return b1[l + (l >> LP)];
+  };
+  T win[P1];
+#pragma unroll
+  for (int a = 0; a < P1 - 1; ++a) win[a] = val(l0 + a);
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    win[P1 - 1] = val(l0 + j + P1 - 1);
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < P1; ++a) acc = fma(w[a], win[a], acc);
+    x[j] = (TC)acc;
+#pragma unroll
+    for (int a = 0; a < P1 - 1; ++a) win[a] = win[a + 1];
+  }
+}
+
+template <typename T, typename TC, int P, int P1>
 __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ CoarseParams<T, TC> A) {
   constexpr int H = P1 / 2;
+  constexpr int LP = Log2c<P>::v;
+  static_assert((1 << LP) == P, "chunk length must be a power of two");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cgc::cluster_group cl = cgc::this_cluster();
-  const int n = A.n, P = A.P, NT = A.nthr, C = A.csize, npc = A.npc, t = threadIdx.x;
+  const int n = A.n, NT = A.nthr, C = A.csize, npc = A.npc, t = threadIdx.x;
   const int rank = (int)cl.block_rank();
-  const int npad = npc + (npc + P - 1) / P;
-  T* sv0 = reinterpret_cast<T*>(smem_raw);
-  T* sv1 = sv0 + npad;
+  const int npad = NT * (P + 1);  // one padded chunk of P + 1 per thread
+  T* const sv0 = reinterpret_cast<T*>(smem_raw);
+  T* const sv1 = sv0 + npad;
   // RHS row: row s+1 is fetched (cp.async) into it as soon as the cluster
   // barrier after step s has retired its last reader, and lands while step
   // s+1 gathers and solves
-  T* sg = sv1 + npad;
-  // scan buffers of the solve precision, 16-byte aligned after the slots
-  size_t slot_bytes = (((size_t)3 * npad * sizeof(T)) + 15) & ~(size_t)15;
-  const int SQ = max(6 * NT, 48);
+  T* const sg = sv1 + npad;
+  const size_t slot_bytes = (((size_t)3 * npad * sizeof(T)) + 15) & ~(size_t)15;
   TC* sqc = reinterpret_cast<TC*>(smem_raw + slot_bytes);
-  TC* sqa = sqc + SQ;
-  TC* aggc = sqa + SQ;
+  TC* sqa = sqc + 48;
+  TC* aggc = sqa + 48;
   TC* agga = aggc + 4;
-  double* red = reinterpret_cast<double*>(agga + 4);
+  double* red = reinterpret_cast<double*>(smem_raw + slot_bytes + ((104 * sizeof(TC) + 15) & ~(size_t)15));
   const int64_t k = blockIdx.x / C;
   const int64_t nn = n;
   const int64_t off = (int64_t)rank * npc;  // first global point of this CTA
-  T* cur = sv0;
-  T* nxt = sv1;
+  const int base = t * (P + 1);
+  auto pos = [](int i) { return i + (i >> LP); };
+  int cur = 0;
 
   if (A.zero_start) {
-    for (int i = t; i < npc; i += NT) cur[i + i / P] = T(0);
+    for (int i = t; i < npc; i += NT) sv0[pos(i)] = T(0);
   } else {
     const T* src = A.start + k * nn + off;
-    for (int i = t; i < npc; i += NT) cur[i + i / P] = src[i];
+    for (int i = t; i < npc; i += NT) sv0[pos(i)] = src[i];
   }
   if (A.mode == kModeFOUT) {
     // the C-points themselves go to RHS row k m (and the last CTA's
@@ -63,95 +98,71 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
     }
   }
   const int64_t gbase = (A.mode == kModeSEQ) ? 0 : k * A.m;
-  auto prefetch = [&](int s, T* dst) {
+  auto prefetch = [&](int s) {
     const T* gr = A.g + (gbase + s) * nn + off;
-    for (int i = t; i < npc; i += NT) __pipeline_memcpy_async(&dst[i + i / P], &gr[i], sizeof(T));
+    for (int i = t; i < npc; i += NT) __pipeline_memcpy_async(&sg[pos(i)], &gr[i], sizeof(T));
     __pipeline_commit();
   };
-  if (A.g && A.nsteps >= 1) prefetch(1, sg);
-  cl.sync();
-
-  TC mtc[9], mta[9];
-  load_carry_power(mtc, A.c, t, NT, -1);
-  load_carry_power(mta, A.a, t, NT, +1);
-  // SL gather window of this thread: global indices gw0 + w, w < P + P1 - 1
+  if (A.g && A.nsteps >= 1) prefetch(1);
+  // departure window of this thread: global points gw0 .. gw0 + P + P1 - 2
   int gw0 = (int)((off + (int64_t)t * P - A.kshift + A.jlo) % nn);
   if (gw0 < 0) gw0 += n;
+  const int r0 = gw0 / npc, l0 = gw0 - r0 * npc, r1 = (r0 + 1) % C;
+  // the window's two CTAs, for either state slot (generic addresses)
+  const T* const w00 = cl.map_shared_rank(sv0, r0);
+  const T* const w01 = cl.map_shared_rank(sv1, r0);
+  const T* const w10 = cl.map_shared_rank(sv0, r1);
+  const T* const w11 = cl.map_shared_rank(sv1, r1);
+  vec_sync(C);
 
   for (int s = 1; s <= A.nsteps; ++s) {
-    TC x[PM];
+    TC x[P];
     if (s == 1 && A.zero_start) {
 #pragma unroll
-      for (int j = 0; j < PM; ++j) x[j] = TC(0);
-      __syncthreads();
+      for (int j = 0; j < P; ++j) x[j] = TC(0);
     } else {
-      T win[P1];
-      auto fetch = [&](int w) -> T {
-        int gi = gw0 + w;
-        if (gi >= n) gi -= n;
-        if (gi >= n) gi -= n;
-        if (C == 1) return cur[gi + gi / P];
-        const int owner = gi / npc;
-        const int li = gi - owner * npc;
-        const T* base = cl.map_shared_rank(cur, owner);
-        return base[li + li / P];
-      };
-#pragma unroll
-      for (int a = 0; a < P1 - 1; ++a) win[a] = fetch(a);
-#pragma unroll
-      for (int j = 0; j < PM; ++j) {
-        if (j < P) {
-          win[P1 - 1] = fetch(j + P1 - 1);
-          T acc = T(0);
-#pragma unroll
-          for (int a = 0; a < P1; ++a) acc = fma(A.w[a], win[a], acc);
-          x[j] = (TC)acc;
-#pragma unroll
-          for (int a = 0; a < P1 - 1; ++a) win[a] = win[a + 1];
-        }
+      if (C == 1) {
+        const T* v = cur ? sv1 : sv0;
+        sl_gather<T, TC, P, P1, LP>(x, v, v, l0, npc, A.w);
+      } else {
+        sl_gather<T, TC, P, P1, LP>(x, cur ? w01 : w00, cur ? w11 : w10, l0, npc, A.w);
       }
-      __syncthreads();
-      banded_solve<H, H, TC, PM>(x, A, sqc, sqa, aggc, agga, mtc, mta, t, rank);
+      banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
     }
     if (A.g) {  // this step's RHS row has landed (for every thread)
       __pipeline_wait_prior(0);
       __syncthreads();
     }
-    // new state v_{i - shift} = x_i + g (the shift stays inside this CTA's
-    // range for the symmetric factorisation: shift = 0)
+    T* nxt = (cur ? sv0 : sv1) + base;
 #pragma unroll
-    for (int j = 0; j < PM; ++j) {
-      if (j < P) {
-        int i2 = t * P + j - A.shift;
-        if (i2 < 0) i2 += npc;
-        T v = (T)x[j];
-        if (A.g) v += sg[i2 + i2 / P];
-        nxt[i2 + i2 / P] = v;
-      }
+    for (int j = 0; j < P; ++j) {
+      T v = (T)x[j];
+      if (A.g) v += sg[base + j];
+      nxt[j] = v;
     }
-    cl.sync();
-    if (A.g && s + 1 <= A.nsteps) prefetch(s + 1, sg);
-    T* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
+    vec_sync(C);
+    if (A.g && s + 1 <= A.nsteps) prefetch(s + 1);
+    cur ^= 1;
     if (A.mode == kModeFOUT || A.mode == kModeSEQ) {  // store only: no read on the critical path
       T* gr = A.g + (gbase + s) * nn + off;
-      for (int i = t; i < npc; i += NT) gr[i] = cur[i + i / P];
+      const T* v = cur ? sv1 : sv0;
+      for (int i = t; i < npc; i += NT) gr[i] = v[pos(i)];
     }
   }
 
+  const T* fin = cur ? sv1 : sv0;
   if (A.mode == kModeCF) {
     T* o = A.out + (k + 1) * nn + off;
-    for (int i = t; i < npc; i += NT) o[i] = cur[i + i / P];
+    for (int i = t; i < npc; i += NT) o[i] = fin[pos(i)];
   } else if (A.mode == kModeAPPLY) {
     T* o = A.out + k * nn + off;
-    for (int i = t; i < npc; i += NT) o[i] = cur[i + i / P];
+    for (int i = t; i < npc; i += NT) o[i] = fin[pos(i)];
   } else if (A.mode == kModeFRES) {
     T* o = A.out + (k + 1) * nn + off;
     const T* sb = A.sub ? A.sub + (k + 1) * nn + off : nullptr;
     double sq = 0.0;
     for (int i = t; i < npc; i += NT) {
-      T r = cur[i + i / P];
+      T r = fin[pos(i)];
       if (sb) r -= sb[i];
       o[i] = r;
       sq += (double)r * (double)r;
@@ -163,29 +174,29 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   }
   // keep this CTA's shared memory alive until the cluster has finished its
   // remote reads of it
-  cl.sync();
+  if (C > 1) cl.sync();
 }
 
 size_t coarse_smem_bytes(int npc, int P, int nthr, int elem) {
   // slots of `elem` bytes; scan buffers budgeted at 8 bytes (FP64 solve)
-  size_t npad = (size_t)npc + (size_t)((npc + P - 1) / P);
-  const size_t sq = std::max<size_t>(6 * (size_t)nthr, 48);
-  return ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + (2 * sq + 8) * 8 + 32 * sizeof(double) + 16;
+  (void)npc;
+  const size_t npad = (size_t)nthr * (size_t)(P + 1);
+  return ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + ((104 * 8 + 15) & ~(size_t)15) + 32 * sizeof(double);
 }
 
-template <typename T, typename TC, int PM, int P1>
+template <typename T, typename TC, int P, int P1>
 static void configure_coarse() {
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(coarse_kernel<T, TC, PM, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(coarse_kernel<T, TC, PM, P1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     configured = true;
   }
 }
 
-template <typename T, typename TC, int PM, int P1>
+template <typename T, typename TC, int P, int P1>
 static int launch_coarse_t(const CoarseParams<T, TC>& A, cudaStream_t st) {
-  configure_coarse<T, TC, PM, P1>();
+  configure_coarse<T, TC, P, P1>();
   if (A.K <= 0) return 0;
   size_t smem = coarse_smem_bytes(A.npc, A.P, A.nthr, (int)sizeof(T));
   cudaLaunchConfig_t cfg = {};
@@ -200,14 +211,21 @@ static int launch_coarse_t(const CoarseParams<T, TC>& A, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, coarse_kernel<T, TC, PM, P1>, A) == cudaSuccess ? 1 : -1;
+  return cudaLaunchKernelEx(&cfg, coarse_kernel<T, TC, P, P1>, A) == cudaSuccess ? 1 : -1;
 }
 
 template <typename T, typename TC, int P1>
 static int launch_coarse_p(const CoarseParams<T, TC>& A, cudaStream_t st) {
-  if (A.P <= 16) return launch_coarse_t<T, TC, 16, P1>(A, st);
-  if (A.P <= 32) return launch_coarse_t<T, TC, 32, P1>(A, st);
-  return launch_coarse_t<T, TC, 64, P1>(A, st);
+  switch (A.P) {
+    case 8:
+      return launch_coarse_t<T, TC, 8, P1>(A, st);
+    case 16:
+      return launch_coarse_t<T, TC, 16, P1>(A, st);
+    case 32:
+      return launch_coarse_t<T, TC, 32, P1>(A, st);
+    default:
+      return -1;
+  }
 }
 
 template <typename T, typename TC>
@@ -230,7 +248,7 @@ int launch_coarse(const CoarseParams<float, double>& p, cudaStream_t st) { retur
 
 // Largest cluster size <= want (power of two) that can be co-scheduled.
 int coarse_max_cluster(int want, size_t smem, int nthr) {
-  configure_coarse<double, double, 32, 4>();
+  configure_coarse<double, double, 16, 4>();
   for (int c = want; c >= 1; c >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c);
@@ -244,7 +262,7 @@ int coarse_max_cluster(int want, size_t smem, int nthr) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, coarse_kernel<double, double, 32, 4>, &cfg) == cudaSuccess && nc > 0)
+    if (cudaOccupancyMaxActiveClusters(&nc, coarse_kernel<double, double, 16, 4>, &cfg) == cudaSuccess && nc > 0)
       return c;
     cudaGetLastError();
   }
