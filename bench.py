@@ -241,6 +241,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision sub-measurement")
     ap.add_argument("--nt", type=int, default=0, help="override n_t of c1-c3 (small profiling cases)")
     ap.add_argument("--no-sequential", action="store_true", help="skip the sequential-stepping baseline")
+    ap.add_argument("--precision", default="", choices=["", "fp64", "mixed"], help="override the workload's")
+    ap.add_argument("--inner", type=int, default=0, help="MIXED: FP32 V-cycles per FP64 residual (0: library default)")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload == "c4" and args.impl == "ours":
@@ -268,6 +270,8 @@ def main():
         w["name"] += "_nt%d" % args.nt
         while w["levels"] > 2 and args.nt % (w["m"] ** (w["levels"] - 1)):
             w["levels"] -= 1
+    if args.precision:
+        w["precision"] = args.precision
     nx, nt, m = w["nx"], w["nt"], w["m"]
     stream = torch.cuda.current_stream()
     kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
@@ -276,6 +280,8 @@ def main():
     def make(precision):
         prm = pkg.make_params(nx, nt, w["cfl"], w["p"], kind=kind, q=w["q"], m=m, levels=w["levels"], nu=w["nu"],
                               tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=precision)
+        if args.inner > 0:
+            prm.inner_cycles = args.inner
         return pkg.Solver(prm, stream=stream.cuda_stream)
 
     s = make(prec)

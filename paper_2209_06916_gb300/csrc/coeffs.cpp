@@ -522,7 +522,7 @@ static double mat3_norm(const double* a) {
   return n;
 }
 
-DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) {
+DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C, double tol) {
   DistScanTables d;
   d.h = h;
   ScanTables base = scan_tables(coef, h, P, 1);  // G only
@@ -535,7 +535,7 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
   double pw[9];
   for (int i = 0; i < 9; ++i) pw[i] = M[i];
   for (int r = 0; (1 << r) < T; ++r) {
-    if (mat3_norm(pw) < 1e-18) break;
+    if (mat3_norm(pw) < tol) break;
     d.Mpow.insert(d.Mpow.end(), pw, pw + 9);
     ++d.rounds;
     mat3_mul(pw, pw, pw);
@@ -544,7 +544,7 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
   double mt[9];
   for (int i = 0; i < 9; ++i) mt[i] = I3[i];
   for (int t = 0; t < T; ++t) {
-    if (t > 0 && mat3_norm(mt) < 1e-18) break;
+    if (t > 0 && mat3_norm(mt) < tol) break;
     d.Mt.insert(d.Mt.end(), mt, mt + 9);
     ++d.tcut;
     mat3_mul(mt, M, mt);
@@ -556,7 +556,7 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
   double mcj[9];
   for (int i = 0; i < 9; ++i) mcj[i] = I3[i];
   for (int j = 0; j < C; ++j) {
-    if (j > 0 && mat3_norm(mcj) < 1e-18) break;
+    if (j > 0 && mat3_norm(mcj) < tol) break;
     d.McPow.insert(d.McPow.end(), mcj, mcj + 9);
     ++d.jterms;
     mat3_mul(mcj, Mc, mcj);
@@ -567,7 +567,7 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
     for (int i = 0; i < 9; ++i) md[i] = M[i];
     for (int dd = 1; dd <= 32; ++dd) {
       d.Mlane.insert(d.Mlane.end(), md, md + 9);
-      if (mat3_norm(md) >= 1e-18) d.dcut = dd;
+      if (mat3_norm(md) >= tol) d.dcut = dd;
       mat3_mul(md, M, md);
     }
     double m32[9];
@@ -576,13 +576,13 @@ DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C) 
     for (int i = 0; i < 9; ++i) pj[i] = I3[i];
     const int nw = (T + 31) / 32;
     for (int j = 0; j < std::min(nw, 8); ++j) {
-      if (j > 0 && mat3_norm(pj) < 1e-18) break;
+      if (j > 0 && mat3_norm(pj) < tol) break;
       d.M32pow.insert(d.M32pow.end(), pj, pj + 9);
       ++d.wterms;
       mat3_mul(pj, m32, pj);
     }
   }
-  if (d.jterms == C && mat3_norm(mcj) >= 1e-18) {
+  if (d.jterms == C && mat3_norm(mcj) >= tol) {
     // the sum wraps the ring: closure (I - Mc^C)^{-1}; mcj = Mc^C here
     double IM[9];
     for (int i = 0; i < 9; ++i) IM[i] = I3[i] - mcj[i];

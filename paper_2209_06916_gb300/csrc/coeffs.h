@@ -92,6 +92,8 @@ struct DistScanTables {
   int wterms = 0;
   int dcut = 0;                // largest d <= 32 with M^d not negligible
 };
-DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C);
+// Terms whose transfer-matrix norm falls below `tol` are dropped (1e-18 for
+// FP64 kernels, 1e-10 for FP32 ones).
+DistScanTables dist_scan_tables(const double* coef, int h, int P, int T, int C, double tol = 1e-18);
 
 }  // namespace mg

@@ -101,6 +101,7 @@ struct mgrit_handle {
   double* partials = nullptr;
   int64_t npart = 0;
   double* dnorm = nullptr;
+  double* dnorm_f = nullptr;  // MIXED: squared norm of the FP32 inner residual
   double* hnorm = nullptr;  // pinned
   double* du0 = nullptr;
   int64_t launches = 0;
@@ -174,23 +175,14 @@ static int check_launch() {
 // setup helpers
 // ---------------------------------------------------------------------------
 
-// Chunk geometry of the in-block solves: nthr (a power of two <= 256) chunks
-// of P points, P as close to 32 as possible, 8 <= P <= 64.
-static bool pick_chunks(int64_t n, int* P, int* nthr) {
-  int best = -1, bestP = 0;
-  for (int t = 256; t >= 1; t >>= 1) {
-    if (n % t) continue;
-    int64_t p = n / t;
-    if (p < 8 || p > 64) continue;
-    int score = (int)std::abs(p - 32);
-    if (best < 0 || score < best || (score == best && p > bestP)) {
-      best = score;
-      bestP = (int)p;
-      *P = (int)p;
-      *nthr = t;
-    }
-  }
-  return best >= 0;
+// Host check that an n-point vector has a chunk geometry of the step
+// kernels at all: C <= 16 CTAs of <= 256 threads with a chunk length P in
+// {8, 16, 32} (so n <= 131072, n a multiple of 8).
+static bool has_chunk_geometry(int64_t n) {
+  for (int C = 1; C <= 16; C *= 2)
+    for (int P : kChunkLens)
+      if (n % ((int64_t)C * P) == 0 && n / ((int64_t)C * P) <= 256) return true;
+  return false;
 }
 
 
@@ -200,7 +192,8 @@ static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int H
   std::memset((void*)d, 0, sizeof(*d));
   double c3[3] = {0, 0, 0};
   for (int q = 0; q < horder; ++q) c3[q] = coef[q];
-  DistScanTables tb = dist_scan_tables(c3, Hpad, P, nthr, C);
+  // carries below the kernel precision are dropped
+  DistScanTables tb = dist_scan_tables(c3, Hpad, P, nthr, C, sizeof(T) == 4 ? 1e-10 : 1e-18);
   d->h = Hpad;
   d->rounds = std::min(tb.rounds, kMaxRounds);
   d->tcut = tb.tcut;
@@ -686,7 +679,7 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
           ++o;
         }
       }
-      if (sp->result != 0) {
+      if (sp->result != 0 || sp->rscale != 1.0) {
         if ((R & 1u) && !sp->resb) {
           sp->resb = 1;
           changed = true;
@@ -806,6 +799,48 @@ static float time_launches(mgrit_handle* h, F launch) {
   return ms;
 }
 
+// The solves of a step programme leave out the 1/kappa of the stage-matrix
+// factorisation: slot s then holds scale_s times its value (a solve
+// multiplies the scale of its input by kappa), every AXPY / AXPYL
+// coefficient is rescaled to the scales of its operands, and the end of the
+// step maps the result back to scale 1 (rscale).  One multiply per point and
+// step replaces one per solve.
+static void fold_solve_scale(SdirkParams<double>* sp) {
+  const double kappa = 1.0 / sp->sscale;
+  double scale[kSdirkMaxSlots + 1];
+  bool zero[kSdirkMaxSlots + 1];
+  for (int s = 0; s <= kSdirkMaxSlots; ++s) {
+    scale[s] = 1.0;
+    zero[s] = false;
+  }
+  for (int o = 0; o < sp->nops; ++o) {
+    const int dst = sp->opd[o], src = sp->ops[o];
+    switch (sp->opk[o]) {
+      case kOpCopy:
+        scale[dst] = scale[src];
+        zero[dst] = false;
+        break;
+      case kOpZero:
+        zero[dst] = true;
+        break;
+      case kOpAxpy:
+      case kOpAxpyL:
+        if (zero[dst]) {  // dst starts at 0: take the source's scale
+          scale[dst] = scale[src];
+          zero[dst] = false;
+        } else {
+          sp->opc[o] *= scale[dst] / scale[src];
+        }
+        break;
+      default:  // kOpSolve
+        scale[dst] = scale[src] * kappa;
+        zero[dst] = false;
+        break;
+    }
+  }
+  sp->rscale = 1.0 / scale[sp->result];
+}
+
 // Geometry-free part of the level-0 SDIRK operator: the step programme with
 // its barrier schedule, L_p taps, the factorised stage matrix.
 static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why) {
@@ -814,7 +849,6 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
   std::memset((void*)sp, 0, sizeof(*sp));
   double gamma = 0.0;
   if (!sdirk_program(P.rk_order_q, P.cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
-  if (!schedule_sdirk(sp, why)) return MGRIT_ERR_UNSUPPORTED;
   Stencil L = upwind_taps(p);
   sp->p1 = L.width();
   sp->llo = L.lo;
@@ -831,6 +865,8 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
     return MGRIT_ERR_UNSUPPORTED;
   }
   sp->sscale = bf->inv_kappa;
+  fold_solve_scale(sp);
+  if (!schedule_sdirk(sp, why)) return MGRIT_ERR_UNSUPPORTED;
   return MGRIT_OK;
 }
 
@@ -874,6 +910,7 @@ static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const
     f.llo = sp.llo;
     for (int i = 0; i < 8; ++i) f.ltaps[i] = (float)sp.ltaps[i];
     f.sscale = (float)sp.sscale;
+    f.rscale = (float)sp.rscale;
     f.nops = sp.nops;
     f.nslots = sp.nslots;
     f.result = sp.result;
@@ -1076,8 +1113,8 @@ static int tune_coarse(mgrit_handle* h, int l) {
 
 
 // Algorithmic flops of `steps` SDIRK steps on K vectors: 2 per multiply-add
-// of the two recurrences of each solve (plus the 1/kappa scaling), of each
-// L_p mat-vec (plus its axpy) and of each axpy.
+// of the two recurrences of each solve, of each L_p mat-vec (plus its axpy)
+// and of each axpy, and 1 for the step's 1/kappa scaling.
 template <typename T>
 static double sdirk_flops(const SdirkParams<T>& sp, int64_t nx, int64_t K, int64_t steps) {
   int nsolve = 0, naxl = 0, nax = 0;
@@ -1086,8 +1123,8 @@ static double sdirk_flops(const SdirkParams<T>& sp, int64_t nx, int64_t K, int64
     naxl += sp.opk[o] == kOpAxpyL;
     nax += sp.opk[o] == kOpAxpy;
   }
-  const double per_pt = nsolve * (sp.c.h + sp.a.h + 1) + naxl * (sp.p1 + 1) + nax;
-  return 2.0 * per_pt * (double)nx * (double)K * (double)steps;
+  const double per_pt = 2.0 * (nsolve * (sp.c.h + sp.a.h) + naxl * (sp.p1 + 1) + nax) + 1.0;
+  return per_pt * (double)nx * (double)K * (double)steps;
 }
 
 static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double* start, double* out,
@@ -1379,7 +1416,7 @@ static int l0f_cf(mgrit_handle* h, bool zero_start) {
 }
 
 // rho_{k+1} = Phi^m e_k + r_{k+1} - e_{k+1}  ->  level-1 RHS (FP32)
-static int l0f_fres(mgrit_handle* h, bool zero_guess) {
+static int l0f_fres(mgrit_handle* h, bool zero_guess, bool want_norm = false) {
   LevelData& L0 = h->lev[0];
   float* g1 = h->lev[1].gf;
   const size_t row = sizeof(float) * (size_t)h->nx;
@@ -1402,6 +1439,7 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess) {
     sp.traj = nullptr;
     ProfScope ps(h, kProfL0F32, sdirk_flops(sp, h->nx, L0.K, h->m));
     if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+    if (want_norm) launch_reduce_sum(h->partials, L0.K * sp.csize, h->dnorm_f, h->st);
   } else {
     StencilParams<float>& sp = *h->fineMf;
     sp.in = L0.uCf[L0.curf];
@@ -1410,10 +1448,15 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess) {
     sp.sub = L0.uCf[L0.curf] + h->nx;
     sp.partial = h->partials;
     sp.rows = L0.K;
-    ProfScope ps(h, kProfL0F32, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
-    launch_stencil_rows(sp, h->st);
+    int64_t nb;
+    {
+      ProfScope ps(h, kProfL0F32, 2.0 * sp.ntaps * (double)h->nx * (double)sp.rows);
+      nb = launch_stencil_rows(sp, h->st);
+    }
+    if (want_norm) launch_reduce_sum(h->partials, nb, h->dnorm_f, h->st);
   }
   ++h->launches;
+  if (want_norm) ++h->launches;
   return check_launch();
 }
 
@@ -1496,7 +1539,10 @@ static int coarse_correct_f(mgrit_handle* h, int l) {
 }
 
 // One FP32 inner cycle for the level-0 error equation with RHS lev[0].gf.
-static int inner_cycle(mgrit_handle* h, bool zero_guess) {
+// One FP32 V-cycle on the error equation A e = r; with want_norm (not on
+// the zero-guess cycle) the squared norm of its level-0 residual after the
+// pre-relaxation goes to dnorm_f.
+static int inner_cycle(mgrit_handle* h, bool zero_guess, bool want_norm = false) {
   const int nu = h->prm.nu;
   int rc;
   if (zero_guess && nu == 0) {
@@ -1506,7 +1552,7 @@ static int inner_cycle(mgrit_handle* h, bool zero_guess) {
       rc = l0f_cf(h, zero_guess && s == 0);
       if (rc) return rc;
     }
-    rc = l0f_fres(h, false);
+    rc = l0f_fres(h, false, want_norm && !zero_guess);
   }
   if (rc) return rc;
   return coarse_correct_f(h, 1);
@@ -1539,14 +1585,84 @@ static int l0_relax_residual_async(mgrit_handle* h) {
   return l0_fres(h);
 }
 
-static int mixed_outer_body(mgrit_handle* h) {
+// One refinement step captured into the graph: FP64 residual -> FP32 RHS,
+// the inner FP32 V-cycles (a fixed count, or adaptive: the first cycle, then
+// a nested conditional while node whose body is one cycle and its check),
+// the FP32 correction added into the FP64 iterate, and the new FP64
+// residual.  cap2 is a second stream for capturing the nested body.
+static int mixed_outer_body(mgrit_handle* h, cudaStream_t cap2) {
   LevelData& L0 = h->lev[0];
-  const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
   int rc;
   launch_convert(kCvtD2F, h->lev[1].g, L0.gf, (L0.K + 1) * h->nx, h->st);
   ++h->launches;
-  for (int j = 0; j < inner; ++j)
-    if ((rc = inner_cycle(h, j == 0))) return rc;
+  if (h->prm.inner_cycles > 0) {
+    for (int j = 0; j < h->prm.inner_cycles; ++j)
+      if ((rc = inner_cycle(h, j == 0))) return rc;
+  } else {
+    if ((rc = inner_cycle(h, true))) return rc;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle hin;
+    if (cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive ||
+        cudaGraphConditionalHandleCreate(&hin, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess) {
+      note_cuda_error("inner conditional handle", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+    launch_inner_init(h->dstate, h->dnorm, hin, h->st);
+    ++h->launches;
+    if (cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess) {
+      note_cuda_error("cudaStreamGetCaptureInfo", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hin;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t ncond;
+    if (cudaGraphAddNode(&ncond, cg, deps, nullptr, nd, &np) != cudaSuccess) {
+      note_cuda_error("inner conditional node", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+    cudaGraph_t ibody = np.conditional.phGraph_out[0];
+    cudaStream_t outer = h->st;
+    if (cudaStreamBeginCaptureToGraph(cap2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+      note_cuda_error("inner body capture", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+    h->st = cap2;
+    // the body replays on the same buffers: it must leave the level-0 error
+    // iterate where it found it (an odd number of C-relaxations moves it)
+    const int curf0 = L0.curf;
+    rc = inner_cycle(h, false, true);
+    if (!rc && L0.curf != curf0) {
+      if (cudaMemcpyAsync(L0.uCf[curf0], L0.uCf[L0.curf], sizeof(float) * (size_t)h->nx * (L0.K + 1),
+                          cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
+        rc = MGRIT_ERR_CUDA;
+      L0.curf = curf0;
+    }
+    if (!rc) {
+      launch_inner_check(h->dstate, h->dnorm_f, hin, h->st);
+      ++h->launches;
+    }
+    cudaGraph_t ib = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cap2, &ib);
+    h->st = outer;
+    if (rc) return rc;
+    if (ee != cudaSuccess) {
+      note_cuda_error("inner body capture end", ee);
+      return MGRIT_ERR_CUDA;
+    }
+    if (cudaStreamUpdateCaptureDependencies(h->st, &ncond, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+        cudaSuccess) {
+      note_cuda_error("cudaStreamUpdateCaptureDependencies", cudaGetLastError());
+      return MGRIT_ERR_CUDA;
+    }
+  }
   launch_convert(kAddF2D, L0.uC[L0.cur] + h->nx, L0.uCf[L0.curf] + h->nx, L0.K * h->nx, h->st);
   ++h->launches;
   return l0_fres(h);
@@ -1572,9 +1688,10 @@ static int build_solve_graph(mgrit_handle* h) {
       return MGRIT_ERR_CUDA;
     }
   }
-  cudaStream_t user = h->st, cap = nullptr;
+  cudaStream_t user = h->st, cap = nullptr, cap2 = nullptr;
   if (cudaStreamSynchronize(user) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) {
     h->prof.on = prof;
     note_cuda_error("capture stream", cudaGetLastError());
     return MGRIT_ERR_CUDA;
@@ -1618,7 +1735,7 @@ static int build_solve_graph(mgrit_handle* h) {
       break;
     }
     if (h->mixed) {
-      rc = mixed_outer_body(h);
+      rc = mixed_outer_body(h, cap2);
     } else {
       rc = coarse_correct(h, 1);
       if (!rc) rc = l0_relax_residual_async(h);
@@ -1636,6 +1753,7 @@ static int build_solve_graph(mgrit_handle* h) {
   if (pro) cudaGraphDestroy(pro);
   h->st = user;
   cudaStreamDestroy(cap);
+  cudaStreamDestroy(cap2);
   h->prof.on = prof;
   if (rc) {
     cudaError_t e = cudaGetLastError();
@@ -1732,6 +1850,7 @@ int mgrit_destroy(mgrit_handle* h) {
   }
   dev_free(h, h->partials);
   dev_free(h, h->dnorm);
+  dev_free(h, h->dnorm_f);
   dev_free(h, h->du0);
   pinned_put(h->hnorm);
   delete h;
@@ -1777,8 +1896,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     }
     if (N < 1) return MGRIT_ERR_INVALID_ARG;
   }
-  int P0, T0;
-  if (!pick_chunks(P.nx, &P0, &T0)) return MGRIT_ERR_INVALID_ARG;
+  if (!has_chunk_geometry(P.nx)) return MGRIT_ERR_INVALID_ARG;
   // stencil wider than the grid is rejected (wrap-around of one step)
   if ((int64_t)(P.order_p + 1) * P.rk_order_q + 1 > P.nx) return MGRIT_ERR_INVALID_ARG;
 
@@ -1871,6 +1989,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   for (int l = 1; l < L; ++l) h->npart = std::max<int64_t>(h->npart, (h->lev[l].K + 1) * 16);
   if ((rc = alloc(&h->partials, sizeof(double) * h->npart))) return rc;
   if ((rc = alloc(&h->dnorm, sizeof(double)))) return rc;
+  if ((rc = alloc(&h->dnorm_f, sizeof(double)))) return rc;
   if ((rc = alloc(&h->du0, row))) return rc;
   CUDA_TRY(cudaMemsetAsync(h->du0, 0, row, h->st));
   if (!(h->hnorm = (double*)pinned_get())) return MGRIT_ERR_OOM;
@@ -2015,7 +2134,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
     // follows the FP64 pre-relaxation; every later one is the FP64 C-point
     // residual of the corrected iterate (F-relaxation implied).
     LevelData& L0 = h->lev[0];
-    const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
+    const int inner = h->prm.inner_cycles;  // 0: adaptive
     rc = level0_relax_residual(h, &nrm);
     if (rc) return rc;
     while (true) {
@@ -2037,10 +2156,31 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
       // r (FP64, rows 0..K of the level-1 RHS) -> FP32 RHS of the inner solve
       launch_convert(kCvtD2F, h->lev[1].g, L0.gf, (L0.K + 1) * h->nx, h->st);
       ++h->launches;
-      for (int j = 0; j < inner; ++j) {
-        rc = inner_cycle(h, j == 0);
+      if (h->prm.inner_cycles > 0) {
+        for (int j = 0; j < inner; ++j) {
+          rc = inner_cycle(h, j == 0);
+          if (rc) return rc;
+          ++st.inner_cycles;
+        }
+      } else {  // adaptive: the rule of inner_check_kernel, on the host
+        rc = inner_cycle(h, true);
         if (rc) return rc;
         ++st.inner_cycles;
+        const double rho0 = nrm;
+        double prev = rho0;
+        int count = 1;
+        bool go = count < kInnerMax;
+        while (go) {
+          rc = inner_cycle(h, false, true);
+          if (rc) return rc;
+          ++st.inner_cycles;
+          ++count;
+          CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm_f, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+          CUDA_TRY(cudaStreamSynchronize(h->st));
+          const double rho = std::sqrt(std::max(0.0, *h->hnorm));
+          go = inner_continue(rho, prev, rho0, count, kInnerMax, kInnerTol);
+          prev = rho;
+        }
       }
       // u += e at the C-points k = 1..K (FP64 master iterate)
       launch_convert(kAddF2D, L0.uC[L0.cur] + h->nx, L0.uCf[L0.curf] + h->nx, L0.K * h->nx, h->st);
@@ -2255,6 +2395,8 @@ int mgrit_solve_async(mgrit_handle* h, const double* u0) {
   std::memset(&init, 0, sizeof(init));
   init.tol = h->prm.tol;
   init.max_iter = h->prm.max_iter;
+  init.in_tol = kInnerTol;
+  init.in_max = kInnerMax;
   *h->hstate = init;
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(DevSolveState), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(cudaGraphLaunch(h->gexec, h->st));
@@ -2296,9 +2438,8 @@ int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats) {
     if (stats->history_len >= 2 && s.hist[stats->history_len - 2] > 0)
       stats->conv_factor = s.hist[stats->history_len - 1] / s.hist[stats->history_len - 2];
     if (h->mixed) {
-      const int inner = h->prm.inner_cycles > 0 ? h->prm.inner_cycles : 2;
       stats->outer_iterations = s.it;
-      stats->inner_cycles = s.it * inner;
+      stats->inner_cycles = h->prm.inner_cycles > 0 ? s.it * h->prm.inner_cycles : s.in_total;
     }
   }
   return s.status;

@@ -205,6 +205,32 @@ __global__ void solve_check_kernel(DevSolveState* s, const double* dnorm_sq, cud
   cudaGraphSetConditional(hnd, go);
 }
 
+__global__ void inner_init_kernel(DevSolveState* s, const double* dnorm64_sq, cudaGraphConditionalHandle hnd) {
+  const double rho0 = sqrt(fmax(0.0, dnorm64_sq[0]));
+  s->in_rho0 = rho0;
+  s->in_prev = rho0;
+  s->in_count = 1;
+  s->in_total += 1;
+  cudaGraphSetConditional(hnd, s->in_count < s->in_max ? 1 : 0);
+}
+
+__global__ void inner_check_kernel(DevSolveState* s, const double* dnormf_sq, cudaGraphConditionalHandle hnd) {
+  const double rho = sqrt(fmax(0.0, dnormf_sq[0]));
+  s->in_count += 1;
+  s->in_total += 1;
+  const bool go = inner_continue(rho, s->in_prev, s->in_rho0, s->in_count, s->in_max, s->in_tol);
+  s->in_prev = rho;
+  cudaGraphSetConditional(hnd, go ? 1 : 0);
+}
+
+void launch_inner_init(DevSolveState* s, const double* dnorm64_sq, cudaGraphConditionalHandle hnd, cudaStream_t st) {
+  inner_init_kernel<<<1, 1, 0, st>>>(s, dnorm64_sq, hnd);
+}
+
+void launch_inner_check(DevSolveState* s, const double* dnormf_sq, cudaGraphConditionalHandle hnd, cudaStream_t st) {
+  inner_check_kernel<<<1, 1, 0, st>>>(s, dnormf_sq, hnd);
+}
+
 void* solve_init_kernel_fn() { return (void*)solve_init_kernel; }
 void* solve_check_kernel_fn() { return (void*)solve_check_kernel; }
 

@@ -102,7 +102,10 @@ size_t coarse_smem_bytes(int npc, int P, int nthr, int elem);
 // SDIRK method, one CF-interval per thread-block cluster.  A step is a small
 // program over shared-memory vector slots (slot 0 holds the state):
 //   COPY  dst = src          ZERO  dst = 0          AXPY  dst += c src
-//   AXPYL dst += c L_p src   SOLVE dst = (I + gamma c L_p)^{-1} src
+//   AXPYL dst += c L_p src   SOLVE dst = kappa (I + gamma c L_p)^{-1} src
+// (the solve leaves out the 1/kappa of its factorisation; the host keeps a
+// scale per slot, folds it into the coefficients and undoes it once per
+// step with rscale)
 // built on the host from the tableau (stiffly accurate stages) or from the
 // factored stability function (SDIRK5).
 // ---------------------------------------------------------------------------
@@ -116,7 +119,8 @@ struct SdirkParams {
   int p1, llo;         // L_p taps at offsets llo = -p1/2 .. llo + p1 - 1
   T ltaps[8];
   SolveDir<T> c, a;    // factored stage matrix (I + gamma c L_p)
-  T sscale;            // 1/kappa of the factorisation (applied before a solve)
+  T sscale;            // 1/kappa of the factorisation (folded into the op coefficients)
+  T rscale;            // end of step: slot 0 = rscale * slot `result` (undoes the folded scales)
   int nops, nslots, result;
   int opk[kSdirkMaxOps], opd[kSdirkMaxOps], ops[kSdirkMaxOps];
   int opg[kSdirkMaxOps];   // AXPYL group head: number of consecutive AXPYL ops on the same src (else 1)
@@ -161,8 +165,17 @@ void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st, con
 struct DevSolveState {
   double r0, rnorm, tol;
   int it, max_iter, converged, status, hist_len, pad;
+  // MIXED adaptive inner solve: FP32 V-cycles of one refinement step repeat
+  // while the FP32 residual of the error equation is above in_tol times the
+  // FP64 residual it corrects and still falls by 0.8 per cycle, at most
+  // in_max cycles
+  double in_rho0, in_prev, in_tol;
+  int in_count, in_max, in_total, in_pad;
   double hist[128];
 };
+constexpr int kInnerMax = 16;
+constexpr double kInnerTol = 1e-5;
+constexpr double kInnerStall = 0.8;
 // First residual: r0, history[0]; sets the loop condition (0 when already
 // converged).  Check: after each iteration, appends the norm and sets the
 // condition to continue, or records converged / diverged / not converged.
@@ -170,6 +183,15 @@ void* solve_init_kernel_fn();
 void* solve_check_kernel_fn();
 void launch_solve_check(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd,
                         cudaStream_t st);
+// Adaptive inner solve: init after the first (zero-guess) FP32 cycle from the
+// FP64 residual norm; check after every further cycle from the FP32 one.
+void launch_inner_init(DevSolveState* s, const double* dnorm64_sq, cudaGraphConditionalHandle hnd, cudaStream_t st);
+void launch_inner_check(DevSolveState* s, const double* dnormf_sq, cudaGraphConditionalHandle hnd, cudaStream_t st);
+// the continuation rule shared by the device check and the eager host loop
+__host__ __device__ inline bool inner_continue(double rho, double prev, double rho0, int count, int max_count,
+                                               double tol) {
+  return rho == rho && rho <= 1e300 && rho > tol * rho0 && rho < kInnerStall * prev && count < max_count;
+}
 // sum of partial[0..n) in a fixed order, written to out[0] (FP64)
 void launch_reduce_sum(const double* partial, int64_t n, double* out, cudaStream_t st);
 // C-point iterate: row 0 = u0, rows k >= 1 uniform [0,1) at time index k*m

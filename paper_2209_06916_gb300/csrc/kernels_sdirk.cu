@@ -122,17 +122,17 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
       } else {  // kOpSolve
         T x[P];
 #pragma unroll
-        for (int j = 0; j < P; ++j) x[j] = A.sscale * src[j];
+        for (int j = 0; j < P; ++j) x[j] = src[j];
         banded_solve<HC, HA, T, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
 #pragma unroll
         for (int j = 0; j < P; ++j) dst[j] = x[j];
       }
     }
-    if (A.result != 0) {
+    if (A.result != 0 || A.rscale != T(1)) {
       if (A.resb) vec_sync(C);
       const T* r = slots + (size_t)A.result * npad + base;
 #pragma unroll
-      for (int j = 0; j < P; ++j) slots[base + j] = r[j];
+      for (int j = 0; j < P; ++j) slots[base + j] = A.rscale * r[j];
     }
     if (A.mode == kModeSEQ && A.traj && A.every > 0 && s % A.every == 0) {
       __syncthreads();

@@ -34,6 +34,9 @@ CASES = [  # kind, p, q, c, m, levels, nx, nt, inner
     ("erk", 5, 5, 0.9, 4, 3, 256, 16 * 6, 3),
     ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2, 2),
     ("sdirk", 3, 3, 5.0, 4, 3, 256, 16 * 8, 2),
+    ("erk", 3, 3, 0.85, 8, 4, 512, 8 ** 3 * 2, 0),      # adaptive inner cycles
+    ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2, 0),
+    ("sdirk", 5, 5, 6.0, 4, 4, 256, 4 ** 3 * 4, 0),
 ]
 
 
@@ -61,3 +64,25 @@ def test_mixed_solve_reaches_fp64_accuracy(kind, p, q, c, m, levels, nx, nt, inn
     # same accuracy class as FP64: within 10x of the FP64 solver's error and
     # below the 1e-8 bound used for FP64 solves
     assert emx < max(10 * e64, 1e-9) and emx < 1e-8, (e64, emx)
+
+
+@pytest.mark.parametrize("kind,p,q,c,m,levels,nx,nt", [("erk", 3, 3, 0.85, 8, 4, 512, 8 ** 3 * 2),
+                                                      ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2)])
+def test_adaptive_inner_cycles_cut_fp64_residuals(kind, p, q, c, m, levels, nx, nt):
+    """Adaptive inner solves (inner_cycles = 0) need fewer FP64 residual
+    evaluations than one FP32 cycle per residual, for no more V-cycles than
+    a fixed count would spend, at the same accuracy."""
+    u0 = ic_sin4_noise(nx, seed=2) if p < 5 else ic_fourier(nx, seed=2)
+    k = pkg.ERK if kind == "erk" else pkg.SDIRK
+    stream = torch.cuda.current_stream().cuda_stream
+    st = {}
+    for inner in (1, 0):
+        prm = pkg.make_params(nx, nt, c, p, kind=k, q=q, m=m, levels=levels, tol=1e-10, max_iter=40,
+                              precision=pkg.MIXED, seed=3, inner_cycles=inner)
+        s = pkg.Solver(prm, stream=stream)
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        st[inner] = s.solve(torch.tensor(u0, device="cuda"), out)
+        s.close()
+    assert st[0]["converged"] and st[1]["converged"]
+    assert st[0]["outer_iterations"] * 2 <= st[1]["outer_iterations"], (st[0], st[1])
+    assert st[0]["inner_cycles"] <= st[1]["inner_cycles"] + 16

@@ -299,7 +299,9 @@ def test_sequential_stepping_matches_oracle(p, c, nx, nsteps, every):
     (pkg.ERK, 1, 0.85, 4, 2, 1, pkg.FP64, 256, 1024),
     (pkg.ERK, 3, 0.85, 4, 3, 2, pkg.FP64, 64, 16 * 6),
     (pkg.SDIRK, 3, 5.0, 4, 3, 1, pkg.FP64, 64, 16 * 8),
-    (pkg.ERK, 3, 0.85, 8, 4, 1, pkg.MIXED, 256, 8 ** 3 * 2),
+    (pkg.ERK, 3, 0.85, 8, 4, 1, pkg.MIXED, 256, 8 ** 3 * 2),   # adaptive inner cycles, odd nu
+    (pkg.ERK, 3, 0.85, 4, 3, 2, pkg.MIXED, 64, 16 * 6),        # adaptive, even nu
+    (pkg.SDIRK, 5, 4.0, 16, 3, 1, pkg.MIXED, 256, 16 * 16 * 2),
 ])
 def test_graph_solve_equals_eager_solve(kind, p, c, m, levels, nu, prec, nx, nt):
     u0 = ic_sin4(nx)
@@ -319,5 +321,6 @@ def test_graph_solve_equals_eager_solve(kind, p, c, m, levels, nu, prec, nx, nt)
         s.close()
     (a, sa), (b, sb) = res
     assert sa["iterations"] == sb["iterations"] and sb["converged"]
+    assert sa["inner_cycles"] == sb["inner_cycles"]
     assert np.array_equal(a, b)
     assert np.allclose(sa["history"], sb["history"], rtol=0, atol=0)
