@@ -140,7 +140,7 @@ struct SdirkParams {
 };
 size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem);
 // Chunk lengths the step kernels are compiled for (one chunk per thread).
-constexpr int kChunkLens[3] = {8, 16, 32};
+constexpr int kChunkLens[4] = {4, 8, 16, 32};
 // Largest co-schedulable cluster size <= want (power of two) for a CTA of
 // nthr threads and smem bytes of dynamic shared memory.
 int sdirk_max_cluster(int want, size_t smem, int nthr);

@@ -21,7 +21,7 @@ from workloads import ic_fourier, ic_sin4
 
 pytestmark = pytest.mark.gpu
 
-GEOMS = [(c, p) for c in (1, 2, 4, 8, 16) for p in (8, 16, 32)]
+GEOMS = [(c, p) for c in (1, 2, 4, 8, 16) for p in (4, 8, 16, 32)]
 
 
 @pytest.fixture(scope="module", autouse=True)
