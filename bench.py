@@ -385,11 +385,19 @@ def main():
     value = ws * dof * args.steps / (ms / 1e3)
     cnt, kms, kfl = prof["stencil0"]
     achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
-    kname = ("stencil_rows_kernel<double,4> (level-0 composite Phi^m)" if w["kind"] == "erk"
-             else "sdirk_kernel<double> (level-0 SDIRK stages: banded solves + L_p mat-vecs)")
+    info0 = s.level_info(0)
+    if w["kind"] == "erk":
+        kname = "stencil_rows_kernel<double,%d> (level-0 composite Phi^m)" % int(info0[6])
+    else:
+        kname = "sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves + L_p mat-vecs), clusters of %d" % (
+            int(info0[6]), w["p"] + 1, int(info0[7]))
+    # DRAM bytes per launch of the level-0 kernel from one ncu capture of
+    # this workload (profiles/stencil_rows_kernel_advection1d_erk3u3_fp64.md)
+    traffic = 94.4e6 if (w["name"] == WORKLOADS["c2"]["name"] and prec == pkg.FP64) else None
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": "derived FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
             "launches": cnt, "ms_per_launch": kms / max(1, cnt),
             "share_of_step": kms / ms if ms > 0 else None}

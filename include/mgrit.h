@@ -229,7 +229,8 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
  * mgrit_level_info -- host-side derived data of a level (no GPU work):
  * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
  * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite
- * stencil taps (level 0, ERK), out[6] = chunk length of the in-block solves,
+ * stencil taps (level 0, ERK), out[6] = chunk length of the in-block solves
+ * (level 0, ERK: outputs per thread of the composite-stencil kernel),
  * out[7] = CTAs per vector (thread-block cluster size) of the level's step
  * kernel (coarse levels; level 0 for SDIRK).  The step kernels' geometry is
  * measured at setup among the candidates that fit (cached per shape in the

@@ -2362,6 +2362,7 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
       out[7] = (double)h->sd0->csize;
     } else {
       out[5] = (double)h->fineM->ntaps;
+      out[6] = (double)(h->fineM->tile_r > 0 ? h->fineM->tile_r : 0);
     }
     return MGRIT_OK;
   }
