@@ -2362,7 +2362,8 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
       out[7] = (double)h->sd0->csize;
     } else {
       out[5] = (double)h->fineM->ntaps;
-      out[6] = (double)(h->fineM->tile_r > 0 ? h->fineM->tile_r : 0);
+      const int64_t nx = h->nx;  // untuned: the kernel's own choice by n_x
+      out[6] = (double)(h->fineM->tile_r > 0 ? h->fineM->tile_r : nx >= 1024 ? 4 : nx >= 512 ? 2 : 1);
     }
     return MGRIT_OK;
   }
