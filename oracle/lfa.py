@@ -10,7 +10,10 @@ it on each side are dropped (footnote to Eq. rho-asym).
 
 Parity pins: Sec. 6.3.4 (FCF factors of the third-order schemes bounded by 0.6)
 and Sec. 6.4 (ERK4+U4, m = 2: about 0.15 just below c/c_max = 0.24 and about
-0.84 just above).
+0.84 just above).  With direct coarse operators (Sec. 5): the factor with
+rediscretisation is bounded below by rho_check (Theorem thm:MOL-rho-lwr-bnd,
+Eq. rho-check-MOL) and equals it where smooth characteristic components set
+the maximum; rho_check tends to |1 - m^-p| (Eq. rho-check-MOL-asym).
 """
 import numpy as np
 
@@ -53,9 +56,23 @@ def corrected_sl_symbol(p, kind, c, m, omega, q=None, d_order=None):
     return S / (1.0 - phi * Dsym)
 
 
-def two_level_factor(p, kind, c, m, nu=1, omit=0, n=1 << 11):
-    """LFA factor of two-level MGRIT with the corrected SL coarse operator."""
+def two_level_factor(p, kind, c, m, nu=1, omit=0, n=1 << 11, coarse_op="sl_corrected"):
+    """LFA factor of two-level MGRIT with the corrected SL coarse operator,
+    or with a direct one: ``sl`` (S_p^{(m dt)}) or ``redisc`` (the fine
+    method with step m dt, Sec. 5)."""
     omega = omega_samples(n, omit)
     lam = ops.FineOperator(p, kind, p, c).symbol(omega)
-    mu = corrected_sl_symbol(p, kind, c, m, omega)
+    if coarse_op == "sl_corrected":
+        mu = corrected_sl_symbol(p, kind, c, m, omega)
+    else:
+        mu = ops.direct_operator(p, kind, p, c, m, 1, coarse_op).symbol(omega)
     return rho(lam, mu, m, nu)
+
+
+def rho_check(p, c, m, e_rk_fine, e_rk_coarse):
+    """Lower bound of the two-level factor with a direct MOL coarse operator
+    on asymptotically smooth characteristic components (Theorem
+    thm:MOL-rho-lwr-bnd, Eq. rho-check-MOL), odd p:
+        c^p |e_F - m^p e_C| / |e_FD + (m c)^p e_C|."""
+    efd = float(co.e_fd(p))
+    return c ** p * abs(e_rk_fine - m ** p * e_rk_coarse) / abs(efd + (m * c) ** p * e_rk_coarse)

@@ -66,19 +66,23 @@ def c_residual(op, u, g, m):
 
 class Hierarchy:
     """Level operators of a uniform-m hierarchy: level 0 is the fine MOL step
-    Phi, level l >= 1 the corrected SL operator Phi^{(m^l dt)} (Eq. MOL-SL-corrected-multilevel).
-    ``coarse`` may replace the level-1 operator (e.g. the ideal Phi^m) for a
-    two-level hierarchy."""
+    Phi, level l >= 1 the corrected SL operator Phi^{(m^l dt)} (Eq. MOL-SL-corrected-multilevel),
+    or with ``coarse_op`` = "sl" / "redisc" the direct SL operator or the
+    rediscretised fine method (operators.direct_operator).  ``coarse`` may
+    replace the level-1 operator (e.g. the ideal Phi^m) for a two-level
+    hierarchy."""
 
-    def __init__(self, p, kind, q, c, m, levels, coarse=None):
+    def __init__(self, p, kind, q, c, m, levels, coarse=None, coarse_op="sl_corrected"):
         self.m, self.levels = m, levels
         self.fine = ops.FineOperator(p, kind, q, c)
         self.ops = [self.fine]
         for l in range(1, levels):
             if l == 1 and coarse is not None:
                 self.ops.append(coarse)
-            else:
+            elif coarse_op == "sl_corrected":
                 self.ops.append(ops.coarse_operator(p, kind, q, c, m, l, levels))
+            else:
+                self.ops.append(ops.direct_operator(p, kind, q, c, m, l, coarse_op))
 
 
 def vcycle(h, level, u, g, nu):

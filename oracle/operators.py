@@ -19,6 +19,9 @@ SLOperator.apply         Sec. 3: S_p^{(Delta)} interpolation at the       exact 
                          departure point                                 Lemma 3.1 order
 CoarseOperator.apply     Eq. (MOL-SL-corrected[-multilevel])                Lemma 6.1 O(h^{p+2}) match with
                          (I - phi D)^{-1} S_p^{(m^l dt)}                  Phi^m; LFA values (Sec. 6.3.4, 6.4)
+direct_operator          Sec. 1 footnote, Sec. 2.2, Sec. 5: direct        symbols == application; LFA with
+                         coarse operators -- S_p^{(m^l dt)} ("sl") and    rediscretisation >= the bound of
+                         the rediscretised R_q(-m^l c L_p) ("redisc")     Theorem thm:MOL-rho-lwr-bnd
 """
 import numpy as np
 import scipy.linalg
@@ -211,6 +214,27 @@ def coarse_operator(p, kind, q, c, m, level, levels):
         return CoarseOperator(p, s, [(phi, p + 1)])
     fp, fq = co.phi_levels_general(p, kind, q, c, m, levels)[level - 1]
     return CoarseOperator(p, s, [(fp, p + 1), (fq, q + 1)])
+
+
+def direct_operator(p, kind, q, c, m, level, coarse_op):
+    """Coarse-grid operator of level ``level`` (>= 1) for the coarse-operator
+    choices compared in the paper:
+
+    ``sl_corrected``  the modified operator (I - phi D)^{-1} S_p^{(m^l dt)}
+                      (Eq. MOL-SL-corrected-multilevel), ``levels`` unused;
+    ``sl``            the direct semi-Lagrangian operator S_p^{(m^l dt)}
+                      (Sec. 3, a direct discretization in the sense of the
+                      footnote to Sec. 1);
+    ``redisc``        rediscretisation: the fine method with the coarse step,
+                      R_q(-m^l c L_p) (Sec. 2.2 and the Sec. 1 footnote;
+                      analysed in Sec. 5).
+    """
+    s = c * m ** level
+    if coarse_op == "sl":
+        return SLOperator(p, s)
+    if coarse_op == "redisc":
+        return FineOperator(p, kind, q, s)
+    raise ValueError(coarse_op)
 
 
 class PowerOperator:

@@ -152,3 +152,78 @@ def test_measured_factor_near_lfa():
     pred = lfa.two_level_factor(1, "erk", c, m)
     assert res["converged"]
     assert 0.5 * pred < res["factor"] < 1.15 * pred
+
+
+# ---------------------------------------------------------------------------
+# direct coarse-grid operators (Sec. 5): rediscretisation and uncorrected SL
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_redisc_lfa_bounded_below_by_theorem(p):
+    """Theorem thm:MOL-rho-lwr-bnd: with a rediscretised coarse operator the
+    two-level factor is at least rho_check_p(c) (Eq. rho-check-MOL), which
+    tends to |1 - m^-p| for m c >> 1 (Eq. rho-check-MOL-asym).  The LFA here
+    comes from the Fourier symbols of the operators, the bound from the error
+    constants: two independent routes."""
+    e = co.e_rk("sdirk", p)
+    for m in (2, 4, 8, 16):
+        for c in (0.5, 1.0, 2.0, 4.0, 8.0):
+            f = lfa.two_level_factor(p, "sdirk", c, m, coarse_op="redisc")
+            b = lfa.rho_check(p, c, m, e, e)
+            assert f >= b * (1 - 1e-3), (p, m, c, f, b)
+        big = lfa.rho_check(p, 512.0 / m, m, e, e)  # m c = 512: within O(1/(m c)^p)
+        assert abs(big - abs(1.0 - m ** -float(p))) < 4.0 / 512.0 ** p
+    # where the smooth characteristic components set the maximum (p = 1,
+    # m = 2) the two agree to the sampling of omega
+    for c in (0.5, 1.0, 2.0, 4.0):
+        f = lfa.two_level_factor(1, "sdirk", c, 2, coarse_op="redisc")
+        assert abs(f - lfa.rho_check(1, c, 2, co.e_rk("sdirk", 1), co.e_rk("sdirk", 1))) < 1e-3
+
+
+def test_redisc_third_order_diverges_for_large_m():
+    """Sec. 5.3: with rediscretisation, SDIRK3+U3 has two-level factors above
+    one (divergence) for the practical m >> 1, while SDIRK1+U1 stays below
+    one for m <= 8."""
+    assert lfa.two_level_factor(3, "sdirk", 2.0, 8, coarse_op="redisc") > 1.0
+    assert lfa.two_level_factor(3, "sdirk", 4.0, 16, coarse_op="redisc") > 1.0
+    for m in (2, 4, 8):
+        assert lfa.two_level_factor(1, "sdirk", 2.0, m, coarse_op="redisc") < 1.0
+
+
+def test_measured_factor_near_lfa_redisc():
+    """Two-level MGRIT with the rediscretised SDIRK1+U1 coarse operator:
+    the final-iteration factor on a long interval is close to (and not above)
+    the LFA prediction, as for the circles of the Sec. 5.3 figure."""
+    nx, nt, m, c = 256, 1024, 2, 1.0
+    h = mgrit.Hierarchy(1, "sdirk", 1, c, m, 2, coarse_op="redisc")
+    res = mgrit.solve(h, ic_sin4(nx), nt, tol=1e-10, max_iter=60)
+    pred = lfa.two_level_factor(1, "sdirk", c, m, coarse_op="redisc")
+    assert res["converged"]
+    assert 0.5 * pred < res["factor"] < 1.15 * pred, (res["factor"], pred)
+
+
+def test_direct_sl_worse_than_corrected():
+    """Sec. 6.3: the correction term is what makes the SL coarse operator
+    work for MOL fine grids; without it (direct SL) the two-level factor of
+    ERK3+U3 is far larger than with it."""
+    cmax = co.cfl_limit(3)
+    for m in (4, 8, 16):
+        for frac in (0.5, 0.85):
+            corr = lfa.two_level_factor(3, "erk", frac * cmax, m, omit=10)
+            direct = lfa.two_level_factor(3, "erk", frac * cmax, m, omit=10, coarse_op="sl")
+            assert direct > 1.5 * corr, (m, frac, corr, direct)
+
+
+@pytest.mark.parametrize("coarse_op", ["sl", "redisc"])
+def test_direct_operator_symbols_match_application(coarse_op):
+    """The direct operators' Fourier symbols (closed form) match their
+    application to Fourier modes on a periodic grid."""
+    nx = 64
+    x = np.arange(nx)
+    for level in (1, 2):
+        op = ops.direct_operator(3, "sdirk", 3, 0.7, 4, level, coarse_op)
+        for k in (1, 5, 17):
+            w = 2 * np.pi * k / nx
+            u = np.exp(1j * w * x)
+            got = op.apply(u.real) + 1j * op.apply(u.imag)
+            assert np.max(np.abs(got - op.symbol(w) * u)) < 1e-12
