@@ -61,6 +61,9 @@ extern "C" {
                       /* condition number > 1e3, FP32 elsewhere               */
 
 #define MGRIT_MAX_LEVELS 16
+#define MGRIT_COARSE_SL_CORRECTED 0
+#define MGRIT_COARSE_SL 1
+#define MGRIT_COARSE_REDISC 2
 #define MGRIT_MAX_HISTORY 128
 
 /* ---- parameters -------------------------------------------------------- */
@@ -84,6 +87,10 @@ typedef struct mgrit_params {
                     /* repeat while the FP32 error-equation residual is above   */
                     /* 1e-5 x the FP64 residual it corrects and still falls by  */
                     /* 0.8 per cycle, at most 16 (checked on the device)        */
+  int coarse_op;    /* coarse-grid operator: MGRIT_COARSE_SL_CORRECTED (0, the  */
+                    /* paper's Eq. MOL-SL-corrected-multilevel), MGRIT_COARSE_SL */
+                    /* (direct S_p, Sec. 3), MGRIT_COARSE_REDISC (SDIRK only:   */
+                    /* the fine method with step m^l dt, Sec. 5)                */
 } mgrit_params;
 
 /* ---- statistics -------------------------------------------------------- */

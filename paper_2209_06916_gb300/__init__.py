@@ -23,6 +23,7 @@ ERRORS = {
 }
 ERK, SDIRK = 0, 1
 FP64, MIXED = 0, 1
+SL_CORRECTED, SL, REDISC = 0, 1, 2  # coarse-grid operators
 MAX_HISTORY = 128
 
 
@@ -33,6 +34,7 @@ class Params(ctypes.Structure):
         ("rk_order_q", ctypes.c_int), ("m", ctypes.c_int), ("levels", ctypes.c_int),
         ("nu", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
         ("precision", ctypes.c_int), ("seed", ctypes.c_uint64), ("inner_cycles", ctypes.c_int),
+        ("coarse_op", ctypes.c_int),
     ]
 
 
@@ -152,10 +154,10 @@ def _check(code, what):
 
 
 def make_params(nx, nt, cfl, p, kind=ERK, q=0, m=4, levels=2, nu=1, tol=1e-10, max_iter=30,
-                precision=FP64, seed=0, alpha=1.0, inner_cycles=0):
+                precision=FP64, seed=0, alpha=1.0, inner_cycles=0, coarse_op=SL_CORRECTED):
     return Params(nx=nx, nt=nt, cfl=cfl, alpha=alpha, order_p=p, rk_kind=kind, rk_order_q=q, m=m,
                   levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed,
-                  inner_cycles=inner_cycles)
+                  inner_cycles=inner_cycles, coarse_op=coarse_op)
 
 
 class Solver:

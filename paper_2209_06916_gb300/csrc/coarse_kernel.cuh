@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
       } else {
         sl_gather<T, TC, P, P1, LP>(x, cur ? w01 : w00, cur ? w11 : w10, l0, npc, A.w);
       }
-      banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
+      if (!A.nosolve) banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
     }
     if (A.g) __pipeline_wait_prior(0);  // this thread's chunk of the RHS row has landed
     T* nxt = (cur ? sv0 : sv1) + base;

@@ -55,6 +55,14 @@ struct LevelData {
   BandFactor bf;
   double slw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double kappa = 1.0;
+  // rediscretised coarse operator (SDIRK with step m^l dt): SDIRK step
+  // parameters in FP64 and, in MIXED, FP32
+  bool redisc = false;
+  bool nosolve = false;  // direct SL coarse operator: no correction solve
+  std::unique_ptr<SdirkParams<double>> rd;
+  std::unique_ptr<SdirkParams<float>> rdf;
+  double* rd_Mt[2] = {nullptr, nullptr};
+  float* rdf_Mt[2] = {nullptr, nullptr};
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
 };
@@ -413,6 +421,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   cp.jlo = -(p + 1) / 2;
   cp.kshift = (int)(((Lv.kshift % h->nx) + h->nx) % h->nx);
   cp.shift = 0;
+  cp.nosolve = Lv.nosolve ? 1 : 0;
   for (int a = 0; a <= p; ++a) cp.w[a] = Lv.slw[a];
   for (int d = 0; d < 2; ++d) {
     dev_free(h, Lv.Mt_dev[d]);
@@ -443,6 +452,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
       q.kshift = cp.kshift;
       q.shift = cp.shift;
       q.m = cp.m;
+      q.nosolve = cp.nosolve;
       for (int a = 0; a <= p; ++a) q.w[a] = (float)cp.w[a];
     };
     geom(Lv.cpfd);
@@ -498,6 +508,31 @@ static std::vector<GeomC> coarse_geometries(mgrit_handle* h, int max_out) {
   for (auto& x : all)
     if ((int)out.size() < max_out) out.push_back(x.second);
   return out;
+}
+
+static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
+                              double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
+                              std::string* why, bool buffers, double cfl);
+
+// Rediscretised coarse operator of level l: the fine SDIRK method with the
+// coarse step m^l dt (c_l = m^l c), as SDIRK step parameters for the level's
+// intervals (the coarsest: one vector).
+static int build_redisc(mgrit_handle* h, int l, bool buffers, std::string* why) {
+  LevelData& Lv = h->lev[l];
+  const bool coarsest = (l == h->L - 1);
+  const double cl = h->prm.cfl * std::pow((double)h->m, (double)l);
+  for (int d = 0; d < 2; ++d) {
+    dev_free(h, Lv.rd_Mt[d]);
+    Lv.rd_Mt[d] = nullptr;
+    dev_free(h, Lv.rdf_Mt[d]);
+    Lv.rdf_Mt[d] = nullptr;
+  }
+  int rc = build_sdirk_params(h, coarsest ? 1 : Lv.K, &Lv.rd, Lv.rd_Mt,
+                              (h->prm.precision == MGRIT_MIXED && !coarsest) ? &Lv.rdf : nullptr, Lv.rdf_Mt, why,
+                              buffers, cl);
+  if (rc) return rc;
+  Lv.redisc = true;
+  return MGRIT_OK;
 }
 
 static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long long k, double eps,
@@ -679,7 +714,7 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
           ++o;
         }
       }
-      if (sp->result != 0 || sp->rscale != 1.0) {
+      {  // end of step: the result copy and/or the RHS add write slot 0
         if ((R & 1u) && !sp->resb) {
           sp->resb = 1;
           changed = true;
@@ -843,12 +878,12 @@ static void fold_solve_scale(SdirkParams<double>* sp) {
 
 // Geometry-free part of the level-0 SDIRK operator: the step programme with
 // its barrier schedule, L_p taps, the factorised stage matrix.
-static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why) {
+static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why, double cfl) {
   const mgrit_params& P = h->prm;
   const int p = P.order_p;
   std::memset((void*)sp, 0, sizeof(*sp));
   double gamma = 0.0;
-  if (!sdirk_program(P.rk_order_q, P.cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
+  if (!sdirk_program(P.rk_order_q, cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
   Stencil L = upwind_taps(p);
   sp->p1 = L.width();
   sp->llo = L.lo;
@@ -857,7 +892,7 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
     return MGRIT_ERR_UNSUPPORTED;
   }
   for (int i = 0; i < L.width(); ++i) sp->ltaps[i] = L.a[i];
-  Stencil A = stencil_add(stencil_identity(), L, gamma * P.cfl);
+  Stencil A = stencil_add(stencil_identity(), L, gamma * cfl);
   if (!band_factor(A, bf, why)) return MGRIT_ERR_UNSTABLE;
   const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
   if (bf->hc > HC || bf->ha > HA || bf->shift != 0) {
@@ -947,10 +982,11 @@ static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const
 // best-scored candidate; decisions are cached per (n_x, K, p, q, precision).
 static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
                               double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
-                              std::string* why, bool buffers = false) {
+                              std::string* why, bool buffers, double cfl) {
   SdirkParams<double> op;
   BandFactor bf;
-  int rc = sdirk_operator(h, &op, &bf, why);
+  if (cfl <= 0.0) cfl = h->prm.cfl;
+  int rc = sdirk_operator(h, &op, &bf, why, cfl);
   if (rc) return rc;
   const int elem = outf ? 4 : 8;
   auto smem_of = [&](const Geom& g) {
@@ -963,8 +999,8 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
   }
   const bool seq = (K == 1);
   char keyb[160];
-  std::snprintf(keyb, sizeof(keyb), "sdirk:n=%lld:K=%lld:p=%d:q=%d:b=%d", (long long)h->nx, (long long)K,
-                h->prm.order_p, h->prm.rk_order_q, elem);
+  std::snprintf(keyb, sizeof(keyb), "sdirk:n=%lld:K=%lld:p=%d:q=%d:b=%d:c=%.3g", (long long)h->nx, (long long)K,
+                h->prm.order_p, h->prm.rk_order_q, elem, cfl);
   const std::string key(keyb);
   Geom best = cand[0];
   Geom cached;
@@ -1025,7 +1061,7 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
 
 static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) {
   int rc = build_sdirk_params(h, h->lev[0].K, &h->sd0, h->sd_Mt,
-                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers);
+                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers, -1.0);
   if (rc) return rc;
   h->sdirk = true;
   return MGRIT_OK;
@@ -1038,6 +1074,10 @@ static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) 
 // in; cached per (n_x, intervals, m, p, precision, solve precision).
 static int tune_coarse(mgrit_handle* h, int l) {
   LevelData& Lv = h->lev[l];
+  if (Lv.redisc) {
+    std::string why;
+    return build_redisc(h, l, true, &why);
+  }
   const bool coarsest = (l == h->L - 1);
   const bool f32 = h->mixed && !coarsest;
   std::vector<GeomC> cand = coarse_geometries(h, 6);
@@ -1275,8 +1315,38 @@ static int l0_fres(mgrit_handle* h) {
   return check_launch();
 }
 
+// A coarse-level launch with a rediscretised (SDIRK) operator: the SDIRK step
+// kernel with the coarse kernel's RHS and output conventions.
+template <typename T>
+static int redisc_launch(mgrit_handle* h, int l, const SdirkParams<T>& base, int mode, int zero_start,
+                         const T* start, T* out, const T* sub, int nsteps, int64_t K, T* g, double* partial) {
+  SdirkParams<T> sp = base;
+  sp.mode = mode;
+  sp.zero_start = zero_start;
+  sp.start = start;
+  sp.out = out;
+  sp.sub = sub;
+  sp.rhs = nullptr;
+  sp.g = g;
+  sp.m = h->m;
+  sp.nsteps = nsteps;
+  sp.K = K;
+  sp.traj = nullptr;
+  sp.every = 0;
+  sp.partial = partial;
+  const double fl = sdirk_flops(sp, h->nx, K, nsteps);
+  ProfScope ps(h, 1, fl);
+  ProfScope psl(h, 4 + std::min(l, kProfCats - 6), fl);
+  if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  ++h->launches;
+  return check_launch();
+}
+
 static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const double* start,
                          double* out, const double* sub, double* parent, int nsteps, int64_t K, double* g) {
+  if (h->lev[l].redisc)
+    return redisc_launch(h, l, *h->lev[l].rd, mode, zero_start, start, out, sub, nsteps, K, g,
+                         mode == kModeFRES ? h->partials : nullptr);
   CoarseParams<double> cp = h->lev[l].cp;
   cp.mode = mode;
   cp.zero_start = zero_start;
@@ -1463,6 +1533,7 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess, bool want_norm = false) {
 static int coarse_launch_f(mgrit_handle* h, int l, int mode, int zero_start, const float* start, float* out,
                            const float* sub, float* parent, int nsteps, int64_t K, float* g) {
   LevelData& Lv = h->lev[l];
+  if (Lv.redisc) return redisc_launch(h, l, *Lv.rdf, mode, zero_start, start, out, sub, nsteps, K, g, nullptr);
   auto fill = [&](auto& cp) {
     cp.mode = mode;
     cp.zero_start = zero_start;
@@ -1842,6 +1913,10 @@ int mgrit_destroy(mgrit_handle* h) {
   pinned_put(h->hstate);
   dev_free(h, h->seq_tmp);
   for (auto& Lv : h->lev) {
+    for (int d = 0; d < 2; ++d) {
+      dev_free(h, Lv.rd_Mt[d]);
+      dev_free(h, Lv.rdf_Mt[d]);
+    }
     dev_free(h, Lv.uCf[0]);
     dev_free(h, Lv.uCf[1]);
     dev_free(h, Lv.gf);
@@ -1872,6 +1947,10 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.rk_kind == MGRIT_ERK && P.rk_order_q != P.order_p) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
   if (P.precision != MGRIT_FP64 && P.precision != MGRIT_MIXED) return MGRIT_ERR_INVALID_ARG;
+  if (P.coarse_op < MGRIT_COARSE_SL_CORRECTED || P.coarse_op > MGRIT_COARSE_REDISC) return MGRIT_ERR_INVALID_ARG;
+  // rediscretising an explicit method at m^l dt is unstable for practical
+  // m c (Sec. 5): offered for SDIRK only
+  if (P.coarse_op == MGRIT_COARSE_REDISC && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_UNSUPPORTED;
   // SDIRKq with q != p adds a phi_q D^{(q+1)}_2 correction term: q must be
   // odd (a symmetric even-order difference) and q <= p (inside the SL band)
   if (P.rk_kind == MGRIT_SDIRK && (P.rk_order_q > P.order_p || P.rk_order_q % 2 == 0))
@@ -1946,8 +2025,14 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   phi_recursion(P, L, &php, &phq, &ks, &es);
   std::string why;
   for (int l = 1; l < L; ++l) {
-    rc = build_coarse(h.get(), l, php[l], phq[l], ks[l], es[l], &why);
+    if (P.coarse_op == MGRIT_COARSE_SL) {  // direct SL operator: phi = 0, no correction solve
+      h->lev[l].nosolve = true;
+      rc = build_coarse(h.get(), l, 0.0, 0.0, ks[l], es[l], &why);
+    } else {
+      rc = build_coarse(h.get(), l, php[l], phq[l], ks[l], es[l], &why);
+    }
     if (rc) return rc;
+    if (P.coarse_op == MGRIT_COARSE_REDISC && (rc = build_redisc(h.get(), l, false, &why))) return rc;
   }
   // buffers
   const size_t row = sizeof(double) * (size_t)P.nx;
@@ -2069,7 +2154,7 @@ int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
     rc = coarse_launch(h, level, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[level + 1].g, Lv.uC[Lv.cur],
                        nullptr, h->m, Lv.K, Lv.g);
     if (!rc) {
-      launch_reduce_sum(h->partials, Lv.K * Lv.cp.csize, h->dnorm, h->st);
+      launch_reduce_sum(h->partials, Lv.K * (Lv.redisc ? Lv.rd->csize : Lv.cp.csize), h->dnorm, h->st);
       ++h->launches;
       rc = check_launch();
     }
@@ -2274,7 +2359,7 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
     if (nsteps > INT32_MAX) return MGRIT_ERR_INVALID_ARG;
     if (!h->sdseq) {
       std::string why;
-      rc = build_sdirk_params(h, 1, &h->sdseq, h->sdseq_Mt, nullptr, nullptr, &why, true);
+      rc = build_sdirk_params(h, 1, &h->sdseq, h->sdseq_Mt, nullptr, nullptr, &why, true, -1.0);
       if (rc) return rc;
     }
     rc = sdirk_launch(h, kModeSEQ, 0, h->du0, dout, nullptr, (int)nsteps, 1, every > 0 ? traj : nullptr,
@@ -2371,8 +2456,8 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   out[2] = Lv.eps;
   out[3] = Lv.phi;
   out[4] = Lv.phi_q;
-  out[6] = (double)Lv.cp.P;
-  out[7] = (double)Lv.cp.csize;
+  out[6] = (double)(Lv.redisc ? Lv.rd->P : Lv.cp.P);
+  out[7] = (double)(Lv.redisc ? Lv.rd->csize : Lv.cp.csize);
   return MGRIT_OK;
 }
 

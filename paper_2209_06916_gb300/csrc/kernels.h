@@ -84,6 +84,7 @@ struct CoarseParams {
   int zero_start;
   int nsteps;
   int m;
+  int nosolve;         // 1: Psi = S (direct SL coarse operator, no correction solve)
   int64_t K;
   const T* start;
   T* g;                // RHS rows; FOUT / SEQ overwrite the rows they consumed with the
@@ -127,11 +128,15 @@ struct SdirkParams {
   int opb[kSdirkMaxOps];   // 1: barrier over the vector's threads before the op (halo hazards)
   int resb;                // barrier before the end-of-step copy result -> slot 0
   T opc[kSdirkMaxOps];
-  int mode;            // kModeCF, kModeFRES, kModeAPPLY, kModeSEQ
+  int mode;            // kModeCF, kModeFRES, kModeFOUT, kModeAPPLY, kModeSEQ
   int zero_start, nsteps;
+  int m;               // coarsening factor (RHS row of step s of interval k: k m + s)
   int64_t K;
   const T* start;      // rows k
-  const T* rhs;        // optional C-point RHS, rows k+1 (CF / FRES)
+  const T* rhs;        // optional C-point RHS, rows k+1 (CF / FRES on level 0)
+  T* g;                // optional RHS at every step (a rediscretised coarse level, as in
+                       // CoarseParams): v <- Phi v + g_{k m + s}; FOUT / SEQ store each step's
+                       // value into the row it consumed
   T* out;              // CF / FRES: rows k+1; APPLY: rows k; SEQ: row 0
   const T* sub;        // FRES: rows k+1
   double* partial;     // FRES: one slot per CTA

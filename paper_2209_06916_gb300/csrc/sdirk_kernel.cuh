@@ -62,6 +62,19 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
     const T* src = A.start + k * nn + off;
     for (int i = t; i < npc; i += NT) slots[pos(i)] = src[i];
   }
+  if (A.mode == kModeFOUT && A.g) {
+    // the C-points themselves go to RHS row k m (and the last CTA's start[K]
+    // to row K m): rows the F post-relaxation does not read
+    const T* src = A.start + k * nn + off;
+    T* gr = A.g + k * A.m * nn + off;
+    for (int i = t; i < npc; i += NT) gr[i] = src[i];
+    if (k == A.K - 1) {
+      const T* s2 = A.start + A.K * nn + off;
+      T* g2 = A.g + A.K * A.m * nn + off;
+      for (int i = t; i < npc; i += NT) g2[i] = s2[i];
+    }
+  }
+  const int64_t gbase = (A.mode == kModeSEQ) ? 0 : k * A.m;
   // neighbouring chunks for the L_p halos (slot 0 of the owning CTA)
   const T* lnb = (t > 0) ? slots + base - (P + 1)
                          : cl.map_shared_rank(slots, (rank + C - 1) % C) + (NT - 1) * (P + 1);
@@ -129,11 +142,22 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
         for (int j = 0; j < P; ++j) dst[j] = x[j];
       }
     }
-    if (A.result != 0 || A.rscale != T(1)) {
-      if (A.resb) vec_sync(C);
+    const bool endcopy = A.result != 0 || A.rscale != T(1);
+    if ((endcopy || A.g) && A.resb) vec_sync(C);
+    if (endcopy) {
       const T* r = slots + (size_t)A.result * npad + base;
 #pragma unroll
       for (int j = 0; j < P; ++j) slots[base + j] = A.rscale * r[j];
+    }
+    if (A.g) {  // + g_{k m + s} on this thread's chunk; FOUT / SEQ keep the value in that row
+      T* gr = A.g + (gbase + s) * nn + off + t * P;
+      const bool keep = A.mode == kModeFOUT || A.mode == kModeSEQ;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const T v = slots[base + j] + gr[j];
+        slots[base + j] = v;
+        if (keep) gr[j] = v;
+      }
     }
     if (A.mode == kModeSEQ && A.traj && A.every > 0 && s % A.every == 0) {
       __syncthreads();
@@ -159,7 +183,7 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
       double tot = block_sum(sq, red);
       if (t == 0) A.partial[blockIdx.x] = tot;
     }
-  } else {
+  } else if (A.out) {  // APPLY: rows k; SEQ: row 0 (FOUT and a coarsest SEQ keep g instead)
     T* o = A.out + (A.mode == kModeAPPLY ? k * nn : 0) + off;
     for (int i = t; i < npc; i += NT) o[i] = slots[pos(i)];
   }

@@ -76,3 +76,13 @@ def test_binding_refuses_wrong_dtypes():
     import numpy as np
     with pytest.raises(ValueError):
         pkg._ptr(np.zeros(4, dtype=np.float32))
+
+
+def test_coarse_operator_choice_validated_on_host(lib):
+    bad = pkg.make_params(64, 128, 0.85, 1, coarse_op=7)
+    h = ctypes.c_void_p()
+    assert lib.mgrit_setup(ctypes.byref(bad), None, ctypes.byref(h)) == -1
+    # rediscretising ERK at m dt is unstable for practical m c (Sec. 5)
+    erk = pkg.make_params(64, 128, 0.85, 1, coarse_op=pkg.REDISC)
+    assert lib.mgrit_setup(ctypes.byref(erk), None, ctypes.byref(h)) == -8
+    assert not h.value
