@@ -203,6 +203,59 @@ def run_serving(args):
     return 0
 
 
+def run_coarse_ops(args):
+    """Coarse-grid operator comparison (Sec. 5.3 and Sec. 6.3.4 settings):
+    two-level MGRIT at n_x x n_t = 2^10 x 2^12, stop at 1e-10 or 20
+    iterations, random initial iterate, IC sin^4.  Per case: iterations,
+    the measured final-iteration factor and the time per solve.
+    Rediscretised vs corrected SL for SDIRK1+U1 and
+    SDIRK3+U3 (FCF); F- vs FCF-relaxation with the corrected SL operator
+    for ERK3+U3 at 0.85 c_max."""
+    import torch
+    import paper_2209_06916_gb300 as pkg
+    from workloads import ic_sin4
+    torch.cuda.set_device(0)
+    nx, nt = 1 << 10, 1 << 12
+    u0 = torch.tensor(ic_sin4(nx), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+
+    def case(kind, p, c, m, op, nu):
+        prm = pkg.make_params(nx, nt, c, p, kind=kind, m=m, levels=2, nu=nu, tol=1e-10, max_iter=20, seed=0,
+                              coarse_op=op)
+        s = pkg.Solver(prm, stream=stream.cuda_stream)
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        st = s.solve(u0, out, allow_unconverged=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            st = s.solve(u0, out, allow_unconverged=True)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+        s.close()
+        kname = "erk" if kind == pkg.ERK else "sdirk"
+        opname = {pkg.SL_CORRECTED: "sl_corrected", pkg.SL: "sl", pkg.REDISC: "redisc"}[op]
+        rows.append({"scheme": "%s%d+U%d" % (kname.upper(), p, p), "c": round(c, 5), "m": m, "nu": nu,
+                     "coarse_op": opname, "iterations": st["iterations"], "converged": st["converged"],
+                     "factor": st["conv_factor"], "ms": ms})
+
+    for p in (1, 3):
+        for m in (2, 4, 8, 16):
+            for c in (1.0, 4.0):
+                for op in (pkg.REDISC, pkg.SL_CORRECTED):
+                    case(pkg.SDIRK, p, c, m, op, 1)
+    cmax = 1.62589  # ERK3 + U3 stability limit (Table 2)
+    for m in (2, 4, 8, 16):
+        for nu in (0, 1):
+            case(pkg.ERK, 3, 0.85 * cmax, m, pkg.SL_CORRECTED, nu)
+    line = {"metric": "two-level MGRIT convergence factor, measured vs LFA", "unit": "factor", "n_gpus": 1,
+            "steps": args.steps, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "advection1d_coarse_operator_comparison", "nx": nx, "nt": nt, "levels": 2,
+                       "tol": 1e-10, "max_iter": 20}, "cases": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -233,7 +286,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5", "coarse_ops"])
     ap.add_argument("--count", type=int, default=512, help="c4: number of solves")
     ap.add_argument("--duration", type=float, default=5.0, help="c5: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=25.0, help="c5: extra seconds before the server stops")
@@ -249,6 +302,8 @@ def main():
         return run_batched(args)
     if args.workload == "c5" and args.impl == "ours":
         return run_serving(args)
+    if args.workload == "coarse_ops" and args.impl == "ours":
+        return run_coarse_ops(args)
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c2"])
     if args.impl == "reference":
         return run_reference(args)
