@@ -442,7 +442,8 @@ def main():
     achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
     info0 = s.level_info(0)
     if w["kind"] == "erk":
-        kname = "stencil_rows_kernel<double,%d> (level-0 composite Phi^m)" % int(info0[6])
+        kname = "%s<double,%d> (level-0 composite Phi^m)" % (
+            "stencil_rows_persistent" if info0[4] else "stencil_rows_kernel", int(info0[6]))
     else:
         kname = "sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves + L_p mat-vecs), clusters of %d" % (
             int(info0[6]), w["p"] + 1, int(info0[7]))

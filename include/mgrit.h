@@ -237,13 +237,15 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
  * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
  * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite
  * stencil taps (level 0, ERK), out[6] = chunk length of the in-block solves
- * (level 0, ERK: outputs per thread of the composite-stencil kernel),
+ * (level 0, ERK: outputs per thread of the composite-stencil kernel, and
+ * out[4] = 1 when its persistent form runs),
  * out[7] = CTAs per vector (thread-block cluster size) of the level's step
  * kernel (coarse levels; level 0 for SDIRK).  The step kernels' geometry is
  * measured at setup among the candidates that fit (cached per shape in the
  * process, and in the file MGRIT_AUTOTUNE_CACHE names); MGRIT_AUTOTUNE=0
  * takes the best-scored candidate unmeasured, MGRIT_GEOM="C:P" forces C CTAs
- * per vector and chunk length P where that geometry fits.
+ * per vector and chunk length P where that geometry fits, MGRIT_STENCIL=R
+ * (or R + 16: the persistent form) the level-0 stencil tile.
  */
 int mgrit_level_info(const mgrit_handle* h, int level, double out[8]);
 

@@ -999,8 +999,10 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
   }
   const bool seq = (K == 1);
   char keyb[160];
-  std::snprintf(keyb, sizeof(keyb), "sdirk:n=%lld:K=%lld:p=%d:q=%d:b=%d:c=%.3g", (long long)h->nx, (long long)K,
-                h->prm.order_p, h->prm.rk_order_q, elem, cfl);
+  // c enters the timing only through the scan lengths (carry decay): one
+  // significant digit of log2 c is enough to reuse a decision
+  std::snprintf(keyb, sizeof(keyb), "sdirk:n=%lld:K=%lld:p=%d:q=%d:b=%d:lc=%d", (long long)h->nx, (long long)K,
+                h->prm.order_p, h->prm.rk_order_q, elem, (int)std::lround(std::log2(cfl)));
   const std::string key(keyb);
   Geom best = cand[0];
   Geom cached;
@@ -1080,7 +1082,7 @@ static int tune_coarse(mgrit_handle* h, int l) {
   }
   const bool coarsest = (l == h->L - 1);
   const bool f32 = h->mixed && !coarsest;
-  std::vector<GeomC> cand = coarse_geometries(h, 6);
+  std::vector<GeomC> cand = coarse_geometries(h, 10);
   int fc, fp;
   if (cand.size() <= 1 || geom_forced(&fc, &fp)) return MGRIT_OK;
   char keyb[160];
@@ -1198,13 +1200,24 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
 // ---------------------------------------------------------------------------
 template <typename T>
 static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out, int64_t rows) {
+  // MGRIT_STENCIL=R or R+16 forces the tile (and the persistent form)
+  const char* force = std::getenv("MGRIT_STENCIL");
+  if (force) {
+    const int code = std::atoi(force);
+    const int R = code & 15;
+    if (R == 1 || R == 2 || R == 4 || R == 8) {
+      sp->tile_r = R;
+      sp->persistent = code >> 4 ? 1 : 0;
+      return MGRIT_OK;
+    }
+  }
   const char* on = std::getenv("MGRIT_AUTOTUNE");
   if ((on && on[0] == '0') || rows <= 0) return MGRIT_OK;
   // rows enter only through the wave count: bucket them by powers of two
   int64_t rb = 1;
   while (rb < rows) rb <<= 1;
   char keyb[128];
-  std::snprintf(keyb, sizeof(keyb), "stencil:nx=%lld:taps=%d:b=%d:rows<=%lld", (long long)sp->nx, sp->ntaps,
+  std::snprintf(keyb, sizeof(keyb), "stencil2:nx=%lld:taps=%d:b=%d:rows<=%lld", (long long)sp->nx, sp->ntaps,
                 (int)sizeof(T), (long long)rb);
   const std::string key(keyb);
   {
@@ -1212,7 +1225,8 @@ static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out
     tune_load();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      sp->tile_r = it->second;
+      sp->tile_r = it->second & 15;
+      sp->persistent = it->second >> 4;
       return MGRIT_OK;
     }
   }
@@ -1228,9 +1242,11 @@ static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out
   p.rows = rows;
   float best = 1e30f;
   int bestR = 0;
-  for (int R : {1, 2, 4, 8}) {
+  for (int code : {1, 2, 4, 8, 17, 18, 20, 24}) {  // R, + 16 for the persistent form
+    const int R = code & 15;
     if ((int64_t)kStencilThreadsHost * R > 2 * sp->nx && R > 1) continue;
     p.tile_r = R;
+    p.persistent = code >> 4;
     launch_stencil_rows(p, h->st);  // warm-up
     cudaEventRecord(e0, h->st);
     for (int i = 0; i < 3; ++i) launch_stencil_rows(p, h->st);
@@ -1240,14 +1256,15 @@ static int autotune_stencil(mgrit_handle* h, StencilParams<T>* sp, T* in, T* out
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      bestR = R;
+      bestR = code;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (check_launch()) return MGRIT_ERR_CUDA;
   if (bestR > 0) {
-    sp->tile_r = bestR;
+    sp->tile_r = bestR & 15;
+    sp->persistent = bestR >> 4;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_store(key, bestR);
   }
@@ -2447,6 +2464,7 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
       out[7] = (double)h->sd0->csize;
     } else {
       out[5] = (double)h->fineM->ntaps;
+      out[4] = (double)h->fineM->persistent;
       const int64_t nx = h->nx;  // untuned: the kernel's own choice by n_x
       out[6] = (double)(h->fineM->tile_r > 0 ? h->fineM->tile_r : nx >= 1024 ? 4 : nx >= 512 ? 2 : 1);
     }

@@ -11,6 +11,7 @@
 //   in kernels_sdirk.cu)
 //  reduce_sum_kernel    fixed-order sum of per-CTA partials (deterministic).
 //  random_cpoints_kernel  SplitMix64 random initial C-point iterate.
+#include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +73,81 @@ __global__ void __launch_bounds__(kStencilThreads)
   }
 }
 
+// Persistent form: gridDim.x CTAs (one wave) walk the rows x tiles in a
+// strided order; the input window of a CTA's next tile streams into the
+// second shared-memory buffer (cp.async) while the current tile computes, so
+// no wave starts with every CTA waiting on its loads.
+template <typename T, int R>
+__global__ void __launch_bounds__(kStencilThreads)
+    stencil_rows_persistent(const __grid_constant__ StencilParams<T> p, int ntx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int B = kStencilThreads;
+  const int W = B * R;
+  const int64_t nx = p.nx;
+  const int nload = W + p.ntaps - 1;
+  const int stride = (nload + 1) & ~1;
+  T* const buf0 = reinterpret_cast<T*>(smem_raw);
+  T* const buf1 = buf0 + stride;
+  const int64_t ntiles = p.rows * (int64_t)ntx;
+  auto fetch = [&](int64_t tl, T* dst) {
+    const int64_t row = tl / ntx;
+    const int64_t x0 = (tl - row * ntx) * W;
+    const T* in = p.in + row * nx;
+    int64_t g0 = (x0 + p.lo) % nx;
+    if (g0 < 0) g0 += nx;
+    for (int j = threadIdx.x; j < nload; j += B) {
+      int64_t gi = g0 + j;
+      while (gi >= nx) gi -= nx;
+      __pipeline_memcpy_async(&dst[j], &in[gi], sizeof(T));
+    }
+    __pipeline_commit();
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) fetch(tile, buf0);
+  int cur = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    if (next < ntiles)
+      fetch(next, cur ? buf0 : buf1);
+    else
+      __pipeline_commit();  // an empty group keeps the wait below uniform
+    __pipeline_wait_prior(1);  // this tile's window has landed
+    __syncthreads();
+    const int64_t row = tile / ntx;
+    const int64_t tx = tile - row * ntx;
+    const int64_t x0 = tx * W;
+    const T* sp = (cur ? buf1 : buf0) + threadIdx.x;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int t = 0; t < p.ntaps; ++t) {
+      const T a = p.taps[t];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = fma(a, sp[B * r + t], acc[r]);
+    }
+    double sq = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = x0 + threadIdx.x + (int64_t)B * r;
+      if (i < nx) {
+        T v = acc[r];
+        if (p.rhs) v += p.rhs[row * nx + i];
+        if (p.sub) v -= p.sub[row * nx + i];
+        p.out[row * nx + i] = v;
+        sq += (double)v * (double)v;
+      }
+    }
+    if (p.partial) {
+      double tot = block_sum(sq, red);
+      if (threadIdx.x == 0) p.partial[row * ntx + tx] = tot;
+    }
+    __syncthreads();  // the window is read before the next fetch refills it
+    cur ^= 1;
+  }
+  __pipeline_wait_prior(0);
+}
+
 static int stencil_r(int64_t nx) {
   if (nx >= 4 * kStencilThreads) return 4;
   if (nx >= 2 * kStencilThreads) return 2;
@@ -86,14 +162,33 @@ int stencil_tiles(int64_t nx, int tile_r) {
 template <typename T, int R>
 static int64_t launch_stencil_r(const StencilParams<T>& p, cudaStream_t st) {
   const int W = kStencilThreads * R;
-  size_t smem = (size_t)(W + p.ntaps - 1) * sizeof(T);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(stencil_rows_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         64 * 1024);
+    cudaFuncSetAttribute(stencil_rows_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(stencil_rows_persistent<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
     configured = true;
   }
-  dim3 grid((unsigned)p.rows, (unsigned)stencil_tiles(p.nx, R));
+  const int ntx = stencil_tiles(p.nx, R);
+  if (p.persistent) {
+    const int nload = W + p.ntaps - 1;
+    const size_t smem = (size_t)2 * ((nload + 1) & ~1) * sizeof(T);
+    static int nsm = 0;
+    if (!nsm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_rows_persistent<T, R>, kStencilThreads,
+                                                      smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    const int64_t ntiles = p.rows * (int64_t)ntx;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
+    stencil_rows_persistent<T, R><<<(unsigned)grid, kStencilThreads, smem, st>>>(p, ntx);
+    return ntiles;
+  }
+  size_t smem = (size_t)(W + p.ntaps - 1) * sizeof(T);
+  dim3 grid((unsigned)p.rows, (unsigned)ntx);
   stencil_rows_kernel<T, R><<<grid, kStencilThreads, smem, st>>>(p);
   return (int64_t)grid.x * grid.y;
 }

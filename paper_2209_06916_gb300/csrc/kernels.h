@@ -26,6 +26,8 @@ struct StencilParams {
   int lo;
   int ntaps;
   int tile_r;          // outputs per thread (tile = 256 * tile_r points); 0 = by n_x
+  int persistent;      // 1: one wave of CTAs looping over the tiles, the next tile's
+                       // window fetched (cp.async) while the current one computes
   T taps[kMaxTaps];
 };
 

@@ -135,3 +135,28 @@ def test_mixed_solve_forced_geometry(forced, C, P):
                 ref.append(u.copy())
         assert _rel(host(out), np.array(ref)) < 1e-8, (kind, C, P)
         s.close()
+
+
+@pytest.mark.parametrize("code", [1, 2, 4, 8, 17, 18, 20, 24])
+def test_level0_stencil_every_tile(monkeypatch, code):
+    """Each tile of the level-0 composite-stencil kernel, classic and
+    persistent (MGRIT_STENCIL = R, R + 16): a full solve matches the oracle's
+    MGRIT iteration for iteration, in FP64 and MIXED (FP32 stencil)."""
+    monkeypatch.setenv("MGRIT_STENCIL", str(code))
+    nx, nt, p, c, m, L = 2048, 8 * 8 * 4, 3, 0.85, 8, 3
+    u0 = ic_sin4(nx)
+    s = _solver(nx, nt, c, p, m, L, seed=5)
+    info = s.level_info(0)
+    assert (int(info[6]), int(info[4])) == (code & 15, code >> 4)
+    out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+    st = s.solve(dev(u0), out, allow_unconverged=True)
+    h = omg.Hierarchy(p, "erk", p, c, m, L)
+    ref = omg.solve(h, u0, nt, nu=1, tol=1e-10, max_iter=40, seed=5)
+    assert st["iterations"] == ref["iterations"]
+    assert np.max(np.abs(host(out) - ref["u"][::m])) < 1e-10
+    s.close()
+    sm = _solver(nx, nt, c, p, m, L, seed=5, precision=pkg.MIXED)
+    stm = sm.solve(dev(u0), out)
+    assert stm["converged"]
+    assert np.max(np.abs(host(out) - ref["u"][::m])) < 1e-8
+    sm.close()
