@@ -55,10 +55,12 @@ extern "C" {
 
 #define MGRIT_FP64 0  /* every kernel in FP64                                  */
 #define MGRIT_MIXED 1 /* FP32 relaxation sweeps inside FP64 iterative          */
-                      /* refinement: FP64 C-point residual and norm (level 0) */
-                      /* and FP64 coarsest sequential solve; correction       */
-                      /* solves in FP64 on levels whose correction matrix has */
-                      /* condition number > 1e3, FP32 elsewhere               */
+                      /* refinement: FP64 C-point residual and norm (level 0),*/
+                      /* FP64 coarsest sequential solve and FP64 truncation-  */
+                      /* error correction solves                              */
+#define MGRIT_MIXED_FAST 2 /* as MGRIT_MIXED, but the correction solves run  */
+                      /* in FP32 on levels whose correction matrix has        */
+                      /* condition number <= 1e3 (FP64 on the others)         */
 
 #define MGRIT_MAX_LEVELS 16
 #define MGRIT_COARSE_SL_CORRECTED 0
@@ -81,7 +83,7 @@ typedef struct mgrit_params {
   int nu;           /* CF sweeps in the pre-relaxation F(CF)^nu, 0 <= nu <= 4   */
   double tol;       /* stop when ||r_it|| <= tol ||r_0|| (default 1e-10)        */
   int max_iter;     /* iteration cap (default 30, Sec. 6.3)                     */
-  int precision;    /* MGRIT_FP64 or MGRIT_MIXED                                */
+  int precision;    /* MGRIT_FP64, MGRIT_MIXED or MGRIT_MIXED_FAST              */
   uint64_t seed;    /* seed of the random initial iterate (SplitMix64)          */
   int inner_cycles; /* MIXED: FP32 V-cycles per FP64 residual; 0: adaptive --  */
                     /* repeat while the FP32 error-equation residual is above   */

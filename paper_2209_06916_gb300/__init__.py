@@ -22,7 +22,7 @@ ERRORS = {
     -6: "CUDA", -7: "UNSTABLE", -8: "UNSUPPORTED",
 }
 ERK, SDIRK = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FAST = 0, 1, 2
 SL_CORRECTED, SL, REDISC = 0, 1, 2  # coarse-grid operators
 MAX_HISTORY = 128
 

@@ -29,6 +29,8 @@
 
 using namespace mg;
 
+static inline bool is_mixed(int precision) { return precision == MGRIT_MIXED || precision == MGRIT_MIXED_FAST; }
+
 namespace {
 
 struct LevelData {
@@ -439,7 +441,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   cp.c.Mt = Lv.Mt_dev[0];
   cp.a.Mt = Lv.Mt_dev[1];
   cp.m = h->m;
-  if (P.precision == MGRIT_MIXED) {
+  if (is_mixed(P.precision)) {
     auto geom = [&](auto& q) {
       std::memset((void*)&q, 0, sizeof(q));
       q.n = cp.n;
@@ -474,7 +476,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
 // Candidate geometries of the coarse kernel on this handle's vectors: the
 // SL window (P + p + 1 points) must lie within two neighbouring CTAs.
 static std::vector<GeomC> coarse_geometries(mgrit_handle* h, int max_out) {
-  const int elem = h->prm.precision == MGRIT_MIXED ? 4 : 8;
+  const int elem = is_mixed(h->prm.precision) ? 4 : 8;
   std::vector<std::pair<double, GeomC>> all;
   for (int C = 1; C <= 16; C *= 2) {
     if (h->nx % C) continue;
@@ -528,7 +530,7 @@ static int build_redisc(mgrit_handle* h, int l, bool buffers, std::string* why) 
     Lv.rdf_Mt[d] = nullptr;
   }
   int rc = build_sdirk_params(h, coarsest ? 1 : Lv.K, &Lv.rd, Lv.rd_Mt,
-                              (h->prm.precision == MGRIT_MIXED && !coarsest) ? &Lv.rdf : nullptr, Lv.rdf_Mt, why,
+                              (is_mixed(h->prm.precision) && !coarsest) ? &Lv.rdf : nullptr, Lv.rdf_Mt, why,
                               buffers, cl);
   if (rc) return rc;
   Lv.redisc = true;
@@ -560,7 +562,7 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   Lv.kappa = band_condition(A);
   // MIXED: FP32 storage and SL gather; the correction solve in FP64 where an
   // FP32 solve would lose more than about four of its seven digits
-  if (P.precision == MGRIT_MIXED) Lv.solve64 = Lv.kappa > 1e3;
+  if (is_mixed(P.precision)) Lv.solve64 = P.precision == MGRIT_MIXED || Lv.kappa > 1e3;
   Lv.kshift = k;
   Lv.eps = eps;
   Lv.phi = phi_p;
@@ -1063,7 +1065,7 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
 
 static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) {
   int rc = build_sdirk_params(h, h->lev[0].K, &h->sd0, h->sd_Mt,
-                              h->prm.precision == MGRIT_MIXED ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers, -1.0);
+                              is_mixed(h->prm.precision) ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers, -1.0);
   if (rc) return rc;
   h->sdirk = true;
   return MGRIT_OK;
@@ -1963,7 +1965,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.rk_kind != MGRIT_ERK && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_kind == MGRIT_ERK && P.rk_order_q != P.order_p) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
-  if (P.precision != MGRIT_FP64 && P.precision != MGRIT_MIXED) return MGRIT_ERR_INVALID_ARG;
+  if (P.precision != MGRIT_FP64 && !is_mixed(P.precision)) return MGRIT_ERR_INVALID_ARG;
   if (P.coarse_op < MGRIT_COARSE_SL_CORRECTED || P.coarse_op > MGRIT_COARSE_REDISC) return MGRIT_ERR_INVALID_ARG;
   // rediscretising an explicit method at m^l dt is unstable for practical
   // m c (Sec. 5): offered for SDIRK only
@@ -2026,7 +2028,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     h->fineM_taps_raw = stepM.width();
     rc = set_stencil(h->fineM.get(), stepM, P.nx);
     if (rc) return rc;
-    if (P.precision == MGRIT_MIXED) {
+    if (is_mixed(P.precision)) {
       h->fineMf.reset(new StencilParams<float>());
       rc = set_stencil(h->fineMf.get(), stepM, P.nx);
       if (rc) return rc;
@@ -2067,7 +2069,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
       CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
     }
   }
-  if (P.precision == MGRIT_MIXED) {
+  if (is_mixed(P.precision)) {
     h->mixed = true;
     const size_t rowf = sizeof(float) * (size_t)P.nx;
     auto allocf = [&](float** p, size_t bytes) -> int {

@@ -46,7 +46,7 @@ extern "C" int64_t mgrit_estimate_bytes(const mgrit_params* p) {
     N /= p->m;
   }
   int64_t bytes = rows * p->nx * 8;
-  if (p->precision == MGRIT_MIXED) bytes += rows * p->nx * 4 + (N + 2) * p->nx * 8;
+  if (p->precision == MGRIT_MIXED || p->precision == MGRIT_MIXED_FAST) bytes += rows * p->nx * 4 + (N + 2) * p->nx * 8;
   return bytes + (4 << 20);
 }
 

@@ -55,6 +55,7 @@ def test_strerror_texts(lib):
     dict(nx=64, nt=128, cfl=-1.0, p=1),            # c <= 0
     dict(nx=64, nt=128, cfl=0.85, p=3, q=1),       # ERK needs q = p
     dict(nx=64, nt=128, cfl=0.85, p=1, nu=7),      # nu range
+    dict(nx=64, nt=128, cfl=0.85, p=1, precision=3),  # precision mode
     dict(nx=8 * 20000, nt=128, cfl=0.85, p=1),     # no chunk geometry (n > 16 CTAs x 256 x 32)
 ])
 def test_invalid_parameters_rejected_on_host(lib, kw):

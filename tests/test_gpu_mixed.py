@@ -46,7 +46,7 @@ def test_mixed_solve_reaches_fp64_accuracy(kind, p, q, c, m, levels, nx, nt, inn
     k = pkg.ERK if kind == "erk" else pkg.SDIRK
     stream = torch.cuda.current_stream().cuda_stream
     res = {}
-    for prec in (pkg.FP64, pkg.MIXED):
+    for prec in (pkg.FP64, pkg.MIXED, pkg.MIXED_FAST):
         prm = pkg.make_params(nx, nt, c, p, kind=k, q=q, m=m, levels=levels, tol=1e-10, max_iter=40,
                               precision=prec, seed=3, inner_cycles=inner)
         s = pkg.Solver(prm, stream=stream)
@@ -58,12 +58,13 @@ def test_mixed_solve_reaches_fp64_accuracy(kind, p, q, c, m, levels, nx, nt, inn
     seq = _seq(p, kind, q, c, u0, nt, m)
     scale = np.max(np.abs(seq))
     e64 = np.max(np.abs(res[pkg.FP64][0] - seq)) / scale
-    emx = np.max(np.abs(res[pkg.MIXED][0] - seq)) / scale
-    st = res[pkg.MIXED][1]
-    assert st["converged"] and st["inner_cycles"] >= st["outer_iterations"] * inner
-    # same accuracy class as FP64: within 10x of the FP64 solver's error and
-    # below the 1e-8 bound used for FP64 solves
-    assert emx < max(10 * e64, 1e-9) and emx < 1e-8, (e64, emx)
+    for prec in (pkg.MIXED, pkg.MIXED_FAST):
+        emx = np.max(np.abs(res[prec][0] - seq)) / scale
+        st = res[prec][1]
+        assert st["converged"] and st["inner_cycles"] >= st["outer_iterations"] * inner
+        # same accuracy class as FP64: within 10x of the FP64 solver's error
+        # and below the 1e-8 bound used for FP64 solves
+        assert emx < max(10 * e64, 1e-9) and emx < 1e-8, (prec, e64, emx)
 
 
 @pytest.mark.parametrize("kind,p,q,c,m,levels,nx,nt", [("erk", 3, 3, 0.85, 8, 4, 512, 8 ** 3 * 2),
