@@ -87,8 +87,10 @@ typedef struct mgrit_params {
   uint64_t seed;    /* seed of the random initial iterate (SplitMix64)          */
   int inner_cycles; /* MIXED: FP32 V-cycles per FP64 residual; 0: adaptive --  */
                     /* repeat while the FP32 error-equation residual is above   */
-                    /* 1e-5 x the FP64 residual it corrects and still falls by  */
-                    /* 0.8 per cycle, at most 16 (checked on the device)        */
+                    /* t x the FP64 residual r it corrects, t = max(1e-2, 0.01  */
+                    /* tol r_0 / r) (at most 0.1), and still falls by 0.8 per   */
+                    /* cycle, at most 16 (checked on the device); the 1e-2      */
+                    /* base can be set with the environment MGRIT_INNER_TOL     */
   int coarse_op;    /* coarse-grid operator: MGRIT_COARSE_SL_CORRECTED (0, the  */
                     /* paper's Eq. MOL-SL-corrected-multilevel), MGRIT_COARSE_SL */
                     /* (direct S_p, Sec. 3), MGRIT_COARSE_REDISC (SDIRK only:   */

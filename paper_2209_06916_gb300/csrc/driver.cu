@@ -112,6 +112,7 @@ struct mgrit_handle {
   int64_t npart = 0;
   double* dnorm = nullptr;
   double* dnorm_f = nullptr;  // MIXED: squared norm of the FP32 inner residual
+  double inner_tol = kInnerTol;  // MIXED: target of one adaptive inner solve (MGRIT_INNER_TOL)
   double* hnorm = nullptr;  // pinned
   double* du0 = nullptr;
   int64_t launches = 0;
@@ -2008,6 +2009,10 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   h->L = L;
   h->nx = P.nx;
   h->m = P.m;
+  if (const char* it = std::getenv("MGRIT_INNER_TOL")) {
+    const double v = std::atof(it);
+    if (v > 0.0 && v < 1.0) h->inner_tol = v;
+  }
   cudaGetDevice(&h->device);
   h->lev.resize(L);
   int64_t N = P.nt;
@@ -2271,6 +2276,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
         if (rc) return rc;
         ++st.inner_cycles;
         const double rho0 = nrm;
+        const double target = inner_target(h->prm.tol, st.rnorm0, rho0, h->inner_tol);
         double prev = rho0;
         int count = 1;
         bool go = count < kInnerMax;
@@ -2282,7 +2288,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
           CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm_f, sizeof(double), cudaMemcpyDeviceToHost, h->st));
           CUDA_TRY(cudaStreamSynchronize(h->st));
           const double rho = std::sqrt(std::max(0.0, *h->hnorm));
-          go = inner_continue(rho, prev, rho0, count, kInnerMax, kInnerTol);
+          go = inner_continue(rho, prev, rho0, count, kInnerMax, target);
           prev = rho;
         }
       }
@@ -2502,7 +2508,7 @@ int mgrit_solve_async(mgrit_handle* h, const double* u0) {
   std::memset(&init, 0, sizeof(init));
   init.tol = h->prm.tol;
   init.max_iter = h->prm.max_iter;
-  init.in_tol = kInnerTol;
+  init.in_base = h->inner_tol;
   init.in_max = kInnerMax;
   *h->hstate = init;
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(DevSolveState), cudaMemcpyHostToDevice, h->st));

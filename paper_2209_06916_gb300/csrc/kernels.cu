@@ -304,6 +304,7 @@ __global__ void inner_init_kernel(DevSolveState* s, const double* dnorm64_sq, cu
   const double rho0 = sqrt(fmax(0.0, dnorm64_sq[0]));
   s->in_rho0 = rho0;
   s->in_prev = rho0;
+  s->in_tol = inner_target(s->tol, s->r0, rho0, s->in_base);
   s->in_count = 1;
   s->in_total += 1;
   cudaGraphSetConditional(hnd, s->in_count < s->in_max ? 1 : 0);

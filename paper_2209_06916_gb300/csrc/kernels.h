@@ -173,16 +173,26 @@ struct DevSolveState {
   double r0, rnorm, tol;
   int it, max_iter, converged, status, hist_len, pad;
   // MIXED adaptive inner solve: FP32 V-cycles of one refinement step repeat
-  // while the FP32 residual of the error equation is above in_tol times the
-  // FP64 residual it corrects and still falls by 0.8 per cycle, at most
-  // in_max cycles
-  double in_rho0, in_prev, in_tol;
+  // while the FP32 residual of the error equation is above the step's
+  // target (inner_target) times the FP64 residual it corrects and still
+  // falls by 0.8 per cycle, at most in_max cycles
+  double in_rho0, in_prev, in_tol, in_base;
   int in_count, in_max, in_total, in_pad;
   double hist[128];
 };
 constexpr int kInnerMax = 16;
-constexpr double kInnerTol = 1e-5;
+constexpr double kInnerTol = 1e-2;
 constexpr double kInnerStall = 0.8;
+// Target of one inner solve, relative to the FP64 residual it corrects:
+// `base` (the handle's inner tolerance), or what the refinement still needs
+// to end two orders under its stop level (0.01 tol r0 / current residual),
+// whichever is larger.  One refinement step cuts the error by at most about
+// kappa eps_FP32; an inner solve driven further leaves the error behind the
+// residual, so the target never goes below `base`.
+__host__ __device__ inline double inner_target(double tol, double r0, double rho0, double base) {
+  const double need = rho0 > 0.0 ? 0.01 * tol * r0 / rho0 : base;
+  return need > base ? (need < 0.1 ? need : 0.1) : base;
+}
 // First residual: r0, history[0]; sets the loop condition (0 when already
 // converged).  Check: after each iteration, appends the norm and sets the
 // condition to continue, or records converged / diverged / not converged.
