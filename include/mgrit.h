@@ -237,6 +237,16 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
                          int64_t every, double* traj);
 
 /*
+ * mgrit_fine_propagate_async -- mgrit_fine_propagate without the final
+ * synchronisation: enqueues the sequential stepping on the handle's stream
+ * and returns.  d_u0, d_out: device pointers (nx doubles), read / written in
+ * stream order; MGRIT_ERR_INVALID_ARG for host pointers.  The caller
+ * synchronises the stream.  The paper has no counterpart (it is the
+ * baseline's launch form for batches).
+ */
+int mgrit_fine_propagate_async(mgrit_handle* h, const double* d_u0, double* d_out, int64_t nsteps);
+
+/*
  * mgrit_level_info -- host-side derived data of a level (no GPU work):
  * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
  * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite
@@ -328,6 +338,14 @@ int mgrit_batch_solve(mgrit_batch* b, const double* const* u0s, mgrit_stats* sta
 int mgrit_batch_get(mgrit_batch* b, int64_t i, double* u_out);
 /* Sum of nx * nt over the batch. */
 int64_t mgrit_batch_dof(const mgrit_batch* b);
+
+/*
+ * mgrit_batch_sequential -- the GPU sequential-stepping baseline of a batch:
+ * solve i stepped nt_i times from d_u0s[i] into d_outs[i] (device, nx_i
+ * doubles each), all solves enqueued over the batch's stream pool at once,
+ * then synchronised.  The paper has no counterpart.
+ */
+int mgrit_batch_sequential(mgrit_batch* b, const double* const* d_u0s, double* const* d_outs);
 int mgrit_batch_destroy(mgrit_batch* b);
 
 typedef struct mgrit_request_result {

@@ -107,6 +107,8 @@ def load_library(path=LIB_PATH):
     lib.mgrit_level_io.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int64)]
     lib.mgrit_fine_propagate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P]
+    lib.mgrit_fine_propagate_async.argtypes = [P, P, P, ctypes.c_int64]
+    lib.mgrit_batch_sequential.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]
     lib.mgrit_level_info.argtypes = [P, ctypes.c_int, dp]
     lib.mgrit_launch_count.argtypes = [P]
     lib.mgrit_launch_count.restype = ctypes.c_int64
@@ -259,6 +261,11 @@ class Solver:
         _check(self.lib.mgrit_fine_propagate(self.h, _ptr(u0), _ptr(u_out), nsteps, every, _ptr(traj)),
                "mgrit_fine_propagate")
 
+    def fine_propagate_async(self, u0, u_out, nsteps):
+        """Enqueue sequential stepping on the handle's stream (device tensors)."""
+        _check(self.lib.mgrit_fine_propagate_async(self.h, _ptr(u0), _ptr(u_out), nsteps),
+               "mgrit_fine_propagate_async")
+
     def launch_count(self):
         return int(self.lib.mgrit_launch_count(self.h))
 
@@ -304,6 +311,14 @@ class Batch:
         if code != MGRIT_OK and not (allow_unconverged and code in (-3, -4)):
             raise MgritError(code, "mgrit_batch_solve")
         return [s.to_dict() for s in stats]
+
+    def sequential(self, u0s, outs):
+        """GPU sequential stepping of every solve (the baseline): u0s and outs
+        are lists of device tensors (nx values each); all solves run
+        concurrently over the batch's streams."""
+        self._seq = (list(u0s), list(outs))
+        _check(self.lib.mgrit_batch_sequential(self.b, _ptr_array(self._seq[0]), _ptr_array(self._seq[1])),
+               "mgrit_batch_sequential")
 
     def get(self, i):
         p = self.params[i]

@@ -2371,8 +2371,21 @@ int mgrit_level_io(mgrit_handle* h, int level, int field, double* ptr, int to_de
   return MGRIT_OK;
 }
 
+static int fine_propagate_impl(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps, int64_t every,
+                               double* traj, bool sync);
+
 int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps, int64_t every,
                          double* traj) {
+  return fine_propagate_impl(h, u0, u_out, nsteps, every, traj, true);
+}
+
+int mgrit_fine_propagate_async(mgrit_handle* h, const double* d_u0, double* d_out, int64_t nsteps) {
+  if (!h || !d_u0 || !d_out || !is_device_ptr(d_u0) || !is_device_ptr(d_out)) return MGRIT_ERR_INVALID_ARG;
+  return fine_propagate_impl(h, d_u0, d_out, nsteps, 0, nullptr, false);
+}
+
+static int fine_propagate_impl(mgrit_handle* h, const double* u0, double* u_out, int64_t nsteps, int64_t every,
+                               double* traj, bool sync) {
   if (!h || !u0 || !u_out || nsteps < 0 || every < 0) return MGRIT_ERR_INVALID_ARG;
   const int64_t nx = h->nx;
   if (h->sdirk) {
@@ -2391,7 +2404,7 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
                       (int)every, 3, h->sdseq.get());
     if (rc) return rc;
     if (!out_dev && (rc = copy_any(u_out, dout, row, h->st))) return rc;
-    CUDA_TRY(cudaStreamSynchronize(h->st));
+    if (sync) CUDA_TRY(cudaStreamSynchronize(h->st));
     return MGRIT_OK;
   }
   Stencil step = erk_step_stencil(h->prm.order_p, h->prm.rk_order_q, h->prm.cfl);
@@ -2457,7 +2470,7 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
     rc = copy_any(u_out, dout, row, h->st);
     if (rc) return rc;
   }
-  CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (sync) CUDA_TRY(cudaStreamSynchronize(h->st));
   return MGRIT_OK;
 }
 

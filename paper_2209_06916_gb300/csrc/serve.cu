@@ -113,6 +113,17 @@ extern "C" int mgrit_batch_get(mgrit_batch* b, int64_t i, double* u_out) {
   return mgrit_level_io(b->hs[i], 0, 0, u_out, 0, nullptr);
 }
 
+extern "C" int mgrit_batch_sequential(mgrit_batch* b, const double* const* d_u0s, double* const* d_outs) {
+  if (!b || !d_u0s || !d_outs) return MGRIT_ERR_INVALID_ARG;
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    int rc = mgrit_fine_propagate_async(b->hs[i], d_u0s[i], d_outs[i], b->prm[i].nt);
+    if (rc) return rc;
+  }
+  for (auto s : b->streams)
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MGRIT_ERR_CUDA;
+  return MGRIT_OK;
+}
+
 extern "C" int64_t mgrit_batch_dof(const mgrit_batch* b) {
   if (!b) return 0;
   int64_t s = 0;

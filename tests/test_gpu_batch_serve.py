@@ -55,6 +55,33 @@ def test_batch_results_equal_standalone(precision):
     b.close()
 
 
+def test_batch_sequential_equals_standalone_stepping():
+    """The batched sequential-stepping baseline (all solves at once over the
+    stream pool) gives each solve's standalone GPU sequential stepping bit for
+    bit, and that agrees with the oracle's stepping."""
+    from oracle import operators as oops
+    mix = batch_mix(8, seed=11, **SMALL)
+    prms = _params(mix, pkg.FP64)
+    u0s = [torch.tensor(ic_sin4_noise(d["nx"], seed=d["seed"]), dtype=torch.float64, device="cuda") for d in mix]
+    outs = [torch.empty(d["nx"], dtype=torch.float64, device="cuda") for d in mix]
+    b = pkg.Batch(prms, nstreams=3)
+    b.sequential(u0s, outs)
+    for i, (prm, d) in enumerate(zip(prms, mix)):
+        s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+        want = torch.empty_like(outs[i])
+        s.fine_propagate(u0s[i], want, prm.nt)
+        s.close()
+        assert torch.equal(outs[i], want), i
+        if i < 3:
+            fine = oops.FineOperator(d["p"], "erk", d["p"], d["cfl"])
+            u = u0s[i].cpu().numpy()
+            for _ in range(prm.nt):
+                u = fine.apply(u)
+            got = outs[i].cpu().numpy()
+            assert np.max(np.abs(got - u)) < 1e-12 * prm.nt * max(1.0, np.max(np.abs(u)))
+    b.close()
+
+
 def test_serving_continuous_batching():
     mix = batch_mix(16, seed=7, **SMALL)
     prms = _params(mix, pkg.MIXED)

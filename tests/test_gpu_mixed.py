@@ -35,6 +35,7 @@ CASES = [  # kind, p, q, c, m, levels, nx, nt, inner
     ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2, 2),
     ("sdirk", 3, 3, 5.0, 4, 3, 256, 16 * 8, 2),
     ("erk", 3, 3, 0.85, 8, 4, 512, 8 ** 3 * 2, 0),      # adaptive inner cycles
+    ("erk", 3, 3, 0.85, 8, 4, 2048, 8 ** 3 * 8, 0),     # long enough for FP32 noise to show in the error
     ("sdirk", 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2, 0),
     ("sdirk", 5, 5, 6.0, 4, 4, 256, 4 ** 3 * 4, 0),
 ]
