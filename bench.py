@@ -51,6 +51,23 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (ms): every rank gets the max (an all-reduce on
+    `device`; NCCL on GPUs, gloo on CPU).  Without a process group: ms."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(dof_per_rank, steps, max_ms, ws):
+    """Whole-job throughput of replicas (weak scaling): the DOF every rank
+    solved in `steps` steps, over the slowest rank's time."""
+    return ws * dof_per_rank * steps / (max_ms / 1e3)
+
+
 def clocks_sampler_start(path):
     try:
         f = open(path, "w")
@@ -389,10 +406,7 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     launches = s.launch_count() - launches0
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     u0_pin = torch.tensor(u0_h, dtype=torch.float64).pin_memory()
@@ -403,10 +417,7 @@ def main():
         s.solve(u0_pin, out_pin)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     # GPU sequential time-stepping of the same problem (the baseline), and the
     # accuracy of the MGRIT solution against it at the final time
     seq_out = torch.empty(nx, dtype=torch.float64, device="cuda")
@@ -456,7 +467,7 @@ def main():
 
     # accuracy of the benched solve against the FP64 ... (reported, not a gate)
     dof = nx * nt
-    value = ws * dof * args.steps / (ms / 1e3)
+    value = whole_job_value(dof, args.steps, ms, ws)
     cnt, kms, kfl = prof["stencil0"]
     achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
     info0 = s.level_info(0)
@@ -487,7 +498,7 @@ def main():
                        "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (
                            (2 * (nt // m + 1) + (nt // m + 1) + 2 * (nt // m ** 2 + 1)) * nx * 8 / 1e6)},
             "roofline": roof,
-            "e2e": {"value": ws * dof * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": whole_job_value(dof, args.steps, e2e_ms, ws), "unit": UNIT,
                     "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8},
             "gpu_launches": launches, "clocks": clocks,
             "sequential": None if seq_ms is None else {
