@@ -247,6 +247,16 @@ int mgrit_fine_propagate(mgrit_handle* h, const double* u0, double* u_out, int64
 int mgrit_fine_propagate_async(mgrit_handle* h, const double* d_u0, double* d_out, int64_t nsteps);
 
 /*
+ * mgrit_output_all -- every time point of the current level-0 iterate:
+ * row n of d_all (device, (nt + 1) x nx doubles, row-major) is u_n, the
+ * C-points u_{km} as they stand and the F-points u_{km+j} regenerated by
+ * F-relaxation from them (Sec. 2.2), all intervals at once.  Call it after
+ * a solve (or mgrit_set_initial).  MGRIT_ERR_INVALID_ARG for a host pointer
+ * or before any iterate exists.
+ */
+int mgrit_output_all(mgrit_handle* h, double* d_all);
+
+/*
  * mgrit_level_info -- host-side derived data of a level (no GPU work):
  * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
  * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite

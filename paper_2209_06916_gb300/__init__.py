@@ -108,6 +108,7 @@ def load_library(path=LIB_PATH):
                                    ctypes.POINTER(ctypes.c_int64)]
     lib.mgrit_fine_propagate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P]
     lib.mgrit_fine_propagate_async.argtypes = [P, P, P, ctypes.c_int64]
+    lib.mgrit_output_all.argtypes = [P, P]
     lib.mgrit_batch_sequential.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]
     lib.mgrit_level_info.argtypes = [P, ctypes.c_int, dp]
     lib.mgrit_launch_count.argtypes = [P]
@@ -260,6 +261,11 @@ class Solver:
     def fine_propagate(self, u0, u_out, nsteps, every=0, traj=None):
         _check(self.lib.mgrit_fine_propagate(self.h, _ptr(u0), _ptr(u_out), nsteps, every, _ptr(traj)),
                "mgrit_fine_propagate")
+
+    def output_all(self, d_all):
+        """Every time point of the current iterate into d_all (device tensor,
+        (nt + 1) x nx): the C-points and the F-points F-relaxed from them."""
+        _check(self.lib.mgrit_output_all(self.h, _ptr(d_all)), "mgrit_output_all")
 
     def fine_propagate_async(self, u0, u_out, nsteps):
         """Enqueue sequential stepping on the handle's stream (device tensors)."""

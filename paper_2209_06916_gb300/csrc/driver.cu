@@ -188,7 +188,7 @@ static int check_launch() {
 
 // Host check that an n-point vector has a chunk geometry of the step
 // kernels at all: C <= 16 CTAs of <= 256 threads with a chunk length P in
-// {8, 16, 32} (so n <= 131072, n a multiple of 8).
+// {4, 8, 16, 32} (so n <= 131072).
 static bool has_chunk_geometry(int64_t n) {
   for (int C = 1; C <= 16; C *= 2)
     for (int P : kChunkLens)
@@ -2471,6 +2471,56 @@ static int fine_propagate_impl(mgrit_handle* h, const double* u0, double* u_out,
     if (rc) return rc;
   }
   if (sync) CUDA_TRY(cudaStreamSynchronize(h->st));
+  return MGRIT_OK;
+}
+
+int mgrit_output_all(mgrit_handle* h, double* d_all) {
+  if (!h || !d_all || !is_device_ptr(d_all)) return MGRIT_ERR_INVALID_ARG;
+  if (!h->have_initial) return MGRIT_ERR_INVALID_ARG;
+  LevelData& L0 = h->lev[0];
+  const double* cpts = L0.uC[L0.cur];
+  const int64_t nx = h->nx, K = L0.K, m = h->m;
+  if (h->sdirk) {
+    // F-relaxation in the step kernel's FOUT mode: C-point k into row k m,
+    // the m - 1 steps after it into the following rows (RHS zero)
+    CUDA_TRY(cudaMemsetAsync(d_all, 0, sizeof(double) * (size_t)nx * (size_t)(K * m + 1), h->st));
+    SdirkParams<double> sp = *h->sd0;
+    sp.mode = kModeFOUT;
+    sp.zero_start = 0;
+    sp.start = cpts;
+    sp.out = nullptr;
+    sp.sub = nullptr;
+    sp.rhs = nullptr;
+    sp.g = d_all;
+    sp.m = (int)m;
+    sp.nsteps = (int)(m - 1);
+    sp.K = K;
+    sp.partial = nullptr;
+    sp.traj = nullptr;
+    sp.every = 0;
+    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+    ++h->launches;
+    if (int rc = check_launch()) return rc;
+  } else {
+    // C-points into rows k m, then F-point j of every interval at once: one
+    // step of the fine stencil on the rows k m + j - 1 (row stride m n_x)
+    CUDA_TRY(cudaMemcpy2DAsync(d_all, sizeof(double) * (size_t)(m * nx), cpts, sizeof(double) * (size_t)nx,
+                               sizeof(double) * (size_t)nx, (size_t)(K + 1), cudaMemcpyDeviceToDevice, h->st));
+    for (int64_t j = 1; j < m; ++j) {
+      StencilParams<double> sp = *h->fine1;
+      sp.in = d_all + (j - 1) * nx;
+      sp.out = d_all + j * nx;
+      sp.rhs = nullptr;
+      sp.sub = nullptr;
+      sp.partial = nullptr;
+      sp.rows = K;
+      sp.ld = m * nx;
+      launch_stencil_rows(sp, h->st);
+      ++h->launches;
+      if (int rc = check_launch()) return rc;
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->st));
   return MGRIT_OK;
 }
 

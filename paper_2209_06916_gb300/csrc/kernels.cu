@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(kStencilThreads)
   const int64_t nx = p.nx;
   const int64_t x0 = (int64_t)blockIdx.y * W;
   const int nload = W + p.ntaps - 1;
-  const T* in = p.in + row * nx;
+  const int64_t ld = p.ld ? p.ld : nx;
+  const T* in = p.in + row * ld;
   for (int j = threadIdx.x; j < nload; j += B) {
     int64_t gi = (x0 + p.lo + j) % nx;
     if (gi < 0) gi += nx;
@@ -61,9 +62,9 @@ __global__ void __launch_bounds__(kStencilThreads)
     const int64_t i = x0 + threadIdx.x + (int64_t)B * r;
     if (i < nx) {
       T v = acc[r];
-      if (p.rhs) v += p.rhs[row * nx + i];
-      if (p.sub) v -= p.sub[row * nx + i];
-      p.out[row * nx + i] = v;
+      if (p.rhs) v += p.rhs[row * ld + i];
+      if (p.sub) v -= p.sub[row * ld + i];
+      p.out[row * ld + i] = v;
       sq += (double)v * (double)v;
     }
   }
@@ -90,10 +91,11 @@ __global__ void __launch_bounds__(kStencilThreads)
   T* const buf0 = reinterpret_cast<T*>(smem_raw);
   T* const buf1 = buf0 + stride;
   const int64_t ntiles = p.rows * (int64_t)ntx;
+  const int64_t ld = p.ld ? p.ld : nx;
   auto fetch = [&](int64_t tl, T* dst) {
     const int64_t row = tl / ntx;
     const int64_t x0 = (tl - row * ntx) * W;
-    const T* in = p.in + row * nx;
+    const T* in = p.in + row * ld;
     int64_t g0 = (x0 + p.lo) % nx;
     if (g0 < 0) g0 += nx;
     for (int j = threadIdx.x; j < nload; j += B) {
@@ -132,9 +134,9 @@ __global__ void __launch_bounds__(kStencilThreads)
       const int64_t i = x0 + threadIdx.x + (int64_t)B * r;
       if (i < nx) {
         T v = acc[r];
-        if (p.rhs) v += p.rhs[row * nx + i];
-        if (p.sub) v -= p.sub[row * nx + i];
-        p.out[row * nx + i] = v;
+        if (p.rhs) v += p.rhs[row * ld + i];
+        if (p.sub) v -= p.sub[row * ld + i];
+        p.out[row * ld + i] = v;
         sq += (double)v * (double)v;
       }
     }

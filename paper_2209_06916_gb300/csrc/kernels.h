@@ -6,7 +6,7 @@
 namespace mg {
 
 constexpr int kMaxTaps = 1024;   // composite level-0 stencil taps (folded mod nx)
-constexpr int kMaxRounds = 11;   // chunk-scan rounds (up to 2048 chunks)
+constexpr int kMaxRounds = 5;    // in-warp chunk-scan rounds (distances 1..16)
 constexpr int kPMax = 64;        // chunk length of the in-block banded solves
 
 // ---------------------------------------------------------------------------
@@ -23,6 +23,7 @@ struct StencilParams {
   double* partial;
   int64_t nx;
   int64_t rows;
+  int64_t ld;          // row stride of in / out / rhs / sub in elements (0: nx)
   int lo;
   int ntaps;
   int tile_r;          // outputs per thread (tile = 256 * tile_r points); 0 = by n_x

@@ -324,3 +324,38 @@ def test_graph_solve_equals_eager_solve(kind, p, c, m, levels, nu, prec, nx, nt)
     assert sa["inner_cycles"] == sb["inner_cycles"]
     assert np.array_equal(a, b)
     assert np.allclose(sa["history"], sb["history"], rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# all time points (final F-relaxation, Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,p,q,c,m,levels,nx,nt", [
+    (pkg.ERK, 3, 3, 0.85, 8, 3, 256, 8 * 8 * 4),
+    (pkg.ERK, 1, 1, 0.85, 4, 2, 128, 256),
+    (pkg.SDIRK, 5, 3, 4.0, 16, 3, 512, 16 * 16 * 2),
+])
+def test_output_all_time_points(kind, p, q, c, m, levels, nx, nt):
+    """mgrit_output_all after a solve: rows k m are the returned C-points,
+    the rows between are the F-relaxation from them (the oracle's f_relax on
+    those C-points), and the whole trajectory matches sequential stepping to
+    the solve's accuracy."""
+    u0 = ic_sin4(nx)
+    s = solver(nx, nt, c, p, m, levels, kind=kind, q=q, tol=1e-11, max_iter=40)
+    cpts = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+    s.solve(dev(u0), cpts)
+    allp = torch.empty((nt + 1, nx), dtype=torch.float64, device="cuda")
+    s.output_all(allp)
+    got, C = host(allp), host(cpts)
+    assert np.array_equal(got[::m], C)
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    fine = oops.FineOperator(p, kname, q, c)
+    want = np.zeros((nt + 1, nx))
+    want[::m] = C
+    omg.f_relax(fine, want, np.zeros_like(want), m)
+    assert np.max(np.abs(got - want)) < 1e-12 * max(1.0, np.max(np.abs(C)))
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = omg.sequential(fine, g)
+    assert np.max(np.abs(got - seq)) < 1e-8 * np.max(np.abs(seq))
+    s.close()
