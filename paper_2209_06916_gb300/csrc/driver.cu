@@ -1650,10 +1650,57 @@ static int inner_cycle(mgrit_handle* h, bool zero_guess, bool want_norm = false)
 }
 
 
+// MIXED pre-relaxation sweep of the FP64 iterate in FP32: C-points rounded
+// to FP32, one C-relaxation (zero RHS on level 0), rows 1..K widened back
+// into the other FP64 buffer (row 0, the initial condition, stays exact).
+// Its rounding is an error like any other that the refinement removes.
+static int l0_cf_fp32(mgrit_handle* h) {
+  LevelData& L0 = h->lev[0];
+  const int64_t nx = h->nx, K = L0.K;
+  float* src = L0.uCf[L0.curf];
+  float* dst = L0.uCf[1 - L0.curf];
+  launch_convert(kCvtD2F, L0.uC[L0.cur], src, (K + 1) * nx, h->st);
+  ++h->launches;
+  if (h->sdirk) {
+    SdirkParams<float> sp = *h->sd0f;
+    sp.mode = kModeCF;
+    sp.zero_start = 0;
+    sp.start = src;
+    sp.out = dst;
+    sp.rhs = nullptr;
+    sp.sub = nullptr;
+    sp.partial = nullptr;
+    sp.nsteps = h->m;
+    sp.K = K;
+    sp.traj = nullptr;
+    ProfScope ps(h, kProfL0F32, sdirk_flops(sp, nx, K, h->m));
+    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  } else {
+    StencilParams<float> sp = *h->fineMf;
+    sp.in = src;
+    sp.out = dst + nx;
+    sp.rhs = nullptr;
+    sp.sub = nullptr;
+    sp.partial = nullptr;
+    sp.rows = K;
+    ProfScope ps(h, kProfL0F32, 2.0 * sp.ntaps * (double)nx * (double)K);
+    launch_stencil_rows(sp, h->st);
+  }
+  ++h->launches;
+  if (int rc = check_launch()) return rc;
+  launch_convert(kCvtF2D, L0.uC[1 - L0.cur] + nx, dst + nx, K * nx, h->st);
+  ++h->launches;
+  // the FP32 buffers hold the error iterate between refinement steps, whose
+  // t = 0 row is zero: no C-relaxation rewrites it, so clear it here
+  CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(float) * (size_t)nx, h->st));
+  L0.cur = 1 - L0.cur;
+  return check_launch();
+}
+
 static int level0_relax_residual_async_mixed(mgrit_handle* h) {
   int rc;
   for (int s = 0; s < h->prm.nu; ++s)
-    if ((rc = l0_cf(h))) return rc;
+    if ((rc = l0_cf_fp32(h))) return rc;
   return l0_fres(h);
 }
 
@@ -2244,7 +2291,12 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
     // residual of the corrected iterate (F-relaxation implied).
     LevelData& L0 = h->lev[0];
     const int inner = h->prm.inner_cycles;  // 0: adaptive
-    rc = level0_relax_residual(h, &nrm);
+    for (int s = 0; s < h->prm.nu; ++s)
+      if ((rc = l0_cf_fp32(h))) return rc;
+    if ((rc = l0_fres(h))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(cudaStreamSynchronize(h->st));
+    nrm = std::sqrt(std::max(0.0, *h->hnorm));
     if (rc) return rc;
     while (true) {
       if (st.history_len < MGRIT_MAX_HISTORY) st.rnorm_history[st.history_len++] = nrm;
