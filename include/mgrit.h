@@ -327,9 +327,10 @@ int mgrit_residual_noalloc(const mgrit_params* params, const double* d_uC, int64
 
 /* ---- batched and served solves ----------------------------------------- */
 /*
- * Many independent advection problems (the batched workload) run as
- * graph-resident solves launched together over a pool of streams, so their
- * kernels share the GPU and no solve waits on the host between iterations.
+ * Many independent advection problems of different sizes (the batched
+ * workload) run as graph-resident solves captured into one CUDA graph and
+ * launched together, so their kernels share the GPU and no solve waits on
+ * the host between iterations.
  * The paper solves one problem at a time; batching is an interface layer.
  */
 typedef struct mgrit_batch mgrit_batch;
@@ -337,11 +338,14 @@ typedef struct mgrit_batch mgrit_batch;
 /* Device bytes mgrit_setup allocates for *p (admission estimate), or -1. */
 int64_t mgrit_estimate_bytes(const mgrit_params* p);
 
-/* count solves with per-solve parameters params[0..count) (host), on
- * nstreams internal streams.  Allocates every hierarchy up front. */
+/* count solves with per-solve parameters params[0..count) (host); the
+ * hierarchies are set up on nstreams internal streams (and the sequential
+ * baseline runs over them).  Allocates every hierarchy up front. */
 int mgrit_batch_create(const mgrit_params* params, int64_t count, int nstreams, mgrit_batch** out);
 /* Solve all: u0s[i] (host or device, params[i].nx values).  stats (host, count
- * entries, may be NULL).  Returns OK, or the first NOT_CONVERGED / DIVERGED
+ * entries, may be NULL).  Every solve of the batch is one independent branch
+ * of a single CUDA graph (captured at the first call), so the whole batch is
+ * one graph launch.  Returns OK, or the first NOT_CONVERGED / DIVERGED
  * status among the solves (all solves still ran). */
 int mgrit_batch_solve(mgrit_batch* b, const double* const* u0s, mgrit_stats* stats);
 /* C-points of solve i ((nt/m + 1) * nx values, host or device). */

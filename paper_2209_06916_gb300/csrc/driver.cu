@@ -25,6 +25,7 @@
 
 #include "../../include/mgrit.h"
 #include "coeffs.h"
+#include "graph_batch.h"
 #include "kernels.h"
 
 using namespace mg;
@@ -1806,26 +1807,34 @@ static int mixed_outer_body(mgrit_handle* h, cudaStream_t cap2) {
   return l0_fres(h);
 }
 
-static int build_solve_graph(mgrit_handle* h) {
-  if (h->gexec) return MGRIT_OK;
+// Device state of a graph-resident solve (allocated once per handle).
+static int ensure_solve_state(mgrit_handle* h) {
+  if (h->dstate) return MGRIT_OK;
+  static_assert(sizeof(DevSolveState) <= kPinBlock, "device state exceeds a pinned block");
+  if (dev_alloc(h, (void**)&h->dstate, sizeof(DevSolveState)) || !(h->hstate = (DevSolveState*)pinned_get()))
+    return MGRIT_ERR_OOM;
+  if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+    note_cuda_error("cudaEventCreate", cudaGetLastError());
+    return MGRIT_ERR_CUDA;
+  }
+  return MGRIT_OK;
+}
+
+// Add one graph-resident solve of h to graph g as an independent branch:
+// prologue (first pre-relaxation and residual, captured from buffer 0) ->
+// stop-test init -> conditional while node whose body is one MGRIT
+// iteration followed by the check kernel.  g may be the handle's own graph
+// or a batch graph holding many solves.
+static int capture_solve(mgrit_handle* h, cudaGraph_t g) {
   const bool prof = h->prof.on;
   h->prof.on = false;  // no event records inside the graph
-  int rc = MGRIT_OK;
-  cudaGraph_t pro = nullptr;
-  // capture on a private stream (the legacy default stream cannot capture);
-  // the graph is later launched on the handle's stream
-  if (!h->dstate) {  // on the handle's stream, ordered before the sync below
-    static_assert(sizeof(DevSolveState) <= kPinBlock, "device state exceeds a pinned block");
-    if (dev_alloc(h, (void**)&h->dstate, sizeof(DevSolveState)) || !(h->hstate = (DevSolveState*)pinned_get())) {
-      h->prof.on = prof;
-      return MGRIT_ERR_OOM;
-    }
-    if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
-      h->prof.on = prof;
-      note_cuda_error("cudaEventCreate", cudaGetLastError());
-      return MGRIT_ERR_CUDA;
-    }
+  int rc = ensure_solve_state(h);
+  if (rc) {
+    h->prof.on = prof;
+    return rc;
   }
+  cudaGraph_t pro = nullptr;
+  // capture on private streams (the legacy default stream cannot capture)
   cudaStream_t user = h->st, cap = nullptr, cap2 = nullptr;
   if (cudaStreamSynchronize(user) != cudaSuccess ||
       cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1836,21 +1845,19 @@ static int build_solve_graph(mgrit_handle* h) {
   }
   h->st = cap;
   do {
-    if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) { note_cuda_error("cudaGraphCreate", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     cudaGraphConditionalHandle hnd;
-    if (cudaGraphConditionalHandleCreate(&hnd, h->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    if (cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
       note_cuda_error("cudaGraphConditionalHandleCreate", cudaGetLastError());
       rc = MGRIT_ERR_CUDA;
       break;
     }
-    // prologue: first (pre-relaxation and) residual, captured from buffer 0
     h->lev[0].cur = 0;
     if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) { note_cuda_error("cudaStreamBeginCapture", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     rc = h->mixed ? level0_relax_residual_async_mixed(h) : l0_relax_residual_async(h);
     if (cudaStreamEndCapture(h->st, &pro) != cudaSuccess && !rc) rc = MGRIT_ERR_CUDA;
     if (rc) break;
     cudaGraphNode_t npro, ninit, ncond;
-    if (cudaGraphAddChildGraphNode(&npro, h->graph, nullptr, 0, pro) != cudaSuccess) { note_cuda_error("cudaGraphAddChildGraphNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    if (cudaGraphAddChildGraphNode(&npro, g, nullptr, 0, pro) != cudaSuccess) { note_cuda_error("cudaGraphAddChildGraphNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     void* args[3] = {(void*)&h->dstate, (void*)&h->dnorm, (void*)&hnd};
     cudaKernelNodeParams kp = {};
     kp.func = solve_init_kernel_fn();
@@ -1858,13 +1865,13 @@ static int build_solve_graph(mgrit_handle* h) {
     kp.blockDim = dim3(1);
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
-    if (cudaGraphAddKernelNode(&ninit, h->graph, &npro, 1, &kp) != cudaSuccess) { note_cuda_error("cudaGraphAddKernelNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    if (cudaGraphAddKernelNode(&ninit, g, &npro, 1, &kp) != cudaSuccess) { note_cuda_error("cudaGraphAddKernelNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = hnd;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    if (cudaGraphAddNode(&ncond, h->graph, &ninit, nullptr, 1, &cp) != cudaSuccess) { note_cuda_error("cudaGraphAddNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
+    if (cudaGraphAddNode(&ncond, g, &ninit, nullptr, 1, &cp) != cudaSuccess) { note_cuda_error("cudaGraphAddNode", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
         cudaSuccess) {
@@ -1886,7 +1893,6 @@ static int build_solve_graph(mgrit_handle* h) {
     if (cudaStreamEndCapture(h->st, &body_out) != cudaSuccess && !rc) rc = MGRIT_ERR_CUDA;
     if (rc) break;
     h->graph_cur = h->lev[0].cur;
-    if (cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) { note_cuda_error("cudaGraphInstantiate", cudaGetLastError()); rc = MGRIT_ERR_CUDA; break; }
   } while (0);
   if (pro) cudaGraphDestroy(pro);
   h->st = user;
@@ -1896,7 +1902,23 @@ static int build_solve_graph(mgrit_handle* h) {
   if (rc) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) note_cuda_error("graph build", e);
-    if (h->graph) cudaGraphDestroy(h->graph);
+  }
+  return rc;
+}
+
+static int build_solve_graph(mgrit_handle* h) {
+  if (h->gexec) return MGRIT_OK;
+  if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) {
+    note_cuda_error("cudaGraphCreate", cudaGetLastError());
+    return MGRIT_ERR_CUDA;
+  }
+  int rc = capture_solve(h, h->graph);
+  if (!rc && cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) {
+    note_cuda_error("cudaGraphInstantiate", cudaGetLastError());
+    rc = MGRIT_ERR_CUDA;
+  }
+  if (rc) {
+    cudaGraphDestroy(h->graph);
     h->graph = nullptr;
     h->gexec = nullptr;
   }
@@ -2603,17 +2625,18 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
 }
 
 
-int mgrit_solve_async(mgrit_handle* h, const double* u0) {
-  if (!h || h->graph_pending) return MGRIT_ERR_INVALID_ARG;
-  int rc = build_solve_graph(h);
-  if (rc) return rc;
+// Everything a graph-resident solve needs before its graph runs, enqueued
+// on st: the initial iterate (u0 and the random C-points, or the one already
+// set) and the device stop-test state.
+static int solve_begin(mgrit_handle* h, const double* u0, cudaStream_t st) {
+  int rc;
   if (u0) {
     LevelData& L0 = h->lev[0];
     const size_t row = sizeof(double) * (size_t)h->nx;
-    if ((rc = copy_any(h->du0, u0, row, h->st))) return rc;
-    launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, h->st);
+    if ((rc = copy_any(h->du0, u0, row, st))) return rc;
+    launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, st);
     ++h->launches;
-    CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, st));
     L0.cur = 0;
     h->have_initial = true;
   } else if (!h->have_initial) {
@@ -2626,7 +2649,15 @@ int mgrit_solve_async(mgrit_handle* h, const double* u0) {
   init.in_base = h->inner_tol;
   init.in_max = kInnerMax;
   *h->hstate = init;
-  CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(DevSolveState), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(DevSolveState), cudaMemcpyHostToDevice, st));
+  return MGRIT_OK;
+}
+
+int mgrit_solve_async(mgrit_handle* h, const double* u0) {
+  if (!h || h->graph_pending) return MGRIT_ERR_INVALID_ARG;
+  int rc = build_solve_graph(h);
+  if (rc) return rc;
+  if ((rc = solve_begin(h, u0, h->st))) return rc;
   CUDA_TRY(cudaGraphLaunch(h->gexec, h->st));
   CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(DevSolveState), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaEventRecord(h->done, h->st));
@@ -2643,6 +2674,8 @@ int mgrit_solve_query(mgrit_handle* h) {
   return MGRIT_ERR_CUDA;
 }
 
+static void fill_solve_stats(const mgrit_handle* h, const DevSolveState& s, mgrit_stats* stats);
+
 int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats) {
   if (!h || !h->graph_pending) return MGRIT_ERR_INVALID_ARG;
   CUDA_TRY(cudaEventSynchronize(h->done));
@@ -2654,6 +2687,11 @@ int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats) {
     if ((rc = copy_any(u_out, L0.uC[L0.cur], sizeof(double) * (size_t)h->nx * (L0.K + 1), h->st))) return rc;
     CUDA_TRY(cudaStreamSynchronize(h->st));
   }
+  fill_solve_stats(h, s, stats);
+  return s.status;
+}
+
+static void fill_solve_stats(const mgrit_handle* h, const DevSolveState& s, mgrit_stats* stats) {
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->iterations = s.it;
@@ -2670,8 +2708,8 @@ int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats) {
       stats->inner_cycles = h->prm.inner_cycles > 0 ? s.it * h->prm.inner_cycles : s.in_total;
     }
   }
-  return s.status;
 }
+
 
 int64_t mgrit_launch_count(const mgrit_handle* h) { return h ? h->launches : 0; }
 
@@ -2709,3 +2747,43 @@ int mgrit_profile_read(mgrit_handle* h, double out[60]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One CUDA graph for a batch of solves (graph_batch.h)
+// ---------------------------------------------------------------------------
+int batch_graph_build(mgrit_handle* const* hs, int64_t n, cudaGraphExec_t* out) {
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+    note_cuda_error("cudaGraphCreate", cudaGetLastError());
+    return MGRIT_ERR_CUDA;
+  }
+  int rc = MGRIT_OK;
+  for (int64_t i = 0; i < n && !rc; ++i) rc = capture_solve(hs[i], g);
+  if (!rc && cudaGraphInstantiate(out, g, 0) != cudaSuccess) {
+    note_cuda_error("cudaGraphInstantiate", cudaGetLastError());
+    rc = MGRIT_ERR_CUDA;
+  }
+  cudaGraphDestroy(g);
+  return rc;
+}
+
+int batch_graph_run(mgrit_handle* const* hs, int64_t n, const double* const* u0s, cudaGraphExec_t ge,
+                    cudaStream_t st) {
+  int rc;
+  for (int64_t i = 0; i < n; ++i)
+    if ((rc = solve_begin(hs[i], u0s[i], st))) return rc;
+  CUDA_TRY(cudaGraphLaunch(ge, st));
+  for (int64_t i = 0; i < n; ++i) {
+    mgrit_handle* h = hs[i];
+    CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(DevSolveState), cudaMemcpyDeviceToHost, st));
+    h->lev[0].cur = h->graph_cur;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return MGRIT_OK;
+}
+
+int batch_graph_stats(const mgrit_handle* h, mgrit_stats* stats) {
+  fill_solve_stats(h, *h->hstate, stats);
+  return h->hstate->status;
+}

@@ -1,0 +1,19 @@
+// One CUDA graph for a batch of graph-resident solves (internal to the
+// library; driver.cu implements it, serve.cu uses it).  Each solve is an
+// independent branch of the graph: its prologue, stop-test init and
+// conditional while node, so one launch runs the whole batch and the graph
+// executor overlaps the branches.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mgrit.h"
+
+// Capture every solve of hs into one graph and instantiate it.
+int batch_graph_build(mgrit_handle* const* hs, int64_t n, cudaGraphExec_t* out);
+// Initial iterates (u0s[i]: host or device, nx_i values) and device states,
+// one launch of the batch graph, the states back; synchronises st.
+int batch_graph_run(mgrit_handle* const* hs, int64_t n, const double* const* u0s, cudaGraphExec_t ge,
+                    cudaStream_t st);
+// Statistics of solve h after batch_graph_run; returns its status.
+int batch_graph_stats(const mgrit_handle* h, mgrit_stats* stats);

@@ -1,11 +1,12 @@
 // Batched and served MGRIT solves (host-side scheduling in C++).
 //
-// Every solve is a graph-resident MGRIT solve (mgrit_solve_async: one CUDA
-// graph launch, iteration loop and stop test on the device).  A batch
-// launches all its solves at once over a pool of streams, so kernels of
-// different solves share the GPU; the server admits requests of a Poisson
-// stream as device memory (an HBM budget) and in-flight slots free up, and
-// records arrival-to-completion latency per request.
+// Every solve is a graph-resident MGRIT solve (iteration loop and stop test
+// on the device).  A batch captures all its solves into one CUDA graph, one
+// independent branch per solve, and runs them with one graph launch, so
+// kernels of different solves share the GPU; the server admits requests of
+// a Poisson stream as device memory (an HBM budget) and in-flight slots
+// free up (one graph launch per request, mgrit_solve_async), and records
+// arrival-to-completion latency per request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "../../include/mgrit.h"
+#include "graph_batch.h"
 
 namespace {
 
@@ -54,10 +56,12 @@ struct mgrit_batch {
   std::vector<mgrit_handle*> hs;
   std::vector<cudaStream_t> streams;
   std::vector<mgrit_params> prm;
+  cudaGraphExec_t ge = nullptr;  // every solve of the batch in one graph (built at the first solve)
 };
 
 extern "C" int mgrit_batch_destroy(mgrit_batch* b) {
   if (!b) return MGRIT_OK;
+  if (b->ge) cudaGraphExecDestroy(b->ge);
   for (auto h : b->hs) mgrit_destroy(h);
   for (auto s : b->streams) cudaStreamDestroy(s);
   delete b;
@@ -93,14 +97,12 @@ extern "C" int mgrit_batch_create(const mgrit_params* params, int64_t count, int
 extern "C" int mgrit_batch_solve(mgrit_batch* b, const double* const* u0s, mgrit_stats* stats) {
   if (!b || !u0s) return MGRIT_ERR_INVALID_ARG;
   const int64_t n = (int64_t)b->hs.size();
-  for (int64_t i = 0; i < n; ++i) {
-    int rc = mgrit_solve_async(b->hs[i], u0s[i]);
-    if (rc) return rc;
-  }
+  int rc;
+  if (!b->ge && (rc = batch_graph_build(b->hs.data(), n, &b->ge))) return rc;
+  if ((rc = batch_graph_run(b->hs.data(), n, u0s, b->ge, b->streams[0]))) return rc;
   int worst = MGRIT_OK;
   for (int64_t i = 0; i < n; ++i) {
-    int rc = mgrit_solve_wait(b->hs[i], nullptr, stats ? &stats[i] : nullptr);
-    if (rc == MGRIT_ERR_CUDA || rc == MGRIT_ERR_INVALID_ARG) return rc;
+    rc = batch_graph_stats(b->hs[i], stats ? &stats[i] : nullptr);
     if (rc && !worst) worst = rc;
   }
   return worst;
