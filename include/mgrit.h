@@ -207,6 +207,14 @@ int mgrit_solve_query(mgrit_handle* h);
 int mgrit_solve_wait(mgrit_handle* h, double* u_out, mgrit_stats* stats);
 
 /*
+ * mgrit_solve_wait_for -- mgrit_solve_wait bounded on the host: returns
+ * MGRIT_ERR_TIMEOUT if the solve has not finished after timeout_s seconds
+ * (it stays in flight; wait for it again later), else as mgrit_solve_wait.
+ * The paper has no counterpart.
+ */
+int mgrit_solve_wait_for(mgrit_handle* h, double timeout_s, double* u_out, mgrit_stats* stats);
+
+/*
  * mgrit_vcycle -- one MGRIT iteration without the stop test: coarse
  * correction from the current level-1 RHS (written by mgrit_residual(0)),
  * then the level-0 pre-relaxation F(CF)^nu and residual; *norm_out (host,

@@ -128,6 +128,7 @@ def load_library(path=LIB_PATH):
     lib.mgrit_solve_async.argtypes = [P, P]
     lib.mgrit_solve_query.argtypes = [P]
     lib.mgrit_solve_wait.argtypes = [P, P, ctypes.POINTER(Stats)]
+    lib.mgrit_solve_wait_for.argtypes = [P, ctypes.c_double, P, ctypes.POINTER(Stats)]
     lib.mgrit_profile.argtypes = [P, ctypes.c_int]
     lib.mgrit_profile_read.argtypes = [P, dp]
     _lib = lib
@@ -224,9 +225,16 @@ class Solver:
             raise MgritError(code, "mgrit_solve_query")
         return code == 0
 
-    def wait(self, u_out=None, allow_unconverged=False):
+    def wait(self, u_out=None, allow_unconverged=False, timeout=None):
+        """Wait for the graph-resident solve; with `timeout` (seconds) return
+        None if it is still running then (it stays in flight)."""
         st = Stats()
-        code = self.lib.mgrit_solve_wait(self.h, _ptr(u_out), ctypes.byref(st))
+        if timeout is None:
+            code = self.lib.mgrit_solve_wait(self.h, _ptr(u_out), ctypes.byref(st))
+        else:
+            code = self.lib.mgrit_solve_wait_for(self.h, float(timeout), _ptr(u_out), ctypes.byref(st))
+            if code == -5:
+                return None
         if code != MGRIT_OK and not (allow_unconverged and code in (-3, -4)):
             raise MgritError(code, "mgrit_solve_wait")
         d = st.to_dict()

@@ -21,6 +21,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mgrit.h"
@@ -2710,6 +2711,23 @@ static void fill_solve_stats(const mgrit_handle* h, const DevSolveState& s, mgri
   }
 }
 
+
+int mgrit_solve_wait_for(mgrit_handle* h, double timeout_s, double* u_out, mgrit_stats* stats) {
+  if (!h || !h->graph_pending || !(timeout_s >= 0.0)) return MGRIT_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    const cudaError_t e = cudaEventQuery(h->done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      note_cuda_error("cudaEventQuery", e);
+      return MGRIT_ERR_CUDA;
+    }
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >= timeout_s)
+      return MGRIT_ERR_TIMEOUT;  // still in flight: wait again later
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+  return mgrit_solve_wait(h, u_out, stats);
+}
 
 int64_t mgrit_launch_count(const mgrit_handle* h) { return h ? h->launches : 0; }
 

@@ -359,3 +359,21 @@ def test_output_all_time_points(kind, p, q, c, m, levels, nx, nt):
     seq = omg.sequential(fine, g)
     assert np.max(np.abs(got - seq)) < 1e-8 * np.max(np.abs(seq))
     s.close()
+
+
+def test_bounded_wait_times_out_then_completes():
+    """mgrit_solve_wait_for: a zero timeout right after launching a solve of
+    tens of milliseconds reports MGRIT_ERR_TIMEOUT and leaves the solve in
+    flight; a generous one then returns its result unchanged."""
+    nx, nt = 4096, 8192
+    s = solver(nx, nt, 0.85, 3, 8, 4, tol=1e-10, max_iter=30)
+    u0 = dev(ic_sin4_noise(nx, seed=0))
+    out = torch.empty((nt // 8 + 1, nx), dtype=torch.float64, device="cuda")
+    s.solve_async(u0)
+    assert s.wait(out, timeout=0.0) is None
+    st = s.wait(out, timeout=60.0)
+    assert st is not None and st["converged"]
+    ref = torch.empty_like(out)
+    st2 = s.solve(u0, ref)
+    assert st2["iterations"] == st["iterations"] and torch.equal(out, ref)
+    s.close()
