@@ -1,0 +1,102 @@
+"""Edge cases of the CUDA path against the oracle: the full-size C3
+configuration (sampled C-points against the Fourier closed form
+u_n = F^{-1}[lambda(omega)^n F u_0], whose symbol the oracle pins against the
+operator's application), the longest vectors the kernels take, and the
+degenerate hierarchies the method has (one CF-interval, a one-step coarsest
+level, F-relaxation, nu = 2)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2209_06916_gb300 as pkg
+from oracle import mgrit as omg
+from oracle import operators as oops
+from workloads import ic_fourier, ic_sin4, ic_sin4_noise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _closed_form(op, u0, ns):
+    """Rows u_n, n in ns, of sequential stepping by the Fourier symbol."""
+    nx = u0.shape[0]
+    lam = op.symbol(2 * np.pi * np.fft.fftfreq(nx))
+    f0 = np.fft.fft(u0)
+    return {n: np.real(np.fft.ifft(lam ** n * f0)) for n in ns}
+
+
+def _solve(prm, u0):
+    s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+    out = torch.empty((prm.nt // prm.m + 1, prm.nx), dtype=torch.float64, device="cuda")
+    st = s.solve(torch.tensor(u0, dtype=torch.float64, device="cuda"), out, allow_unconverged=True)
+    torch.cuda.synchronize()
+    s.close()
+    return out, st
+
+
+def test_full_size_c3_sampled_cpoints():
+    """16384 x 65536, U5 + SDIRK3 at c = 4, MIXED, m = 16, 5 levels (the
+    bench configuration): sampled C-points within 1e-8 of exact stepping."""
+    nx, nt, m = 16384, 65536, 16
+    u0 = ic_fourier(nx, seed=0)
+    prm = pkg.make_params(nx, nt, 4.0, 5, kind=pkg.SDIRK, q=3, m=m, levels=5, tol=1e-10, max_iter=30,
+                          precision=pkg.MIXED, seed=0)
+    out, st = _solve(prm, u0)
+    assert st["converged"]
+    ks = (1, 7, 1000, 2048, 4095, 4096)
+    want = _closed_form(oops.FineOperator(5, "sdirk", 3, 4.0), u0, [k * m for k in ks])
+    scale = np.max(np.abs(u0))
+    rows = out[list(ks)].cpu().numpy()
+    for i, k in enumerate(ks):
+        assert np.max(np.abs(rows[i] - want[k * m])) < 1e-8 * scale, k
+
+
+@pytest.mark.parametrize("kind,p,q,c,nx,m,levels", [
+    (pkg.ERK, 3, 3, 0.85, 131072, 4, 3),     # the longest vector the kernels take (16 CTAs x 256 x 32)
+    (pkg.SDIRK, 5, 5, 6.0, 65536, 4, 3),     # the longest SDIRK5 vector of the serving mix
+])
+def test_longest_vectors(kind, p, q, c, nx, m, levels):
+    nt = m ** (levels - 1) * 2
+    u0 = ic_fourier(nx, seed=3)
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, tol=1e-11, max_iter=30, seed=1)
+    out, st = _solve(prm, u0)
+    assert st["converged"]
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    ks = list(range(nt // m + 1))
+    want = _closed_form(oops.FineOperator(p, kname, q, c), u0, [k * m for k in ks])
+    got = out.cpu().numpy()
+    scale = np.max(np.abs(u0))
+    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("kind,p,q,c,nx,nt,m,levels,nu", [
+    (pkg.ERK, 3, 3, 0.85, 96, 4, 4, 2, 1),       # one CF-interval, a one-step coarsest level
+    (pkg.ERK, 1, 1, 0.85, 64, 8, 4, 2, 0),       # two intervals, F-relaxation
+    (pkg.ERK, 3, 3, 0.85, 128, 16, 4, 3, 1),     # coarsest level of one step
+    (pkg.ERK, 5, 5, 0.9, 128, 32, 2, 5, 2),      # m = 2, five levels, nu = 2
+    (pkg.SDIRK, 3, 3, 5.0, 64, 16, 16, 2, 1),    # one interval of sixteen SDIRK steps
+    (pkg.SDIRK, 1, 1, 1.0, 64, 64, 4, 4, 0),     # one-step coarsest level, F-relaxation
+])
+def test_degenerate_hierarchies(kind, p, q, c, nx, nt, m, levels, nu):
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    u0 = ic_sin4_noise(nx, seed=2)
+    for prec in (pkg.FP64, pkg.MIXED):
+        prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, nu=nu, tol=1e-10,
+                              max_iter=40, seed=4, precision=prec)
+        out, st = _solve(prm, u0)
+        g = np.zeros((nt + 1, nx))
+        g[0] = u0
+        seq = omg.sequential(oops.FineOperator(p, kname, q, c), g)[::m]
+        assert st["converged"], (prec, st["iterations"])
+        assert np.max(np.abs(out.cpu().numpy() - seq)) < 1e-9 * np.max(np.abs(seq)), prec
+        if prec == pkg.FP64:
+            ref = omg.solve(omg.Hierarchy(p, kname, q, c, m, levels), u0, nt, nu=nu, tol=1e-10, max_iter=40,
+                            seed=4)
+            assert st["iterations"] == ref["iterations"]
