@@ -17,6 +17,8 @@ Modules
                 S_p (Sec. 3), Psi = (I - phi D)^{-1} S_p (Eq. MOL-SL-corrected).
   mgrit         sequential time-stepping (Eq. one-step-general), two-level and
                 V-cycle linear MGRIT (Sec. 2.2) with F / FCF relaxation.
+  gmres         GMRES from a zero guess with the Sec. 6.3 stop rule, for the
+                approximate correction solves of the coarse operators.
   lfa           two-level LFA convergence factor (Eq. rho-asym).
   rng           SplitMix64 counter-based uniform generator for the random
                 initial MGRIT iterate (Sec. 5.3 numerical setup).

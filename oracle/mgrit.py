@@ -70,9 +70,10 @@ class Hierarchy:
     or with ``coarse_op`` = "sl" / "redisc" the direct SL operator or the
     rediscretised fine method (operators.direct_operator).  ``coarse`` may
     replace the level-1 operator (e.g. the ideal Phi^m) for a two-level
-    hierarchy."""
+    hierarchy.  ``gmres`` = (rtol, maxit) solves the correction systems of
+    the corrected operators approximately by GMRES (Sec. 6.3)."""
 
-    def __init__(self, p, kind, q, c, m, levels, coarse=None, coarse_op="sl_corrected"):
+    def __init__(self, p, kind, q, c, m, levels, coarse=None, coarse_op="sl_corrected", gmres=None):
         self.m, self.levels = m, levels
         self.fine = ops.FineOperator(p, kind, q, c)
         self.ops = [self.fine]
@@ -80,7 +81,7 @@ class Hierarchy:
             if l == 1 and coarse is not None:
                 self.ops.append(coarse)
             elif coarse_op == "sl_corrected":
-                self.ops.append(ops.coarse_operator(p, kind, q, c, m, l, levels))
+                self.ops.append(ops.coarse_operator(p, kind, q, c, m, l, levels, gmres))
             else:
                 self.ops.append(ops.direct_operator(p, kind, q, c, m, l, coarse_op))
 

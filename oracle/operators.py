@@ -18,7 +18,8 @@ FineOperator.apply       Eq. (MOL_M_def): one RK step of du/dt =         Fourier
 SLOperator.apply         Sec. 3: S_p^{(Delta)} interpolation at the       exact shift for integer offset;
                          departure point                                 Lemma 3.1 order
 CoarseOperator.apply     Eq. (MOL-SL-corrected[-multilevel])                Lemma 6.1 O(h^{p+2}) match with
-                         (I - phi D)^{-1} S_p^{(m^l dt)}                  Phi^m; LFA values (Sec. 6.3.4, 6.4)
+                         (I - phi D)^{-1} S_p^{(m^l dt)}; the correction  Phi^m; LFA values (Sec. 6.3.4, 6.4);
+                         solve exact or by GMRES (Sec. 6.1, 6.3)           GMRES pins in oracle/gmres.py
 direct_operator          Sec. 1 footnote, Sec. 2.2, Sec. 5: direct        symbols == application; LFA with
                          coarse operators -- S_p^{(m^l dt)} ("sl") and    rediscretisation >= the bound of
                          the rediscretised R_q(-m^l c L_p) ("redisc")     Theorem thm:MOL-rho-lwr-bnd
@@ -27,6 +28,7 @@ import numpy as np
 import scipy.linalg
 
 from . import coefficients as co
+from . import gmres as _gm
 
 
 def apply_stencil(u, taps):
@@ -184,10 +186,13 @@ class CoarseOperator:
 
     With one term (phi, p+1) this is Eq. (MOL-SL-corrected) / (MOL-SL-corrected-multilevel); the
     two-term form is the q != p reading (see coefficients.phi_levels_general).
-    ``terms`` is a list of (phi, derivative order).
+    ``terms`` is a list of (phi, derivative order).  ``gmres`` = (rtol, maxit)
+    replaces the exact correction solve by GMRES from a zero guess, one
+    system per row (Sec. 6.1, Sec. 6.3; oracle/gmres.py); the iteration count
+    of every solve is appended to ``gmres_its``.
     """
 
-    def __init__(self, p, s, terms):
+    def __init__(self, p, s, terms, gmres=None):
         self.p = p
         self.sl = SLOperator(p, s)
         self.terms = list(terms)
@@ -196,24 +201,37 @@ class CoarseOperator:
             for j, d in co.diff_taps(order).items():
                 corr[j] = corr.get(j, 0.0) - phi * float(d)
         self.corr = corr  # taps of -(sum phi D), the matrix is I + corr
+        self.gmres = gmres
+        self.gmres_its = []
+
+    def correction_matvec(self, v):
+        """(I - sum phi D) v."""
+        return v + apply_stencil(v, self.corr)
 
     def apply(self, u):
-        return circulant_solve(self.corr, self.sl.apply(u), diag=1.0)
+        b = self.sl.apply(u)
+        if self.gmres is None:
+            return circulant_solve(self.corr, b, diag=1.0)
+        rtol, maxit = self.gmres
+        X, its = _gm.gmres_rows(self.correction_matvec, b.reshape(-1, b.shape[-1]), rtol, maxit)
+        self.gmres_its.extend(its)
+        return X.reshape(b.shape)
 
     def symbol(self, omega):
         den = 1.0 + sum(a * np.exp(1j * j * omega) for j, a in self.corr.items())
         return self.sl.symbol(omega) / den
 
 
-def coarse_operator(p, kind, q, c, m, level, levels):
+def coarse_operator(p, kind, q, c, m, level, levels, gmres=None):
     """Level-``level`` (>= 1) corrected SL operator of a ``levels``-level
-    hierarchy with uniform coarsening m (Eq. MOL-SL-corrected-multilevel and the Sec. 6.2 phi recursion)."""
+    hierarchy with uniform coarsening m (Eq. MOL-SL-corrected-multilevel and the Sec. 6.2 phi recursion);
+    ``gmres`` = (rtol, maxit) solves its correction systems by GMRES."""
     s = c * m ** level
     if q == p:
         phi = co.phi_levels(p, kind, c, m, levels)[level - 1]
-        return CoarseOperator(p, s, [(phi, p + 1)])
+        return CoarseOperator(p, s, [(phi, p + 1)], gmres)
     fp, fq = co.phi_levels_general(p, kind, q, c, m, levels)[level - 1]
-    return CoarseOperator(p, s, [(fp, p + 1), (fq, q + 1)])
+    return CoarseOperator(p, s, [(fp, p + 1), (fq, q + 1)], gmres)
 
 
 def direct_operator(p, kind, q, c, m, level, coarse_op):
