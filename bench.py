@@ -478,9 +478,17 @@ def main():
     else:
         kname = "sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves + L_p mat-vecs), clusters of %d" % (
             int(info0[6]), w["p"] + 1, int(info0[7]))
-    # DRAM bytes per launch of the level-0 kernel from one ncu capture of
-    # this workload (profiles/stencil_rows_kernel_advection1d_erk3u3_fp64.md)
-    traffic = 94.4e6 if (w["name"] == WORKLOADS["c2"]["name"] and prec == pkg.FP64) else None
+    # DRAM bytes per launch of the level-0 kernel from one ncu capture:
+    # the composite stencil of the 4096 x 16384 ERK3 workload
+    # (profiles/stencil_rows_kernel_advection1d_erk3u3_fp64.md), and the
+    # FP64 SDIRK kernel of the 16384 x 65536 workload, captured at nt = 8192
+    # and scaled by the 8x intervals of a full launch
+    # (profiles/sdirk_kernel_advection1d_sdirk3u5_mixed_nt8192.md)
+    traffic = None
+    if w["name"] == WORKLOADS["c2"]["name"] and prec == pkg.FP64 and nt == WORKLOADS["c2"]["nt"]:
+        traffic = 94.1e6
+    elif w["name"] == WORKLOADS["c3"]["name"] and nt == WORKLOADS["c3"]["nt"]:
+        traffic = 805e6
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
