@@ -66,6 +66,8 @@ extern "C" {
 #define MGRIT_COARSE_SL_CORRECTED 0
 #define MGRIT_COARSE_SL 1
 #define MGRIT_COARSE_REDISC 2
+#define MGRIT_SOLVE_DIRECT 0 /* exact periodic banded correction solve        */
+#define MGRIT_SOLVE_GMRES 1  /* GMRES correction solve (Sec. 6.1, Sec. 6.3)   */
 #define MGRIT_MAX_HISTORY 128
 
 /* ---- parameters -------------------------------------------------------- */
@@ -95,6 +97,13 @@ typedef struct mgrit_params {
                     /* paper's Eq. MOL-SL-corrected-multilevel), MGRIT_COARSE_SL */
                     /* (direct S_p, Sec. 3), MGRIT_COARSE_REDISC (SDIRK only:   */
                     /* the fine method with step m^l dt, Sec. 5)                */
+  int coarse_solve; /* correction solve (I - phi D) x = S v of the corrected    */
+                    /* operator on every coarse level: MGRIT_SOLVE_DIRECT (0)   */
+                    /* or MGRIT_SOLVE_GMRES: GMRES from a zero guess, stopped   */
+                    /* once ||b - A x_k|| <= gmres_rtol ||b|| or at gmres_maxit */
+                    /* (Sec. 6.1, Sec. 6.3); SL_CORRECTED only, n_x <= 32768    */
+  int gmres_maxit;  /* 1..32; 0: 10 for p = 1, 20 otherwise (Sec. 6.3)         */
+  double gmres_rtol;/* in (0, 1); 0: 1e-2 (Sec. 6.3)                           */
 } mgrit_params;
 
 /* ---- statistics -------------------------------------------------------- */
@@ -280,6 +289,14 @@ int mgrit_output_all(mgrit_handle* h, double* d_all);
  * (or R + 16: the persistent form) the level-0 stencil tile.
  */
 int mgrit_level_info(const mgrit_handle* h, int level, double out[8]);
+
+/*
+ * mgrit_gmres_stats -- GMRES work on coarse level `level` (>= 1) since setup:
+ * out[0] = iterations summed over all correction solves, out[1] = solves
+ * (zeros when the level solves directly).  Waits for the handle's stream.
+ * Errors: INVALID_ARG (level out of range, out NULL), CUDA.
+ */
+int mgrit_gmres_stats(mgrit_handle* h, int level, int64_t out[2]);
 
 /* Number of CUDA kernels this handle launched since setup (kernel-launch
  * counter maintained by the library). */

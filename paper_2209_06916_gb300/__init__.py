@@ -24,6 +24,7 @@ ERRORS = {
 ERK, SDIRK = 0, 1
 FP64, MIXED, MIXED_FAST = 0, 1, 2
 SL_CORRECTED, SL, REDISC = 0, 1, 2  # coarse-grid operators
+DIRECT, GMRES = 0, 1  # correction solves of the corrected coarse operator
 MAX_HISTORY = 128
 
 
@@ -34,7 +35,8 @@ class Params(ctypes.Structure):
         ("rk_order_q", ctypes.c_int), ("m", ctypes.c_int), ("levels", ctypes.c_int),
         ("nu", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
         ("precision", ctypes.c_int), ("seed", ctypes.c_uint64), ("inner_cycles", ctypes.c_int),
-        ("coarse_op", ctypes.c_int),
+        ("coarse_op", ctypes.c_int), ("coarse_solve", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+        ("gmres_rtol", ctypes.c_double),
     ]
 
 
@@ -111,6 +113,7 @@ def load_library(path=LIB_PATH):
     lib.mgrit_output_all.argtypes = [P, P]
     lib.mgrit_batch_sequential.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]
     lib.mgrit_level_info.argtypes = [P, ctypes.c_int, dp]
+    lib.mgrit_gmres_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
     lib.mgrit_launch_count.argtypes = [P]
     lib.mgrit_launch_count.restype = ctypes.c_int64
     lib.mgrit_estimate_bytes.argtypes = [ctypes.POINTER(Params)]
@@ -158,10 +161,12 @@ def _check(code, what):
 
 
 def make_params(nx, nt, cfl, p, kind=ERK, q=0, m=4, levels=2, nu=1, tol=1e-10, max_iter=30,
-                precision=FP64, seed=0, alpha=1.0, inner_cycles=0, coarse_op=SL_CORRECTED):
+                precision=FP64, seed=0, alpha=1.0, inner_cycles=0, coarse_op=SL_CORRECTED,
+                coarse_solve=DIRECT, gmres_maxit=0, gmres_rtol=0.0):
     return Params(nx=nx, nt=nt, cfl=cfl, alpha=alpha, order_p=p, rk_kind=kind, rk_order_q=q, m=m,
                   levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed,
-                  inner_cycles=inner_cycles, coarse_op=coarse_op)
+                  inner_cycles=inner_cycles, coarse_op=coarse_op, coarse_solve=coarse_solve,
+                  gmres_maxit=gmres_maxit, gmres_rtol=gmres_rtol)
 
 
 class Solver:
@@ -265,6 +270,13 @@ class Solver:
         out = (ctypes.c_double * 8)()
         _check(self.lib.mgrit_level_info(self.h, level, out), "mgrit_level_info")
         return list(out)
+
+    def gmres_stats(self, level):
+        """(GMRES iterations, correction solves) on coarse level ``level``
+        since setup."""
+        out = (ctypes.c_int64 * 2)()
+        _check(self.lib.mgrit_gmres_stats(self.h, level, out), "mgrit_gmres_stats")
+        return int(out[0]), int(out[1])
 
     def fine_propagate(self, u0, u_out, nsteps, every=0, traj=None):
         _check(self.lib.mgrit_fine_propagate(self.h, _ptr(u0), _ptr(u_out), nsteps, every, _ptr(traj)),

@@ -5,6 +5,8 @@
 // C-relaxation after F (CF), F-relaxation + C-point residual (FRES), F
 // post-relaxation added into the parent level (FOUT, the coarse-grid
 // correction), sequential coarsest solve (SEQ) and plain apply (APPLY).
+// GM = true replaces the exact banded correction solve by GMRES (Sec. 6.1,
+// Sec. 6.3; gmres.cuh).
 #include <cooperative_groups.h>
 #include <cuda_pipeline.h>
 #include <cuda_runtime.h>
@@ -13,6 +15,7 @@
 #include <algorithm>
 
 #include "dsolve.cuh"
+#include "gmres.cuh"
 #include "kernels.h"
 
 namespace mg {
@@ -51,7 +54,7 @@ __device__ __forceinline__ void sl_gather(TC (&x)[P], const T* b0, const T* b1, 
   }
 }
 
-template <typename T, typename TC, int P, int P1>
+template <typename T, typename TC, int P, int P1, bool GM>
 __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ CoarseParams<T, TC> A) {
   constexpr int H = P1 / 2;
   constexpr int LP = Log2c<P>::v;
@@ -73,6 +76,11 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   TC* aggc = sqa + 48;
   TC* agga = aggc + 4;
   double* red = reinterpret_cast<double*>(smem_raw + slot_bytes + ((104 * sizeof(TC) + 15) & ~(size_t)15));
+  // GMRES: the Krylov vector's halo buffer and the reduction / Hessenberg area
+  const size_t gm_off = slot_bytes + ((104 * 8 + 15) & ~(size_t)15) + 32 * sizeof(double);
+  TC* const gmv = reinterpret_cast<TC*>(smem_raw + gm_off);
+  double* const gms =
+      reinterpret_cast<double*>(smem_raw + gm_off + (((size_t)npad * sizeof(TC) + 15) & ~(size_t)15));
   const int64_t k = blockIdx.x / C;
   const int64_t nn = n;
   const int64_t off = (int64_t)rank * npc;  // first global point of this CTA
@@ -131,7 +139,11 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
       } else {
         sl_gather<T, TC, P, P1, LP>(x, cur ? w01 : w00, cur ? w11 : w10, l0, npc, A.w);
       }
-      if (!A.nosolve) banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
+      if constexpr (GM) {
+        gmres_solve<TC, P, H>(x, A, gmv, gms, t, rank, C, k);
+      } else {
+        if (!A.nosolve) banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
+      }
     }
     if (A.g) __pipeline_wait_prior(0);  // this thread's chunk of the RHS row has landed
     T* nxt = (cur ? sv0 : sv1) + base;
@@ -178,21 +190,22 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
   if (C > 1) cl.sync();
 }
 
-template <typename T, typename TC, int P, int P1>
+template <typename T, typename TC, int P, int P1, bool GM>
 static void configure_coarse() {
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1, GM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     configured = true;
   }
 }
 
-template <typename T, typename TC, int P, int P1>
+template <typename T, typename TC, int P, int P1, bool GM>
 static int launch_coarse_t(const CoarseParams<T, TC>& A, cudaStream_t st) {
-  configure_coarse<T, TC, P, P1>();
+  configure_coarse<T, TC, P, P1, GM>();
   if (A.K <= 0) return 0;
-  size_t smem = coarse_smem_bytes(A.npc, A.P, A.nthr, (int)sizeof(T));
+  size_t smem = coarse_smem_bytes(A.npc, A.P, A.nthr, (int)sizeof(T), GM ? (int)sizeof(TC) : 0);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.K * A.csize));
   cfg.blockDim = dim3((unsigned)A.nthr);
@@ -205,20 +218,31 @@ static int launch_coarse_t(const CoarseParams<T, TC>& A, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, coarse_kernel<T, TC, P, P1>, A) == cudaSuccess ? 1 : -1;
+  return cudaLaunchKernelEx(&cfg, coarse_kernel<T, TC, P, P1, GM>, A) == cudaSuccess ? 1 : -1;
 }
 
 template <typename T, typename TC, int P1>
 static int launch_coarse_p(const CoarseParams<T, TC>& A, cudaStream_t st) {
+  if (A.gm_max > 0) {  // GMRES correction solves: chunks of 4 or 8 points
+    if (A.gm_max > kGmMax || !A.gm_V) return -1;
+    switch (A.P) {
+      case 4:
+        return launch_coarse_t<T, TC, 4, P1, true>(A, st);
+      case 8:
+        return launch_coarse_t<T, TC, 8, P1, true>(A, st);
+      default:
+        return -1;
+    }
+  }
   switch (A.P) {
     case 4:
-      return launch_coarse_t<T, TC, 4, P1>(A, st);
+      return launch_coarse_t<T, TC, 4, P1, false>(A, st);
     case 8:
-      return launch_coarse_t<T, TC, 8, P1>(A, st);
+      return launch_coarse_t<T, TC, 8, P1, false>(A, st);
     case 16:
-      return launch_coarse_t<T, TC, 16, P1>(A, st);
+      return launch_coarse_t<T, TC, 16, P1, false>(A, st);
     case 32:
-      return launch_coarse_t<T, TC, 32, P1>(A, st);
+      return launch_coarse_t<T, TC, 32, P1, false>(A, st);
     default:
       return -1;
   }

@@ -69,6 +69,14 @@ struct LevelData {
   float* rdf_Mt[2] = {nullptr, nullptr};
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
+  // GMRES correction solves: unscaled SL weights, the taps of I - sum phi D
+  // (offsets -3..3), the Krylov basis scratch for gm_cap intervals (sized
+  // for doubles) and the device counters [iterations, solves]
+  double slw_raw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double gm_taps[7] = {0, 0, 0, 0, 0, 0, 0};
+  double* gm_V = nullptr;
+  int64_t gm_cap = 0;
+  unsigned long long* gm_stats = nullptr;
 };
 
 }  // namespace
@@ -428,6 +436,12 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   cp.shift = 0;
   cp.nosolve = Lv.nosolve ? 1 : 0;
   for (int a = 0; a <= p; ++a) cp.w[a] = Lv.slw[a];
+  if (P.coarse_solve == MGRIT_SOLVE_GMRES) {  // GMRES solves the unscaled system
+    cp.gm_max = P.gmres_maxit;
+    cp.gm_rtol = P.gmres_rtol;
+    for (int a = 0; a <= p; ++a) cp.w[a] = Lv.slw_raw[a];
+    for (int i = 0; i < 7; ++i) cp.gm_taps[i] = Lv.gm_taps[i];
+  }
   for (int d = 0; d < 2; ++d) {
     dev_free(h, Lv.Mt_dev[d]);
     Lv.Mt_dev[d] = nullptr;
@@ -459,6 +473,9 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
       q.m = cp.m;
       q.nosolve = cp.nosolve;
       for (int a = 0; a <= p; ++a) q.w[a] = (float)cp.w[a];
+      q.gm_max = cp.gm_max;
+      q.gm_rtol = cp.gm_rtol;
+      for (int i = 0; i < 7; ++i) q.gm_taps[i] = cp.gm_taps[i];
     };
     geom(Lv.cpfd);
     Lv.cpfd.c = cp.c;
@@ -480,19 +497,22 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
 // SL window (P + p + 1 points) must lie within two neighbouring CTAs.
 static std::vector<GeomC> coarse_geometries(mgrit_handle* h, int max_out) {
   const int elem = is_mixed(h->prm.precision) ? 4 : 8;
+  const bool gm = h->prm.coarse_solve == MGRIT_SOLVE_GMRES;  // GMRES kernels: P = 4 or 8
   std::vector<std::pair<double, GeomC>> all;
   for (int C = 1; C <= 16; C *= 2) {
     if (h->nx % C) continue;
     const int64_t npc = h->nx / C;
     for (int P : kChunkLens) {
+      if (gm && P > 8) continue;
       if (npc % P || npc < P + h->prm.order_p + 2) continue;
       const int64_t nthr = npc / P;
       if (nthr < 1 || nthr > 256) continue;
-      const size_t sm = coarse_smem_bytes((int)npc, P, (int)nthr, 8);
+      const size_t sm = coarse_smem_bytes((int)npc, P, (int)nthr, 8, gm ? 8 : 0);
       if (sm > 227 * 1024) continue;
       if (C > 1 && coarse_max_cluster(C, sm, (int)nthr) < C) continue;
       const int warps = ((int)nthr + 31) / 32;
-      const int regs = elem == 8 ? (P <= 8 ? 80 : P <= 16 ? 112 : 192) : (P <= 8 ? 64 : P <= 16 ? 96 : 160);
+      int regs = elem == 8 ? (P <= 8 ? 80 : P <= 16 ? 112 : 192) : (P <= 8 ? 64 : P <= 16 ? 96 : 160);
+      if (gm) regs = 128;
       int cps = std::min<int>((int)(228 * 1024 / (sm + 1024)), 64 / warps);
       cps = std::min(cps, 65536 / (regs * warps * 32));
       cps = std::min(cps, 32);
@@ -561,7 +581,11 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   }
   Lv.bf = bf;
   std::vector<double> w = sl_weights(p, eps);
-  for (int a = 0; a <= p; ++a) Lv.slw[a] = w[a] * bf.inv_kappa;
+  for (int a = 0; a <= p; ++a) {
+    Lv.slw[a] = w[a] * bf.inv_kappa;
+    Lv.slw_raw[a] = w[a];
+  }
+  for (int t = -3; t <= 3; ++t) Lv.gm_taps[3 + t] = A.at(t);
   Lv.kappa = band_condition(A);
   // MIXED: FP32 storage and SL gather; the correction solve in FP64 where an
   // FP32 solve would lose more than about four of its seven digits
@@ -1085,6 +1109,9 @@ static int tune_coarse(mgrit_handle* h, int l) {
     std::string why;
     return build_redisc(h, l, true, &why);
   }
+  // GMRES levels keep the best-scored geometry: timing depends on the data
+  // through the iteration counts
+  if (h->prm.coarse_solve == MGRIT_SOLVE_GMRES) return MGRIT_OK;
   const bool coarsest = (l == h->L - 1);
   const bool f32 = h->mixed && !coarsest;
   std::vector<GeomC> cand = coarse_geometries(h, 10);
@@ -1380,11 +1407,30 @@ static int coarse_launch(mgrit_handle* h, int l, int mode, int zero_start, const
   cp.K = K;
   cp.g = g;
   cp.partial = (mode == kModeFRES) ? h->partials : nullptr;
+  cp.gm_V = h->lev[l].gm_V;
+  cp.gm_stats = h->lev[l].gm_stats;
   const int H = cp.p1 / 2;
   double steps = (double)K * (double)(nsteps - (zero_start ? 1 : 0));
   const double fl = 2.0 * (double)h->nx * steps * (double)(cp.p1 + 2 * H);
   ProfScope ps(h, 1, fl);
   ProfScope psl(h, 4 + std::min(l, kProfCats - 6), fl);
+  const int64_t cap = h->lev[l].gm_cap;
+  if (cp.gm_max > 0 && K > cap) {
+    // the GMRES scratch holds gm_cap intervals: plain applies to more
+    // vectors run in pieces
+    if (mode != kModeAPPLY || cap < 1) return MGRIT_ERR_UNSUPPORTED;
+    for (int64_t k0 = 0; k0 < K; k0 += cap) {
+      CoarseParams<double> c2 = cp;
+      c2.K = std::min<int64_t>(cap, K - k0);
+      c2.start = start + k0 * h->nx;
+      c2.out = out + k0 * h->nx;
+      if (launch_coarse(c2, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+      ++h->launches;
+      int rc = check_launch();
+      if (rc) return rc;
+    }
+    return MGRIT_OK;
+  }
   if (launch_coarse(cp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
   ++h->launches;
   return check_launch();
@@ -1573,14 +1619,19 @@ static int coarse_launch_f(mgrit_handle* h, int l, int mode, int zero_start, con
   const double fl = 2.0 * (double)h->nx * steps * (double)(Lv.cp.p1 + 2 * H);
   ProfScope ps(h, 1, fl);
   ProfScope psl(h, 4 + std::min(l, kProfCats - 6), fl);
+  if (Lv.gm_V && K > Lv.gm_cap) return MGRIT_ERR_UNSUPPORTED;
   int r;
   if (Lv.solve64) {
     CoarseParams<float, double> cp = Lv.cpfd;
     fill(cp);
+    cp.gm_V = Lv.gm_V;
+    cp.gm_stats = Lv.gm_stats;
     r = launch_coarse(cp, h->st);
   } else {
     CoarseParams<float, float> cp = Lv.cpf;
     fill(cp);
+    cp.gm_V = reinterpret_cast<float*>(Lv.gm_V);
+    cp.gm_stats = Lv.gm_stats;
     r = launch_coarse(cp, h->st);
   }
   if (r < 0) return MGRIT_ERR_UNSUPPORTED;
@@ -2012,6 +2063,8 @@ int mgrit_destroy(mgrit_handle* h) {
     dev_free(h, Lv.gf);
     dev_free(h, Lv.Mtf_dev[0]);
     dev_free(h, Lv.Mtf_dev[1]);
+    dev_free(h, Lv.gm_V);
+    dev_free(h, Lv.gm_stats);
   }
   dev_free(h, h->partials);
   dev_free(h, h->dnorm);
@@ -2038,6 +2091,15 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
   if (P.precision != MGRIT_FP64 && !is_mixed(P.precision)) return MGRIT_ERR_INVALID_ARG;
   if (P.coarse_op < MGRIT_COARSE_SL_CORRECTED || P.coarse_op > MGRIT_COARSE_REDISC) return MGRIT_ERR_INVALID_ARG;
+  if (P.coarse_solve != MGRIT_SOLVE_DIRECT && P.coarse_solve != MGRIT_SOLVE_GMRES) return MGRIT_ERR_INVALID_ARG;
+  if (P.coarse_solve == MGRIT_SOLVE_GMRES) {
+    // only the corrected operator has a correction system to solve
+    if (P.coarse_op != MGRIT_COARSE_SL_CORRECTED) return MGRIT_ERR_INVALID_ARG;
+    if (P.gmres_maxit == 0) P.gmres_maxit = P.order_p == 1 ? 10 : 20;  // Sec. 6.3
+    if (P.gmres_rtol == 0.0) P.gmres_rtol = 1e-2;
+    if (P.gmres_maxit < 1 || P.gmres_maxit > kGmMax || !(P.gmres_rtol > 0.0 && P.gmres_rtol < 1.0))
+      return MGRIT_ERR_INVALID_ARG;
+  }
   // rediscretising an explicit method at m^l dt is unstable for practical
   // m c (Sec. 5): offered for SDIRK only
   if (P.coarse_op == MGRIT_COARSE_REDISC && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_UNSUPPORTED;
@@ -2142,6 +2204,12 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     if (l >= 1) {
       if ((rc = alloc(&Lv.g, row * (Lv.N + 1)))) return rc;
       CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
+    }
+    if (l >= 1 && P.coarse_solve == MGRIT_SOLVE_GMRES) {
+      Lv.gm_cap = std::max<int64_t>(Lv.K, 1);
+      if ((rc = alloc(&Lv.gm_V, row * (size_t)Lv.gm_cap * (size_t)(P.gmres_maxit + 1)))) return rc;
+      if ((rc = dev_alloc(h.get(), (void**)&Lv.gm_stats, 2 * sizeof(unsigned long long)))) return rc;
+      CUDA_TRY(cudaMemsetAsync(Lv.gm_stats, 0, 2 * sizeof(unsigned long long), h->st));
     }
   }
   if (is_mixed(P.precision)) {
@@ -2622,6 +2690,19 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   out[4] = Lv.phi_q;
   out[6] = (double)(Lv.redisc ? Lv.rd->P : Lv.cp.P);
   out[7] = (double)(Lv.redisc ? Lv.rd->csize : Lv.cp.csize);
+  return MGRIT_OK;
+}
+
+int mgrit_gmres_stats(mgrit_handle* h, int level, int64_t out[2]) {
+  if (!h || level < 1 || level >= h->L || !out) return MGRIT_ERR_INVALID_ARG;
+  out[0] = out[1] = 0;
+  const LevelData& Lv = h->lev[level];
+  if (!Lv.gm_stats) return MGRIT_OK;
+  unsigned long long v[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(v, Lv.gm_stats, sizeof(v), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(cudaStreamSynchronize(h->st));
+  out[0] = (int64_t)v[0];
+  out[1] = (int64_t)v[1];
   return MGRIT_OK;
 }
 

@@ -69,6 +69,9 @@ struct SolveDir {
 // then the factored periodic solve (causal then anticausal recurrences).
 enum CoarseMode { kModeCF = 0, kModeFRES = 1, kModeFOUT = 2, kModeSEQ = 3, kModeAPPLY = 4 };
 
+// largest GMRES iteration cap of the coarse kernel's correction solves
+constexpr int kGmMax = 32;
+
 // TS: storage / SL-gather precision; TC: precision of the banded correction
 // solve (and of its tables).
 template <typename TS, typename TC = TS>
@@ -97,9 +100,18 @@ struct CoarseParams {
   const T* sub;
   T* parent;           // unused by the kernel (kept for the host's bookkeeping)
   double* partial;     // FRES: one slot per CTA (K * csize)
+  // GMRES correction solves (Sec. 6.1, Sec. 6.3), used when gm_max > 0: the
+  // SL weights w are then unscaled and the system is (I - sum phi D) x = S v
+  int gm_max;                    // iteration cap (<= kGmMax); 0: exact banded solve
+  double gm_rtol;                // stop at ||b - A x_k|| <= gm_rtol ||b||
+  TC gm_taps[7];                 // the matrix's taps at offsets -3..3
+  TC* gm_V;                      // Krylov basis scratch: K x (gm_max + 1) x n values
+  unsigned long long* gm_stats;  // [0] += GMRES iterations, [1] += solves (may be null)
 };
 
-size_t coarse_smem_bytes(int npc, int P, int nthr, int elem);
+// bytes of dynamic shared memory of the coarse kernel; gm_elem = sizeof of
+// the GMRES vector type (0: no GMRES)
+size_t coarse_smem_bytes(int npc, int P, int nthr, int elem, int gm_elem = 0);
 
 // ---------------------------------------------------------------------------
 // Level-0 SDIRK step kernel: m (or nsteps) steps of Phi = R_q(-c L_p) for an

@@ -4,18 +4,21 @@
 
 namespace mg {
 
-size_t coarse_smem_bytes(int npc, int P, int nthr, int elem) {
-  // slots of `elem` bytes; scan buffers budgeted at 8 bytes (FP64 solve)
+size_t coarse_smem_bytes(int npc, int P, int nthr, int elem, int gm_elem) {
+  // slots of `elem` bytes; scan buffers budgeted at 8 bytes (FP64 solve);
+  // GMRES: the Krylov vector's halo buffer and the reduction area
   (void)npc;
   const size_t npad = (size_t)nthr * (size_t)(P + 1);
-  return ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + ((104 * 8 + 15) & ~(size_t)15) + 32 * sizeof(double);
+  size_t b = ((3 * npad * (size_t)elem + 15) & ~(size_t)15) + ((104 * 8 + 15) & ~(size_t)15) + 32 * sizeof(double);
+  if (gm_elem > 0) b += ((npad * (size_t)gm_elem + 15) & ~(size_t)15) + (size_t)kGmSharedDoubles * sizeof(double);
+  return b;
 }
 
 int launch_coarse(const CoarseParams<double>& p, cudaStream_t st) { return launch_coarse_any(p, st); }
 
 // Largest cluster size <= want (power of two) that can be co-scheduled.
 int coarse_max_cluster(int want, size_t smem, int nthr) {
-  configure_coarse<double, double, 16, 4>();
+  configure_coarse<double, double, 16, 4, false>();
   for (int c = want; c >= 1; c >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c);
@@ -29,7 +32,7 @@ int coarse_max_cluster(int want, size_t smem, int nthr) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, coarse_kernel<double, double, 16, 4>, &cfg) == cudaSuccess && nc > 0)
+    if (cudaOccupancyMaxActiveClusters(&nc, coarse_kernel<double, double, 16, 4, false>, &cfg) == cudaSuccess && nc > 0)
       return c;
     cudaGetLastError();
   }

@@ -41,10 +41,12 @@ extern "C" int64_t mgrit_estimate_bytes(const mgrit_params* p) {
   if (!p || p->nx <= 0 || p->nt <= 0 || p->m < 2) return -1;
   const int64_t L = levels_of(*p);
   int64_t rows = 0, N = p->nt;
+  const int64_t gm_it = p->coarse_solve == MGRIT_SOLVE_GMRES ? (p->gmres_maxit > 0 ? p->gmres_maxit : 20) : -1;
   for (int64_t l = 0; l < L; ++l) {
     int64_t K = (l < L - 1) ? N / p->m : 0;
     if (l < L - 1) rows += 2 * (K + 1);  // C-point double buffer
     if (l >= 1) rows += N + 1;           // RHS
+    if (l >= 1 && gm_it > 0) rows += std::max<int64_t>(K, 1) * (gm_it + 1);  // GMRES Krylov basis
     N /= p->m;
   }
   int64_t bytes = rows * p->nx * 8;

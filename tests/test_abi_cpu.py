@@ -87,3 +87,28 @@ def test_coarse_operator_choice_validated_on_host(lib):
     erk = pkg.make_params(64, 128, 0.85, 1, coarse_op=pkg.REDISC)
     assert lib.mgrit_setup(ctypes.byref(erk), None, ctypes.byref(h)) == -8
     assert not h.value
+
+
+@pytest.mark.parametrize("kw", [
+    dict(coarse_solve=2),                                  # unknown correction solve
+    dict(coarse_solve=pkg.GMRES, coarse_op=pkg.SL),        # the direct SL operator has no correction system
+    dict(coarse_solve=pkg.GMRES, gmres_maxit=33),          # above the kernel's cap of 32
+    dict(coarse_solve=pkg.GMRES, gmres_maxit=-1),
+    dict(coarse_solve=pkg.GMRES, gmres_rtol=1.5),          # relative tolerance outside (0, 1)
+    dict(coarse_solve=pkg.GMRES, gmres_rtol=-1e-2),
+])
+def test_gmres_parameters_validated_on_host(lib, kw):
+    prm = pkg.make_params(64, 128, 0.85, 3, **kw)
+    h = ctypes.c_void_p()
+    assert lib.mgrit_setup(ctypes.byref(prm), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+def test_estimate_counts_the_gmres_basis(lib):
+    """The admission estimate grows by the Krylov basis: max(K_l, 1) x
+    (cap + 1) rows of n_x doubles per coarse level."""
+    lib.mgrit_estimate_bytes.restype = ctypes.c_int64
+    d = pkg.make_params(256, 1024, 0.85, 3, m=4, levels=3)
+    g = pkg.make_params(256, 1024, 0.85, 3, m=4, levels=3, coarse_solve=pkg.GMRES, gmres_maxit=20)
+    extra = lib.mgrit_estimate_bytes(ctypes.byref(g)) - lib.mgrit_estimate_bytes(ctypes.byref(d))
+    assert extra == (64 + 1) * 21 * 256 * 8  # level 1: 64 intervals; level 2 (coarsest): one vector
