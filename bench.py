@@ -330,6 +330,8 @@ def main():
     ap.add_argument("--precision", default="", choices=["", "fp64", "mixed", "mixed_fast"],
                     help="override the workload's")
     ap.add_argument("--inner", type=int, default=0, help="MIXED: FP32 V-cycles per FP64 residual (0: library default)")
+    ap.add_argument("--coarse-solve", default="direct", choices=["direct", "gmres"],
+                    help="correction solves of the coarse operator (gmres: Sec. 6.3's GMRES)")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload == "c4" and args.impl == "ours":
@@ -366,14 +368,18 @@ def main():
     kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
     prec = {"fp64": pkg.FP64, "mixed": pkg.MIXED, "mixed_fast": pkg.MIXED_FAST}[w["precision"]]
 
-    def make(precision):
+    def make(precision, coarse_solve=pkg.DIRECT):
         prm = pkg.make_params(nx, nt, w["cfl"], w["p"], kind=kind, q=w["q"], m=m, levels=w["levels"], nu=w["nu"],
-                              tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=precision)
+                              tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=precision,
+                              coarse_solve=coarse_solve)
         if args.inner > 0:
             prm.inner_cycles = args.inner
         return pkg.Solver(prm, stream=stream.cuda_stream)
 
-    s = make(prec)
+    main_solve = pkg.GMRES if args.coarse_solve == "gmres" else pkg.DIRECT
+    if main_solve == pkg.GMRES:
+        w["name"] += "_gmres"
+    s = make(prec, main_solve)
     u0_h = make_ic(w)
     u0 = torch.tensor(u0_h, dtype=torch.float64, device="cuda")
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
@@ -440,29 +446,51 @@ def main():
         err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
     dof = nx * nt
     variants = {}
-    if not args.no_variants and prec == pkg.FP64:
-        # the same workload with FP32 relaxation inside FP64 refinement:
-        # "mixed" keeps every correction solve in FP64, "mixed_fast" runs the
-        # well-conditioned ones (kappa <= 1e3) in FP32
-        for vname, vprec in (("mixed", pkg.MIXED), ("mixed_fast", pkg.MIXED_FAST)):
-            sm = make(vprec)
-            outm = torch.empty_like(out)
-            for _ in range(max(1, args.warmup)):
-                stm = sm.solve(u0, outm)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(args.steps):
-                stm = sm.solve(u0, outm)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            mms = e0.elapsed_time(e1) / args.steps
-            errm = (float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
-                    if seq_ms is not None else None)
-            variants[vname] = {"value": dof / (mms / 1e3), "unit": UNIT, "ms": mms,
-                               "outer_iterations": stm["outer_iterations"], "inner_cycles": stm["inner_cycles"],
-                               "max_rel_err_vs_sequential": errm,
-                               "over_sequential": seq_ms / mms if seq_ms is not None else None}
-            sm.close()
+    # the same workload with other choices of the method:
+    #   "mixed" / "mixed_fast"  FP32 relaxation inside FP64 refinement ("mixed"
+    #                           keeps every correction solve in FP64,
+    #                           "mixed_fast" runs the well-conditioned ones,
+    #                           kappa <= 1e3, in FP32)
+    #   "gmres"                 the coarse correction systems solved by GMRES
+    #                           (rel. 1e-2, at most 20 iterations, Sec. 6.3)
+    #                           instead of the exact banded solve
+    vlist = []
+    if not args.no_variants:
+        if prec == pkg.FP64:
+            vlist += [("mixed", pkg.MIXED, pkg.DIRECT), ("mixed_fast", pkg.MIXED_FAST, pkg.DIRECT)]
+        if main_solve == pkg.DIRECT:
+            vlist.append(("gmres", prec, pkg.GMRES))
+    for vname, vprec, vsolve in vlist:
+        sm = make(vprec, vsolve)
+        outm = torch.empty_like(out)
+        for _ in range(max(1, args.warmup)):
+            stm = sm.solve(u0, outm, allow_unconverged=True)
+        torch.cuda.synchronize()
+        g0 = [sm.gmres_stats(l) for l in range(1, w["levels"])]
+        sm.profile(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stm = sm.solve(u0, outm, allow_unconverged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vprof = sm.profile_read()
+        sm.profile(False)
+        mms = e0.elapsed_time(e1) / args.steps
+        errm = (float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+                if seq_ms is not None else None)
+        v = {"value": dof / (mms / 1e3), "unit": UNIT, "ms": mms, "converged": stm["converged"],
+             "rel_residual": stm["rnorm"] / stm["rnorm0"] if stm["rnorm0"] > 0 else 0.0,
+             "iterations": stm["iterations"],
+             "outer_iterations": stm["outer_iterations"], "inner_cycles": stm["inner_cycles"],
+             "max_rel_err_vs_sequential": errm,
+             "over_sequential": seq_ms / mms if seq_ms is not None else None,
+             "coarse_ms": {k: vv[1] / args.steps for k, vv in vprof.items() if k.startswith("coarse")}}
+        if vsolve == pkg.GMRES:
+            g1 = [sm.gmres_stats(l) for l in range(1, w["levels"])]
+            v["gmres_iterations_per_solve"] = [
+                (b[0] - a[0]) / max(1, b[1] - a[1]) for a, b in zip(g0, g1)]
+        variants[vname] = v
+        sm.close()
     clocks = clocks_sampler_stop(cp, cf, clk_path, local)
     scnt, sms, sfl = sprof["sequential"]
 
@@ -503,6 +531,7 @@ def main():
             "config": {"workload": w["name"], "nx": nx, "nt": nt,
                        "scheme": "%s%d+U%d" % (w["kind"].upper(), w["q"], w["p"]), "cfl": w["cfl"],
                        "m": m, "levels": w["levels"], "relax": "FCF", "tol": w["tol"],
+                       "coarse_solve": args.coarse_solve,
                        "iterations": iters, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (
                            (2 * (nt // m + 1) + (nt // m + 1) + 2 * (nt // m ** 2 + 1)) * nx * 8 / 1e6)},

@@ -1109,18 +1109,16 @@ static int tune_coarse(mgrit_handle* h, int l) {
     std::string why;
     return build_redisc(h, l, true, &why);
   }
-  // GMRES levels keep the best-scored geometry: timing depends on the data
-  // through the iteration counts
-  if (h->prm.coarse_solve == MGRIT_SOLVE_GMRES) return MGRIT_OK;
+  const bool gm = h->prm.coarse_solve == MGRIT_SOLVE_GMRES;
   const bool coarsest = (l == h->L - 1);
   const bool f32 = h->mixed && !coarsest;
   std::vector<GeomC> cand = coarse_geometries(h, 10);
   int fc, fp;
   if (cand.size() <= 1 || geom_forced(&fc, &fp)) return MGRIT_OK;
   char keyb[160];
-  std::snprintf(keyb, sizeof(keyb), "coarse:n=%lld:K=%lld:N=%lld:m=%d:p=%d:b=%d:s=%d", (long long)h->nx,
+  std::snprintf(keyb, sizeof(keyb), "coarse:n=%lld:K=%lld:N=%lld:m=%d:p=%d:b=%d:s=%d:gm=%d", (long long)h->nx,
                 (long long)Lv.K, (long long)(coarsest ? Lv.N : 0), h->m, h->prm.order_p, f32 ? 4 : 8,
-                f32 ? (Lv.solve64 ? 8 : 4) : 8);
+                f32 ? (Lv.solve64 ? 8 : 4) : 8, gm ? h->prm.gmres_maxit : 0);
   const std::string key(keyb);
   Geom cg;
   GeomC best = cand[0];
@@ -1129,6 +1127,24 @@ static int tune_coarse(mgrit_handle* h, int l) {
       if (g.C == cg.C && g.P == cg.P && g.nthr == cg.nthr) return coarse_with_geom(h, l, g);
   }
   if (!tuning_on()) return MGRIT_OK;
+  if (gm) {
+    // a GMRES solve's time grows with its iteration count: every candidate
+    // runs on random level data with the stop tolerance at zero (exactly
+    // gmres_maxit iterations per solve); setup zeroes the buffers afterwards
+    const uint64_t sd = h->prm.seed + 0x9e37u + (uint64_t)l;
+    launch_random_cpoints(Lv.g, h->du0, Lv.N + 1, h->nx, 1, sd, h->st);
+    if (Lv.uC[0]) launch_random_cpoints(Lv.uC[0], h->du0, Lv.K + 1, h->nx, 1, sd + 1, h->st);
+    if (f32) {
+      launch_convert(kCvtD2F, Lv.g, Lv.gf, (Lv.N + 1) * h->nx, h->st);
+      launch_convert(kCvtD2F, Lv.uC[0], Lv.uCf[0], (Lv.K + 1) * h->nx, h->st);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  auto gm_timing = [&](auto& cp) {
+    cp.gm_rtol = 0.0;
+    cp.gm_V = reinterpret_cast<decltype(cp.gm_V)>(Lv.gm_V);
+    cp.gm_stats = nullptr;
+  };
   float bms = 1e30f;
   for (auto& g : cand) {
     int rc = coarse_with_geom(h, l, g);
@@ -1136,6 +1152,7 @@ static int tune_coarse(mgrit_handle* h, int l) {
     float ms;
     if (coarsest) {
       CoarseParams<double> cp = Lv.cp;
+      gm_timing(cp);
       cp.mode = kModeSEQ;
       cp.zero_start = 1;
       cp.start = nullptr;
@@ -1149,6 +1166,7 @@ static int tune_coarse(mgrit_handle* h, int l) {
     } else {
       const int64_t Kt = std::min<int64_t>(Lv.K, 608);
       auto fill = [&](auto& cp, auto* start, auto* out, auto* gg) {
+        gm_timing(cp);
         cp.mode = kModeCF;
         cp.zero_start = 0;
         cp.start = start;
