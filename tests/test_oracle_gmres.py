@@ -103,8 +103,9 @@ def _levels_until_two(nt, m):
 
 def test_mgrit_with_gmres_keeps_the_direct_iteration_counts(golden):
     """Sec. 6.3: the GMRES halting rule (1e-2, at most 20) leaves MGRIT's
-    convergence as with direct solves; the V-cycle counts (which the paper
-    measured with GMRES on every level) stay within 2 of Table 3."""
+    convergence as with direct solves; the V-cycle counts stay within 2 of
+    Table 3 (the paper's multilevel ERK runs used GMRES on every level, its
+    SDIRK runs direct solves)."""
     cmax = co.cfl_limit(3)
     for kind, nx, nt, m, two, vc in golden("table3_iterations.txt"):
         nx, nt, m, vc = int(nx), int(nt), int(m), int(vc)
