@@ -76,7 +76,9 @@ typedef struct mgrit_params {
   int64_t nt;       /* time steps; nt % m^(levels-1) == 0                       */
   double cfl;       /* c = alpha dt / h, absolute (not a fraction of c_max)     */
   double alpha;     /* wave speed > 0 (only c enters the discrete operators)    */
-  int order_p;      /* upwind order p in {1, 3, 5} (odd: Sec. 6.3)              */
+  int order_p;      /* upwind order p in 1..5: odd p dissipative (Sec. 6.3),    */
+                    /* even p dispersive (Sec. 6.4: eps-dependent SL nodes,     */
+                    /* first-order left-biased D^{(p+1)}_1; q = p)              */
   int rk_kind;      /* MGRIT_ERK or MGRIT_SDIRK                                 */
   int rk_order_q;   /* q; 0 means q = p.  ERK q = p only; SDIRK q in 1..5       */
   int m;            /* coarsening factor >= 2                                   */
@@ -132,7 +134,7 @@ typedef struct mgrit_handle mgrit_handle;
  *            on the host in FP64 (Sec. 3, Lemma 6.1, Sec. 6.2).
  *   stream : cudaStream_t (as void*) on which all work of the handle runs.
  *   out    : receives the new handle (NULL on failure).
- * Errors: INVALID_ARG (sizes, p even, nt % m^(levels-1), stencil wider than
+ * Errors: INVALID_ARG (sizes, p outside 1..5, nt % m^(levels-1), stencil wider than
  * nx), UNSTABLE (singular correction matrix), OOM, CUDA.
  */
 int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out);

@@ -56,7 +56,12 @@ __device__ __forceinline__ void sl_gather(TC (&x)[P], const T* b0, const T* b1, 
 
 template <typename T, typename TC, int P, int P1, bool GM>
 __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ CoarseParams<T, TC> A) {
-  constexpr int H = P1 / 2;
+  // recurrence orders of the correction solve: (p+1)/2 both ways for the
+  // centred D of odd p (P1 even); (p+2)/2 causal and p/2 anticausal for the
+  // left-biased D of even p (P1 odd).  The GMRES mat-vec reads HCm points on
+  // either side.
+  constexpr int HCm = (P1 % 2 == 0) ? P1 / 2 : (P1 + 1) / 2;
+  constexpr int HAm = (P1 % 2 == 0) ? P1 / 2 : (P1 - 1) / 2;
   constexpr int LP = Log2c<P>::v;
   static_assert((1 << LP) == P, "chunk length must be a power of two");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -140,9 +145,9 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
         sl_gather<T, TC, P, P1, LP>(x, cur ? w01 : w00, cur ? w11 : w10, l0, npc, A.w);
       }
       if constexpr (GM) {
-        gmres_solve<TC, P, H>(x, A, gmv, gms, t, rank, C, k);
+        gmres_solve<TC, P, HCm>(x, A, gmv, gms, t, rank, C, k);
       } else {
-        if (!A.nosolve) banded_solve<H, H, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
+        if (!A.nosolve) banded_solve<HCm, HAm, TC, P>(x, A, sqc, sqa, aggc, agga, t, rank, C);
       }
     }
     if (A.g) __pipeline_wait_prior(0);  // this thread's chunk of the RHS row has landed
@@ -253,8 +258,12 @@ static int launch_coarse_any(const CoarseParams<T, TC>& A, cudaStream_t st) {
   switch (A.p1) {
     case 2:
       return launch_coarse_p<T, TC, 2>(A, st);
+    case 3:
+      return launch_coarse_p<T, TC, 3>(A, st);
     case 4:
       return launch_coarse_p<T, TC, 4>(A, st);
+    case 5:
+      return launch_coarse_p<T, TC, 5>(A, st);
     case 6:
       return launch_coarse_p<T, TC, 6>(A, st);
     default:

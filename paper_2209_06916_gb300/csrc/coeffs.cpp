@@ -292,8 +292,13 @@ void sl_shift(double s, long long* k, double* eps) {
   *eps = e;
 }
 
+int sl_lo(int p, double eps) {
+  if (p % 2) return -(p + 1) / 2;
+  return eps < 0.5 ? -p / 2 : -p / 2 - 1;
+}
+
 std::vector<double> sl_weights(int p, double eps) {
-  int lo = -(p + 1) / 2, n = p + 1;
+  int lo = sl_lo(p, eps), n = p + 1;
   std::vector<double> w(n);
   for (int a = 0; a < n; ++a) {
     ld v = 1.0L;
@@ -305,7 +310,7 @@ std::vector<double> sl_weights(int p, double eps) {
 }
 
 double f_poly(int p, double eps) {
-  int lo = -(p + 1) / 2, hi = (p - 1) / 2;
+  int lo = sl_lo(p, eps), hi = lo + p;
   ld v = 1.0L;
   for (int j = lo; j <= hi; ++j) v *= ((ld)j + (ld)eps);
   return (double)(v / (ld)factorial(p + 1));
@@ -322,6 +327,23 @@ Stencil central_diff(int order) {
   for (int j = -n; j <= n; ++j) {
     double binom = factorial(2 * n) / (factorial(n + j) * factorial(n - j));
     s.a[j + n] = (((n + j) % 2) ? -1.0 : 1.0) * binom;
+  }
+  return s;
+}
+
+Stencil diff_stencil(int order) {
+  if (order % 2 == 0) return central_diff(order);
+  // h^{order} times the order-th derivative of the interpolant through the
+  // order + 1 nodes -(order+1)/2 .. (order-1)/2: d_j = order! / prod (j - k)
+  Stencil s;
+  s.lo = -(order + 1) / 2;
+  s.hi = (order - 1) / 2;
+  s.a.resize(order + 1);
+  for (int j = s.lo; j <= s.hi; ++j) {
+    double den = 1.0;
+    for (int k = s.lo; k <= s.hi; ++k)
+      if (k != j) den *= (double)(j - k);
+    s.a[j - s.lo] = factorial(order) / den;
   }
   return s;
 }

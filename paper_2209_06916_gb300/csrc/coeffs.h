@@ -40,9 +40,18 @@ double e_rk(int kind, int q);
 
 // Sec. 3: semi-Lagrangian shift and weights for odd p.
 void sl_shift(double s, long long* k, double* eps);
-std::vector<double> sl_weights(int p, double eps);  // index j + (p+1)/2, j = -(p+1)/2..(p-1)/2
-double f_poly(int p, double eps);                    // Eq. fpoly_def
+// SL interpolation nodes x_{i-k} + j h, j = sl_lo(p, eps) .. sl_lo + p: odd
+// p the (p+1)/2 points west and (p-1)/2 east of x_{i-k}; even p the p + 1
+// points centred on the mesh point nearer to the departure point (x_{i-k}
+// for eps < 1/2, x_{i-k-1} otherwise, Sec. 3)
+int sl_lo(int p, double eps);
+std::vector<double> sl_weights(int p, double eps);  // index j - sl_lo(p, eps)
+double f_poly(int p, double eps);                    // Eq. fpoly_def on the same node set
 Stencil central_diff(int order);                     // D^{(order)}_2, even order
+// D^{(order)}_s of the corrected coarse operator (Eq. Dp+1_def): even order
+// (odd p, Sec. 6.3) the centred second-order stencil, odd order (even p,
+// Sec. 6.4) the first-order stencil with a one-point bias to the left
+Stencil diff_stencil(int order);
 
 // ERK one-step stencil R(-c L) and its m-th power (Eq. MOL_M_def).
 Stencil erk_step_stencil(int p, int q, double c);

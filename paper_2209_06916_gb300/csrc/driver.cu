@@ -69,6 +69,7 @@ struct LevelData {
   float* rdf_Mt[2] = {nullptr, nullptr};
   long long kshift = 0;
   double eps = 0.0, phi = 0.0, phi_q = 0.0;
+  int jlo = 0;  // SL node offset of weight 0 (sl_lo: depends on eps for even p)
   // GMRES correction solves: unscaled SL weights, the taps of I - sum phi D
   // (offsets -3..3), the Krylov basis scratch for gm_cap intervals (sized
   // for doubles) and the device counters [iterations, solves]
@@ -211,6 +212,10 @@ template <typename T>
 static void fill_solve_dir(SolveDir<T>* d, const double* coef, int horder, int Hpad, int P, int nthr, int C,
                            std::vector<T>* mt_out) {
   std::memset((void*)d, 0, sizeof(*d));
+  if (Hpad == 0) {  // no recurrence in this direction (the kernel skips it)
+    mt_out->clear();
+    return;
+  }
   double c3[3] = {0, 0, 0};
   for (int q = 0; q < horder; ++q) c3[q] = coef[q];
   // carries below the kernel precision are dropped
@@ -349,16 +354,20 @@ static int upload_table(mgrit_handle* h, const std::vector<T>& v, T** dev) {
   return MGRIT_OK;
 }
 
-// Condition number of a symmetric periodic banded matrix from its (real)
-// symbol sampled on the unit circle.
+// Condition number of a periodic banded (circulant, hence normal) matrix:
+// the extreme moduli of its symbol sampled on the unit circle.
 static double band_condition(const Stencil& A) {
   double amin = 1e300, amax = 0.0;
   const int ns = 4096;
   for (int i = 0; i < ns; ++i) {
-    double th = 2.0 * M_PI * i / ns, v = 0.0;
-    for (int t = A.lo; t <= A.hi; ++t) v += A.at(t) * std::cos(t * th);
-    amin = std::min(amin, std::fabs(v));
-    amax = std::max(amax, std::fabs(v));
+    double th = 2.0 * M_PI * i / ns, re = 0.0, im = 0.0;
+    for (int t = A.lo; t <= A.hi; ++t) {
+      re += A.at(t) * std::cos(t * th);
+      im += A.at(t) * std::sin(t * th);
+    }
+    const double v = std::hypot(re, im);
+    amin = std::min(amin, v);
+    amax = std::max(amax, v);
   }
   return amin > 0.0 ? amax / amin : 1e300;
 }
@@ -421,7 +430,8 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   const mgrit_params& P = h->prm;
   LevelData& Lv = h->lev[l];
   const int p = P.order_p;
-  const int H = (p + 1) / 2;
+  // recurrence orders of the kernel (the template's): see build_coarse
+  const int HC = (p % 2) ? (p + 1) / 2 : (p + 2) / 2, HA = (p % 2) ? (p + 1) / 2 : p / 2;
   const BandFactor& bf = Lv.bf;
   CoarseParams<double>& cp = Lv.cp;
   std::memset((void*)&cp, 0, sizeof(cp));
@@ -431,7 +441,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   cp.csize = g.C;
   cp.npc = (int)(h->nx / g.C);
   cp.p1 = p + 1;
-  cp.jlo = -(p + 1) / 2;
+  cp.jlo = Lv.jlo;
   cp.kshift = (int)(((Lv.kshift % h->nx) + h->nx) % h->nx);
   cp.shift = 0;
   cp.nosolve = Lv.nosolve ? 1 : 0;
@@ -449,8 +459,8 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
     Lv.Mtf_dev[d] = nullptr;
   }
   std::vector<double> mtc, mta;
-  fill_solve_dir(&cp.c, bf.cc, bf.hc, H, g.P, g.nthr, g.C, &mtc);
-  fill_solve_dir(&cp.a, bf.ca, bf.ha, H, g.P, g.nthr, g.C, &mta);
+  fill_solve_dir(&cp.c, bf.cc, bf.hc, HC, g.P, g.nthr, g.C, &mtc);
+  fill_solve_dir(&cp.a, bf.ca, bf.ha, HA, g.P, g.nthr, g.C, &mta);
   for (int d = 0; d < 2; ++d) {
     int rc = upload_table(h, d ? mta : mtc, &Lv.Mt_dev[d]);
     if (rc) return rc;
@@ -482,8 +492,8 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
     Lv.cpfd.a = cp.a;
     geom(Lv.cpf);
     std::vector<float> mtcf, mtaf;
-    fill_solve_dir(&Lv.cpf.c, bf.cc, bf.hc, H, g.P, g.nthr, g.C, &mtcf);
-    fill_solve_dir(&Lv.cpf.a, bf.ca, bf.ha, H, g.P, g.nthr, g.C, &mtaf);
+    fill_solve_dir(&Lv.cpf.c, bf.cc, bf.hc, HC, g.P, g.nthr, g.C, &mtcf);
+    fill_solve_dir(&Lv.cpf.a, bf.ca, bf.ha, HA, g.P, g.nthr, g.C, &mtaf);
     int rc = upload_table(h, mtcf, &Lv.Mtf_dev[0]);
     if (!rc) rc = upload_table(h, mtaf, &Lv.Mtf_dev[1]);
     if (rc) return rc;
@@ -566,12 +576,14 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   LevelData& Lv = h->lev[l];
   int p = P.order_p, q = P.rk_order_q;
   Stencil A = stencil_identity();
-  A = stencil_add(A, central_diff(p + 1), -phi_p);
-  if (q != p && phi_q != 0.0) A = stencil_add(A, central_diff(q + 1), -phi_q);
+  A = stencil_add(A, diff_stencil(p + 1), -phi_p);
+  if (q != p && phi_q != 0.0) A = stencil_add(A, diff_stencil(q + 1), -phi_q);
   BandFactor bf;
   if (!band_factor(A, &bf, why)) return MGRIT_ERR_UNSTABLE;
-  const int H = (p + 1) / 2;
-  if (bf.hc > H || bf.ha > H) {
+  // the kernel's recurrence orders: (p+1)/2 both ways for the centred D of
+  // odd p; (p+2)/2 causal and p/2 anticausal for the left-biased D of even p
+  const int HCm = (p % 2) ? (p + 1) / 2 : (p + 2) / 2, HAm = (p % 2) ? (p + 1) / 2 : p / 2;
+  if (bf.hc > HCm || bf.ha > HAm) {
     if (why) *why = "correction band wider than the SL stencil order supports";
     return MGRIT_ERR_UNSUPPORTED;
   }
@@ -592,6 +604,7 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   if (is_mixed(P.precision)) Lv.solve64 = P.precision == MGRIT_MIXED || Lv.kappa > 1e3;
   Lv.kshift = k;
   Lv.eps = eps;
+  Lv.jlo = sl_lo(p, eps);
   Lv.phi = phi_p;
   Lv.phi_q = phi_q;
   std::vector<GeomC> cand = coarse_geometries(h, 1);
@@ -914,16 +927,19 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
   double gamma = 0.0;
   if (!sdirk_program(P.rk_order_q, cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
   Stencil L = upwind_taps(p);
+  int ul, ur;
+  upwind_bias(p, &ul, &ur);
   sp->p1 = L.width();
   sp->llo = L.lo;
-  if (L.lo != -(L.width() / 2)) {
+  // the kernel's layout: taps at -l(p) .. r(p) (Sec. 4.1 bias)
+  if (L.lo != -ul || L.hi != ur) {
     if (why) *why = "upwind stencil offsets outside the kernel's layout";
     return MGRIT_ERR_UNSUPPORTED;
   }
   for (int i = 0; i < L.width(); ++i) sp->ltaps[i] = L.a[i];
   Stencil A = stencil_add(stencil_identity(), L, gamma * cfl);
   if (!band_factor(A, bf, why)) return MGRIT_ERR_UNSTABLE;
-  const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
+  const int HC = ul, HA = ur;
   if (bf->hc > HC || bf->ha > HA || bf->shift != 0) {
     if (why) *why = "stage matrix factorisation outside the kernel's orders";
     return MGRIT_ERR_UNSUPPORTED;
@@ -939,8 +955,8 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
 static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const BandFactor& bf, const Geom& g,
                            std::unique_ptr<SdirkParams<double>>* out, double** mt_dev,
                            std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev) {
-  const int p = h->prm.order_p;
-  const int HC = (p + 1) / 2, HA = (p + 1) / 2 - 1;
+  int HC, HA;  // the kernel's recurrence orders: the upwind bias l(p), r(p)
+  upwind_bias(h->prm.order_p, &HC, &HA);
   out->reset(new SdirkParams<double>(op));
   SdirkParams<double>& sp = **out;
   sp.n = (int)h->nx;
@@ -2103,7 +2119,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.alpha <= 0.0) P.alpha = 1.0;
   if (P.nx < 32 || P.nx % 8 || P.nt < 2 || P.m < 2 || P.cfl <= 0.0 || P.nu < 0 || P.nu > 4)
     return MGRIT_ERR_INVALID_ARG;
-  if (P.order_p != 1 && P.order_p != 3 && P.order_p != 5) return MGRIT_ERR_INVALID_ARG;
+  if (P.order_p < 1 || P.order_p > 5) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_kind != MGRIT_ERK && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_kind == MGRIT_ERK && P.rk_order_q != P.order_p) return MGRIT_ERR_INVALID_ARG;
   if (P.rk_order_q < 1 || P.rk_order_q > 5) return MGRIT_ERR_INVALID_ARG;
@@ -2122,8 +2138,10 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   // m c (Sec. 5): offered for SDIRK only
   if (P.coarse_op == MGRIT_COARSE_REDISC && P.rk_kind != MGRIT_SDIRK) return MGRIT_ERR_UNSUPPORTED;
   // SDIRKq with q != p adds a phi_q D^{(q+1)}_2 correction term: q must be
-  // odd (a symmetric even-order difference) and q <= p (inside the SL band)
-  if (P.rk_kind == MGRIT_SDIRK && (P.rk_order_q > P.order_p || P.rk_order_q % 2 == 0))
+  // odd (a symmetric even-order difference) and q <= p (inside the SL band);
+  // even p (the dispersive schemes of Sec. 6.4) pairs q = p only
+  if (P.rk_kind == MGRIT_SDIRK && P.rk_order_q != P.order_p &&
+      (P.order_p % 2 == 0 || P.rk_order_q > P.order_p || P.rk_order_q % 2 == 0))
     return MGRIT_ERR_UNSUPPORTED;
   if (P.nt % P.m) return MGRIT_ERR_INVALID_ARG;
   int L = P.levels;

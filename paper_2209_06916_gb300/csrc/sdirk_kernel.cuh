@@ -31,8 +31,11 @@ struct Log2<1> {
 
 template <typename T, int P, int P1>
 __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ SdirkParams<T> A) {
-  constexpr int HC = P1 / 2, HA = P1 / 2 - 1;
-  constexpr int LLO = -(P1 / 2);     // L_p taps at offsets LLO .. LLO + P1 - 1
+  // L_p taps at offsets LLO .. LLO + P1 - 1, LLO = -l(p) (Sec. 4.1 bias:
+  // l = (p+1)/2 for odd p, p/2 + 1 for even p); the stage solves' recurrence
+  // orders are l (causal) and r = P1 - 1 - l (anticausal)
+  constexpr int LLO = (P1 % 2 == 0) ? -(P1 / 2) : -((P1 + 1) / 2);
+  constexpr int HC = -LLO, HA = P1 - 1 + LLO;
   constexpr int HL = -LLO;           // left halo width
   constexpr int HR = P1 - 1 + LLO;   // right halo width
   constexpr int LP = Log2<P>::v;
@@ -242,8 +245,12 @@ static int launch_sdirk_any(const SdirkParams<T>& A, cudaStream_t st) {
   switch (A.p1) {
     case 2:
       return launch_sdirk_p<T, 2>(A, st);
+    case 3:
+      return launch_sdirk_p<T, 3>(A, st);
     case 4:
       return launch_sdirk_p<T, 4>(A, st);
+    case 5:
+      return launch_sdirk_p<T, 5>(A, st);
     case 6:
       return launch_sdirk_p<T, 6>(A, st);
     default:

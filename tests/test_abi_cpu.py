@@ -49,7 +49,8 @@ def test_strerror_texts(lib):
 
 @pytest.mark.parametrize("kw", [
     dict(nx=30, nt=128, cfl=0.85, p=1),            # nx too small / not a multiple of 8
-    dict(nx=64, nt=128, cfl=0.85, p=2),            # even p
+    dict(nx=64, nt=128, cfl=0.85, p=6),            # p outside 1..5
+    dict(nx=64, nt=128, cfl=0.85, p=0),
     dict(nx=64, nt=130, cfl=0.85, p=1, m=4),       # nt % m
     dict(nx=64, nt=128, cfl=0.85, p=1, m=4, levels=5),  # nt % m^(L-1)
     dict(nx=64, nt=128, cfl=-1.0, p=1),            # c <= 0
@@ -65,10 +66,11 @@ def test_invalid_parameters_rejected_on_host(lib, kw):
     assert not h.value
 
 
-@pytest.mark.parametrize("q", [2, 4, 5])
-def test_sdirk_q_outside_the_correction_band_unsupported(lib, q):
-    """SDIRKq with q != p needs an odd q <= p (the phi_q D^{(q+1)} term)."""
-    prm = pkg.make_params(64, 128, 2.0, 3, kind=pkg.SDIRK, q=q)
+@pytest.mark.parametrize("p,q", [(3, 2), (3, 4), (3, 5), (2, 1), (4, 3), (4, 2)])
+def test_sdirk_q_outside_the_correction_band_unsupported(lib, p, q):
+    """SDIRKq with q != p needs an odd q <= p (the phi_q D^{(q+1)} term);
+    even p pairs q = p only."""
+    prm = pkg.make_params(64, 128, 2.0, p, kind=pkg.SDIRK, q=q)
     h = ctypes.c_void_p()
     assert lib.mgrit_setup(ctypes.byref(prm), None, ctypes.byref(h)) == -8
 

@@ -137,7 +137,7 @@ def _rel(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
 
-@pytest.mark.parametrize("p", [1, 3, 5])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_lemma_3_1_sl_truncation_error(p):
     """u(t+dt) - S u(t) = (-1)^{p+1} f_{p+1}(eps) D^{(p+1)} u(t+dt) + O(h^{p+2})."""
     ratios = []
@@ -153,7 +153,8 @@ def test_lemma_3_1_sl_truncation_error(p):
     assert ratios[-1] < 0.1 and ratios[-1] < ratios[0]
 
 
-@pytest.mark.parametrize("p,kind", [(1, "erk"), (3, "erk"), (5, "erk"), (1, "sdirk"), (3, "sdirk")])
+@pytest.mark.parametrize("p,kind", [(1, "erk"), (2, "erk"), (3, "erk"), (4, "erk"), (5, "erk"), (1, "sdirk"),
+                                    (2, "sdirk"), (3, "sdirk"), (4, "sdirk")])
 def test_lemma_4_2_mol_truncation_error(p, kind):
     """u(t+dt) - Phi u(t) = -[c e_FD D^{(p+1)} + (-c)^{q+1} e_RK D^{(q+1)}]
     u(t+dt) + O(h^{p+2}) for q = p (Lemma 4.2)."""
@@ -183,11 +184,14 @@ def _ideal_vs_coarse(p, kind, c, m, nx, phi_override=None):
 
 
 @pytest.mark.parametrize("p,kind,c,m", [(1, "erk", 0.85, 4), (3, "erk", 0.85, 8), (1, "sdirk", 1.3, 4),
-                                        (3, "sdirk", 2.2, 4), (5, "erk", 0.9, 4)])
+                                        (3, "sdirk", 2.2, 4), (5, "erk", 0.9, 4),
+                                        (2, "erk", 0.5, 4), (4, "erk", 0.6, 4), (2, "sdirk", 1.3, 4),
+                                        (4, "sdirk", 2.2, 4)])
 def test_lemma_6_1_corrected_operator_order(p, kind, c, m):
     """Psi_ideal u = (I - phi D)^{-1} S^{(m dt)} u + O(h^{p+2})  (Lemma 6.1):
     halving h cuts the mismatch by ~2^{p+2}; the uncorrected SL step (phi = 0)
-    and a sign-flipped phi only by ~2^{p+1}."""
+    and a sign-flipped phi only by ~2^{p+1}.  Even p (Sec. 6.4): the same
+    with the eps-dependent SL node set and the first-order, left-biased D."""
     n1, n2 = (32, 64) if p == 5 else (64, 128)
     e1 = _ideal_vs_coarse(p, kind, c, m, n1)
     e2 = _ideal_vs_coarse(p, kind, c, m, n2)

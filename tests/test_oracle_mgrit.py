@@ -227,3 +227,22 @@ def test_direct_operator_symbols_match_application(coarse_op):
             u = np.exp(1j * w * x)
             got = op.apply(u.real) + 1j * op.apply(u.imag)
             assert np.max(np.abs(got - op.symbol(w) * u)) < 1e-12
+
+
+def test_even_p_measured_factor_follows_the_lfa_jump():
+    """Sec. 6.4: for ERK4+U4 with m = 2 the two-level LFA factor jumps from
+    about 0.15 just below c/c_max = 0.24 to about 0.84 just above (a shift of
+    the coarse SL stencil); two-level MGRIT measures the same jump and stays
+    at or below the LFA value on both sides."""
+    cmax = co.cfl_limit(4)
+    nx, nt = 256, 1024
+    u0 = ic_sin4(nx)
+    out = {}
+    for frac in (0.23, 0.25):
+        c = frac * cmax
+        res = mgrit.solve(mgrit.Hierarchy(4, "erk", 4, c, 2, 2), u0, nt, tol=1e-10, max_iter=80)
+        pred = lfa.two_level_factor(4, "erk", c, 2, omit=10)
+        assert res["converged"] and res["factor"] < 1.05 * pred, (frac, res["factor"], pred)
+        out[frac] = res
+    assert out[0.25]["factor"] > 3 * out[0.23]["factor"]
+    assert out[0.25]["iterations"] > 3 * out[0.23]["iterations"]
