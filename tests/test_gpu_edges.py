@@ -100,3 +100,56 @@ def test_degenerate_hierarchies(kind, p, q, c, nx, nt, m, levels, nu):
             ref = omg.solve(omg.Hierarchy(p, kname, q, c, m, levels), u0, nt, nu=nu, tol=1e-10, max_iter=40,
                             seed=4)
             assert st["iterations"] == ref["iterations"]
+
+
+def test_gmres_at_the_largest_vector():
+    """GMRES correction solves (P <= 8 chunks, clusters of up to 16 CTAs x
+    256 threads) at n_x = 32768, the largest vector they take; Psi_1 on 3
+    random vectors against the oracle's GMRES, same iteration counts."""
+    nx, m, levels = 32768, 4, 3
+    prm = pkg.make_params(nx, m ** (levels - 1) * 2, 1.38, 3, m=m, levels=levels, coarse_solve=pkg.GMRES)
+    s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+    x = np.random.default_rng(3).standard_normal((3, nx))
+    y = torch.empty((3, nx), dtype=torch.float64, device="cuda")
+    s.coarse_apply(1, torch.tensor(x, device="cuda"), y, 3)
+    torch.cuda.synchronize()
+    op = oops.coarse_operator(3, "erk", 3, 1.38, m, 1, levels, gmres=(1e-2, 20))
+    want = op.apply(x)
+    assert np.max(np.abs(y.cpu().numpy() - want)) < 1e-12 * np.max(np.abs(want))
+    assert s.gmres_stats(1)[0] == sum(op.gmres_its)
+    s.close()
+    # one past it is refused on the host
+    with pytest.raises(pkg.MgritError):
+        pkg.Solver(pkg.make_params(65536, 32, 1.38, 3, m=4, levels=3, coarse_solve=pkg.GMRES))
+
+
+@pytest.mark.parametrize("kind,p,c,nx,m,levels", [
+    (pkg.ERK, 4, 0.3, 131072, 4, 3),    # the longest vector, dispersive U4
+    (pkg.SDIRK, 2, 1.0, 65536, 4, 3),
+])
+def test_even_p_longest_vectors(kind, p, c, nx, m, levels):
+    nt = m ** (levels - 1) * 2
+    u0 = ic_fourier(nx, seed=8)
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=p, m=m, levels=levels, tol=1e-11, max_iter=40, seed=2)
+    out, st = _solve(prm, u0)
+    assert st["converged"]
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    ks = list(range(nt // m + 1))
+    want = _closed_form(oops.FineOperator(p, kname, p, c), u0, [k * m for k in ks])
+    got = out.cpu().numpy()
+    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-9 * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("kind,p,c,nx,nt,m,levels,nu", [
+    (pkg.ERK, 2, 0.3, 64, 4, 4, 2, 1),        # one CF-interval
+    (pkg.ERK, 4, 0.25, 64, 16, 4, 3, 0),      # one-step coarsest level, F-relaxation
+    (pkg.SDIRK, 4, 1.0, 64, 8, 2, 3, 1),
+])
+def test_even_p_degenerate_hierarchies(kind, p, c, nx, nt, m, levels, nu):
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    u0 = ic_sin4_noise(nx, seed=6)
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=p, m=m, levels=levels, nu=nu, tol=1e-10, max_iter=60, seed=4)
+    out, st = _solve(prm, u0)
+    ref = omg.solve(omg.Hierarchy(p, kname, p, c, m, levels), u0, nt, nu=nu, tol=1e-10, max_iter=60, seed=4)
+    assert st["converged"] and st["iterations"] == ref["iterations"]
+    assert np.max(np.abs(out.cpu().numpy() - ref["u"][::m])) < 1e-10 * np.max(np.abs(u0))
