@@ -615,12 +615,15 @@ static int build_coarse(mgrit_handle* h, int l, double phi_p, double phi_q, long
   return coarse_with_geom(h, l, cand[0]);
 }
 
-// Level-0 SDIRK step programme: stiffly accurate stages (q <= 4),
-//   R_i = u (i >= 1);  Y_i = (I + gamma c L)^{-1} R_i;  R_j += -c a_ji L Y_i,
+// Level-0 SDIRK step programme: stiffly accurate stages (q <= 4), with the
+// stage derivative taken from the solve itself: (I + gamma c L) Y_i = R_i
+// gives c L Y_i = (R_i - Y_i) / gamma, so
+//   R_0 = u, R_i = u (i >= 1);  Y_i = (I + gamma c L)^{-1} R_i;
+//   R_j += -(a_ji / gamma) (R_i - Y_i) for j > i  (local: no L_p halos);
 // u_new = Y_s; or the factored SDIRK5 stability function
 //   v <- (I + gamma c L)^{-1} f_k(-c L) v for each real factor f_k of P,
 // then the remaining solves.
-static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamma, std::string* why) {
+static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamma, std::string* why, bool deriv) {
   int n = 0;
   auto op = [&](int kind, int dst, int src, double cf) {
     if (n >= kSdirkMaxOps) return;
@@ -630,7 +633,7 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
     sp->opc[n] = cf;
     ++n;
   };
-  if (q <= 4) {
+  if (q <= 4 && !deriv) {
     SdirkTableau tb;
     if (!sdirk_tableau(q, &tb)) return false;
     *gamma = tb.A[0][0];
@@ -641,6 +644,29 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
     }
     sp->nslots = tb.s;
     sp->result = tb.s - 1;
+  } else if (q <= 4) {
+    SdirkTableau tb;
+    if (!sdirk_tableau(q, &tb)) return false;
+    const double g = tb.A[0][0];
+    *gamma = g;
+    const int s = tb.s;
+    // slots: 0 = u (= R_0), 1 .. s-1 = R_1 .. R_{s-1}, s = the solve output
+    // of stages 0 .. s-2; the last stage solves straight into slot 0
+    const int T = s;
+    for (int i = 1; i < s; ++i) op(kOpCopy, i, 0, 0.0);
+    for (int i = 0; i < s; ++i) {
+      const bool last = (i == s - 1);
+      op(kOpSolve, last ? 0 : T, i, 0.0);
+      if (last) break;
+      for (int j = i + 1; j < s; ++j) {
+        const double a = tb.A[j][i] / g;
+        if (a == 0.0) continue;
+        op(kOpAxpy, j, i, -a);
+        op(kOpAxpy, j, T, a);
+      }
+    }
+    sp->nslots = (s == 1) ? 1 : s + 1;
+    sp->result = 0;
   } else {
     std::vector<std::vector<double>> f = sdirk5_factors(gamma);
     for (auto& fk : f) {
@@ -698,7 +724,7 @@ static void tune_store(const std::string& key, int r) {
 // to a slot whose halos were read since the last barrier (write after read).
 // Consecutive AXPYLs on one source form a group (one mat-vec).  The
 // schedule is iterated over steps until it is stable.
-static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
+static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why, bool one_pass) {
   const int n = sp->nops;
   for (int o = 0; o < n; ++o) {
     sp->opg[o] = 1;
@@ -721,9 +747,15 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
     for (int e = 1; e < g; ++e) sp->opg[o + e] = 0;
     o += g;
   }
+  // A solve with a single recurrence direction (one_pass: no anticausal
+  // order) ends with remote reads of its cluster-visible carry aggregate and
+  // of the CTA's warp carries; the next solve rewrites both, so a barrier
+  // must separate two such solves (the anticausal pass's barrier does it
+  // otherwise).  `S` tracks a one-pass solve since the last barrier.
   for (int pass = 0; pass < 16; ++pass) {
     bool changed = false;
     unsigned W = 0, R = 0;  // slots written / halo-read since the last barrier
+    bool S = false;
     for (int step = 0; step < 4; ++step) {
       for (int o = 0; o < n;) {
         const int kind = sp->opk[o];
@@ -736,13 +768,20 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
             sp->opb[o] = 1;
             changed = true;
           }
-          if (sp->opb[o]) W = R = 0;
+          if (sp->opb[o]) {
+            W = R = 0;
+            S = false;
+          }
           R |= 1u << sp->ops[o];
           W |= dsts;
           o += g;
         } else if (kind == kOpSolve) {
-          if (sp->opb[o]) W = R = 0;
+          if (S && !sp->opb[o]) {
+            sp->opb[o] = 1;
+            changed = true;
+          }
           W = R = 0;  // the solve's own barriers precede its write
+          S = one_pass;
           W |= 1u << sp->opd[o];
           ++o;
         } else {
@@ -751,7 +790,10 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
             sp->opb[o] = 1;
             changed = true;
           }
-          if (sp->opb[o]) W = R = 0;
+          if (sp->opb[o]) {
+            W = R = 0;
+            S = false;
+          }
           W |= 1u << dst;
           ++o;
         }
@@ -761,7 +803,10 @@ static bool schedule_sdirk(SdirkParams<double>* sp, std::string* why) {
           sp->resb = 1;
           changed = true;
         }
-        if (sp->resb) W = R = 0;
+        if (sp->resb) {
+          W = R = 0;
+          S = false;
+        }
         W |= 1u;
       }
     }
@@ -920,12 +965,13 @@ static void fold_solve_scale(SdirkParams<double>* sp) {
 
 // Geometry-free part of the level-0 SDIRK operator: the step programme with
 // its barrier schedule, L_p taps, the factorised stage matrix.
-static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why, double cfl) {
+static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* bf, std::string* why, double cfl,
+                          bool deriv) {
   const mgrit_params& P = h->prm;
   const int p = P.order_p;
   std::memset((void*)sp, 0, sizeof(*sp));
   double gamma = 0.0;
-  if (!sdirk_program(P.rk_order_q, cfl, sp, &gamma, why)) return MGRIT_ERR_UNSUPPORTED;
+  if (!sdirk_program(P.rk_order_q, cfl, sp, &gamma, why, deriv)) return MGRIT_ERR_UNSUPPORTED;
   Stencil L = upwind_taps(p);
   int ul, ur;
   upwind_bias(p, &ul, &ur);
@@ -946,15 +992,15 @@ static int sdirk_operator(mgrit_handle* h, SdirkParams<double>* sp, BandFactor* 
   }
   sp->sscale = bf->inv_kappa;
   fold_solve_scale(sp);
-  if (!schedule_sdirk(sp, why)) return MGRIT_ERR_UNSUPPORTED;
+  if (!schedule_sdirk(sp, why, bf->ha == 0)) return MGRIT_ERR_UNSUPPORTED;
   return MGRIT_OK;
 }
 
 // The SDIRK step parameters for geometry g (FP64, and FP32 when outf):
 // chunk-scan tables on the host, per-chunk carry tables uploaded.
-static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const BandFactor& bf, const Geom& g,
-                           std::unique_ptr<SdirkParams<double>>* out, double** mt_dev,
-                           std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev) {
+static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const SdirkParams<double>& op32,
+                           const BandFactor& bf, const Geom& g, std::unique_ptr<SdirkParams<double>>* out,
+                           double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev) {
   int HC, HA;  // the kernel's recurrence orders: the upwind bias l(p), r(p)
   upwind_bias(h->prm.order_p, &HC, &HA);
   out->reset(new SdirkParams<double>(op));
@@ -988,20 +1034,21 @@ static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const
     f.npc = sp.npc;
     f.p1 = sp.p1;
     f.llo = sp.llo;
-    for (int i = 0; i < 8; ++i) f.ltaps[i] = (float)sp.ltaps[i];
-    f.sscale = (float)sp.sscale;
-    f.rscale = (float)sp.rscale;
-    f.nops = sp.nops;
-    f.nslots = sp.nslots;
-    f.result = sp.result;
-    f.resb = sp.resb;
+    // the FP32 step runs its own programme (op32)
+    for (int i = 0; i < 8; ++i) f.ltaps[i] = (float)op32.ltaps[i];
+    f.sscale = (float)op32.sscale;
+    f.rscale = (float)op32.rscale;
+    f.nops = op32.nops;
+    f.nslots = op32.nslots;
+    f.result = op32.result;
+    f.resb = op32.resb;
     for (int o = 0; o < kSdirkMaxOps; ++o) {
-      f.opk[o] = sp.opk[o];
-      f.opd[o] = sp.opd[o];
-      f.ops[o] = sp.ops[o];
-      f.opg[o] = sp.opg[o];
-      f.opb[o] = sp.opb[o];
-      f.opc[o] = (float)sp.opc[o];
+      f.opk[o] = op32.opk[o];
+      f.opd[o] = op32.opd[o];
+      f.ops[o] = op32.ops[o];
+      f.opg[o] = op32.opg[o];
+      f.opb[o] = op32.opb[o];
+      f.opc[o] = (float)op32.opc[o];
     }
     for (int d = 0; d < 2; ++d) {
       dev_free(h, mtf_dev[d]);
@@ -1028,14 +1075,22 @@ static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const
 static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkParams<double>>* out,
                               double** mt_dev, std::unique_ptr<SdirkParams<float>>* outf, float** mtf_dev,
                               std::string* why, bool buffers, double cfl) {
-  SdirkParams<double> op;
-  BandFactor bf;
+  // FP64 steps take the stage derivatives from the solves (no L_p
+  // applications); FP32 steps keep the mat-vec form, whose rounding leaves
+  // MIXED refinement at FP64 MGRIT's accuracy (the derivative form's FP32
+  // rounding let the error at a 1e-10 residual grow ~15x on the 16384 x
+  // 65536 SDIRK3+U5 workload)
+  SdirkParams<double> op, op32;
+  BandFactor bf, bf32;
   if (cfl <= 0.0) cfl = h->prm.cfl;
-  int rc = sdirk_operator(h, &op, &bf, why, cfl);
+  int rc = sdirk_operator(h, &op, &bf, why, cfl, true);
   if (rc) return rc;
+  if (outf && (rc = sdirk_operator(h, &op32, &bf32, why, cfl, false))) return rc;
   const int elem = outf ? 4 : 8;
   auto smem_of = [&](const Geom& g) {
-    return sdirk_smem_bytes((int)(h->nx / g.C), g.P, g.nthr, op.nslots, elem);
+    size_t b = sdirk_smem_bytes((int)(h->nx / g.C), g.P, g.nthr, op.nslots, 8);
+    if (outf) b = std::max(b, sdirk_smem_bytes((int)(h->nx / g.C), g.P, g.nthr, op32.nslots, 4));
+    return b;
   };
   std::vector<Geom> cand = chunk_geometries(h->nx, 1, elem, smem_of, 6);
   if (cand.empty()) {
@@ -1066,7 +1121,7 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
     const int64_t Kt = seq ? 1 : std::min<int64_t>(K, 608);
     float bms = 1e30f;
     for (auto& g : cand) {
-      if ((rc = sdirk_with_geom(h, op, bf, g, out, mt_dev, outf, mtf_dev))) return rc;
+      if ((rc = sdirk_with_geom(h, op, op32, bf, g, out, mt_dev, outf, mtf_dev))) return rc;
       float ms;
       if (outf) {
         SdirkParams<float> sp = **outf;
@@ -1103,7 +1158,7 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
     }
     geom_store(key, best);
   }
-  return sdirk_with_geom(h, op, bf, best, out, mt_dev, outf, mtf_dev);
+  return sdirk_with_geom(h, op, op32, bf, best, out, mt_dev, outf, mtf_dev);
 }
 
 static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) {

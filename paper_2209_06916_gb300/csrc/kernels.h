@@ -127,7 +127,7 @@ size_t coarse_smem_bytes(int npc, int P, int nthr, int elem, int gm_elem = 0);
 // ---------------------------------------------------------------------------
 enum SdirkOpKind { kOpCopy = 0, kOpZero = 1, kOpAxpy = 2, kOpAxpyL = 3, kOpSolve = 4 };
 constexpr int kSdirkMaxOps = 40;
-constexpr int kSdirkMaxSlots = 5;
+constexpr int kSdirkMaxSlots = 6;
 
 template <typename T>
 struct SdirkParams {
