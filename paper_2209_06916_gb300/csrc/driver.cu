@@ -631,7 +631,13 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
     sp->opd[n] = dst;
     sp->ops[n] = src;
     sp->opc[n] = cf;
+    sp->opc2[n] = 0.0;
     ++n;
+  };
+  auto axpby = [&](int dst, int src, double cf2, double cf) {  // dst = cf2 dst + cf src
+    if (n >= kSdirkMaxOps) return;
+    op(kOpAxpby, dst, src, cf);
+    sp->opc2[n - 1] = cf2;
   };
   if (q <= 4 && !deriv) {
     SdirkTableau tb;
@@ -650,22 +656,54 @@ static bool sdirk_program(int q, double c, SdirkParams<double>* sp, double* gamm
     const double g = tb.A[0][0];
     *gamma = g;
     const int s = tb.s;
-    // slots: 0 = u (= R_0), 1 .. s-1 = R_1 .. R_{s-1}, s = the solve output
-    // of stages 0 .. s-2; the last stage solves straight into slot 0
-    const int T = s;
-    for (int i = 1; i < s; ++i) op(kOpCopy, i, 0, 0.0);
-    for (int i = 0; i < s; ++i) {
-      const bool last = (i == s - 1);
-      op(kOpSolve, last ? 0 : T, i, 0.0);
-      if (last) break;
-      for (int j = i + 1; j < s; ++j) {
-        const double a = tb.A[j][i] / g;
-        if (a == 0.0) continue;
-        op(kOpAxpy, j, i, -a);
-        op(kOpAxpy, j, T, a);
+    if (s == 1) {
+      op(kOpSolve, 0, 0, 0.0);
+      sp->nslots = 1;
+    } else {
+      // the later stages' right-hand sides P_j accumulate in slots freed by
+      // earlier stages: Y_0 = solve(u); P_j = (1 - al_j) u + al_j Y_0 with
+      // al_j = a_j0 / gamma (P_1 in place of Y_0, formed last); then for
+      // each stage i >= 1: Y_i = solve(P_i), P_j -= (a_ji/gamma)(P_i - Y_i);
+      // the last stage solves into slot 0.  Peak s slots (3 for SDIRK3).
+      std::vector<int> Pj(s, -1), freel;
+      int nsl = 1;  // slot 0 holds u
+      auto alloc = [&]() {
+        if (!freel.empty()) {
+          const int x = freel.back();
+          freel.pop_back();
+          return x;
+        }
+        return nsl++;
+      };
+      const int y0 = alloc();
+      op(kOpSolve, y0, 0, 0.0);
+      for (int j = s - 1; j >= 1; --j) {
+        const double al = tb.A[j][0] / g;
+        if (j == 1) {
+          axpby(y0, 0, al, 1.0 - al);
+          Pj[1] = y0;
+        } else {
+          Pj[j] = alloc();
+          op(kOpCopy, Pj[j], 0, 0.0);
+          if (al != 0.0) axpby(Pj[j], y0, 1.0 - al, al);
+        }
       }
+      freel.push_back(0);  // u is dead
+      for (int i = 1; i < s - 1; ++i) {
+        const int yi = alloc();
+        op(kOpSolve, yi, Pj[i], 0.0);
+        for (int j = i + 1; j < s; ++j) {
+          const double a = tb.A[j][i] / g;
+          if (a == 0.0) continue;
+          op(kOpAxpy, Pj[j], Pj[i], -a);
+          op(kOpAxpy, Pj[j], yi, a);
+        }
+        freel.push_back(Pj[i]);
+        freel.push_back(yi);
+      }
+      op(kOpSolve, 0, Pj[s - 1], 0.0);
+      sp->nslots = nsl;
     }
-    sp->nslots = (s == 1) ? 1 : s + 1;
     sp->result = 0;
   } else {
     std::vector<std::vector<double>> f = sdirk5_factors(gamma);
@@ -954,6 +992,9 @@ static void fold_solve_scale(SdirkParams<double>* sp) {
           sp->opc[o] *= scale[dst] / scale[src];
         }
         break;
+      case kOpAxpby:  // dst keeps its scale; only the source term is rescaled
+        sp->opc[o] *= scale[dst] / scale[src];
+        break;
       default:  // kOpSolve
         scale[dst] = scale[src] * kappa;
         zero[dst] = false;
@@ -1049,6 +1090,7 @@ static int sdirk_with_geom(mgrit_handle* h, const SdirkParams<double>& op, const
       f.opg[o] = op32.opg[o];
       f.opb[o] = op32.opb[o];
       f.opc[o] = (float)op32.opc[o];
+      f.opc2[o] = (float)op32.opc2[o];
     }
     for (int d = 0; d < 2; ++d) {
       dev_free(h, mtf_dev[d]);
@@ -1277,16 +1319,17 @@ static int tune_coarse(mgrit_handle* h, int l) {
 
 // Algorithmic flops of `steps` SDIRK steps on K vectors: 2 per multiply-add
 // of the two recurrences of each solve, of each L_p mat-vec (plus its axpy)
-// and of each axpy, and 1 for the step's 1/kappa scaling.
+// and of each axpy, 3 per axpby, and 1 for the step's 1/kappa scaling.
 template <typename T>
 static double sdirk_flops(const SdirkParams<T>& sp, int64_t nx, int64_t K, int64_t steps) {
-  int nsolve = 0, naxl = 0, nax = 0;
+  int nsolve = 0, naxl = 0, nax = 0, naxb = 0;
   for (int o = 0; o < sp.nops; ++o) {
     nsolve += sp.opk[o] == kOpSolve;
     naxl += sp.opk[o] == kOpAxpyL;
     nax += sp.opk[o] == kOpAxpy;
+    naxb += sp.opk[o] == kOpAxpby;
   }
-  const double per_pt = 2.0 * (nsolve * (sp.c.h + sp.a.h) + naxl * (sp.p1 + 1) + nax) + 1.0;
+  const double per_pt = 2.0 * (nsolve * (sp.c.h + sp.a.h) + naxl * (sp.p1 + 1) + nax) + 3.0 * naxb + 1.0;
   return per_pt * (double)nx * (double)K * (double)steps;
 }
 

@@ -119,13 +119,14 @@ size_t coarse_smem_bytes(int npc, int P, int nthr, int elem, int gm_elem = 0);
 // program over shared-memory vector slots (slot 0 holds the state):
 //   COPY  dst = src          ZERO  dst = 0          AXPY  dst += c src
 //   AXPYL dst += c L_p src   SOLVE dst = kappa (I + gamma c L_p)^{-1} src
+//   AXPBY dst = c2 dst + c src
 // (the solve leaves out the 1/kappa of its factorisation; the host keeps a
 // scale per slot, folds it into the coefficients and undoes it once per
 // step with rscale)
 // built on the host from the tableau (stiffly accurate stages) or from the
 // factored stability function (SDIRK5).
 // ---------------------------------------------------------------------------
-enum SdirkOpKind { kOpCopy = 0, kOpZero = 1, kOpAxpy = 2, kOpAxpyL = 3, kOpSolve = 4 };
+enum SdirkOpKind { kOpCopy = 0, kOpZero = 1, kOpAxpy = 2, kOpAxpyL = 3, kOpSolve = 4, kOpAxpby = 5 };
 constexpr int kSdirkMaxOps = 40;
 constexpr int kSdirkMaxSlots = 6;
 
@@ -143,6 +144,7 @@ struct SdirkParams {
   int opb[kSdirkMaxOps];   // 1: barrier over the vector's threads before the op (halo hazards)
   int resb;                // barrier before the end-of-step copy result -> slot 0
   T opc[kSdirkMaxOps];
+  T opc2[kSdirkMaxOps];  // AXPBY: dst = opc2 * dst + opc * src
   int mode;            // kModeCF, kModeFRES, kModeFOUT, kModeAPPLY, kModeSEQ
   int zero_start, nsteps;
   int m;               // coarsening factor (RHS row of step s of interval k: k m + s)

@@ -101,6 +101,10 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
         const T cf = A.opc[o];
 #pragma unroll
         for (int j = 0; j < P; ++j) dst[j] = fma(cf, src[j], dst[j]);
+      } else if (kind == kOpAxpby) {
+        const T cf = A.opc[o], cf2 = A.opc2[o];
+#pragma unroll
+        for (int j = 0; j < P; ++j) dst[j] = fma(cf, src[j], cf2 * dst[j]);
       } else if (kind == kOpAxpyL) {
         // acc = L_p src on this chunk (sliding window), then every op of
         // the group: dst_g += c_g acc
