@@ -528,7 +528,7 @@ def main():
     if w["name"] == WORKLOADS["c2"]["name"] and prec == pkg.FP64 and nt == WORKLOADS["c2"]["nt"]:
         traffic = 94.1e6
     elif w["name"] == WORKLOADS["c3"]["name"] and nt == WORKLOADS["c3"]["nt"]:
-        traffic = 794e6
+        traffic = 798e6
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
