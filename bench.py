@@ -400,7 +400,11 @@ def main():
         st = s.solve(u0, out)
     torch.cuda.synchronize()
 
-    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    # raw nvidia-smi samples of the timed region (BENCH_CLOCKS_DIR, else the
+    # system's temporary directory); the JSON line carries their summary
+    import tempfile
+    clk_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, "bench_clocks_rank%d.csv" % rank)
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     cp, cf = clocks_sampler_start(clk_path)
     time.sleep(0.5)
