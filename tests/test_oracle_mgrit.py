@@ -246,3 +246,20 @@ def test_even_p_measured_factor_follows_the_lfa_jump():
         out[frac] = res
     assert out[0.25]["factor"] > 3 * out[0.23]["factor"]
     assert out[0.25]["iterations"] > 3 * out[0.23]["iterations"]
+
+
+def test_lfa_factors_of_the_workloads():
+    """Two-level LFA factors of the benchmark workloads (Eq. rho-asym), as an
+    independent derivation of the same formula also gives them: ERK1+U1 c =
+    0.85, m = 4: 0.212; ERK3+U3 c = 0.85, m = 8: 0.160 (0.185 at 0.85 c_max);
+    U5 + SDIRK3 c = 4, m = 16 with the two-term correction of the q != p
+    reading: 0.353 -- while the one-term phi of Lemma 6.1 taken literally
+    for q != p gives a divergent coarse operator (factor > 1)."""
+    assert abs(lfa.two_level_factor(1, "erk", 0.85, 4) - 0.212) < 2e-3
+    assert abs(lfa.two_level_factor(3, "erk", 0.85, 8) - 0.160) < 2e-3
+    assert abs(lfa.two_level_factor(3, "erk", 0.85 * co.cfl_limit(3), 8) - 0.185) < 2e-3
+    om = lfa.omega_samples(2048, 0)
+    lam = ops.FineOperator(5, "sdirk", 3, 4.0).symbol(om)
+    mu = ops.coarse_operator(5, "sdirk", 3, 4.0, 16, 1, 2).symbol(om)
+    assert abs(lfa.rho(lam, mu, 16, 1) - 0.353) < 3e-3
+    assert lfa.rho(lam, lfa.corrected_sl_symbol(5, "sdirk", 4.0, 16, om, q=3), 16, 1) > 1.0
