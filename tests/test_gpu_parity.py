@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2209_06916_gb300 as pkg
 from oracle import coefficients as co
+from oracle import lfa
 from oracle import mgrit as omg
 from oracle import operators as oops
 from oracle import rng as orng
@@ -257,6 +258,9 @@ def test_full_size_vcycle_against_sequential_stepping():
             err = max(err, float(np.max(np.abs(got[n // m] - u))))
     print("full-size: iterations=%d rel err vs sequential=%.3e" % (st["iterations"], err / scale))
     assert err / scale < 1e-8
+    # the V-cycle converges as fast as the two-level LFA predicts (Sec. 6.3:
+    # little deterioration from two levels to V-cycles)
+    assert st["conv_factor"] < 1.2 * lfa.two_level_factor(3, "erk", c, m), st["conv_factor"]
 
 
 # ---------------------------------------------------------------------------
