@@ -244,7 +244,8 @@ def run_coarse_ops(args):
     Rediscretised vs corrected SL for SDIRK1+U1 and
     SDIRK3+U3 (FCF); F- vs FCF-relaxation with the corrected SL operator
     for ERK3+U3 at 0.85 c_max; the dispersive schemes of Sec. 6.4 (even p,
-    corrected SL operator, FCF, at most 30 iterations as in Sec. 6.3)."""
+    corrected SL operator, FCF, at most 30 iterations as in Sec. 6.3); the
+    approach to the CFL limit of ERK3+U3 and ERK5+U5 (Sec. 6.3.3)."""
     import torch
     import paper_2209_06916_gb300 as pkg
     from workloads import ic_sin4
@@ -293,6 +294,12 @@ def run_coarse_ops(args):
         for m in (2, 4):
             for c in (0.5, 1.0, 2.0):
                 case(pkg.SDIRK, p, c, m, pkg.SL_CORRECTED, 1, max_iter=30)
+    # convergence near the CFL limit (Sec. 6.3.3): ERK3+U3 and ERK5+U5, m = 4,
+    # over c / c_max (ERK5: c_max = 1.9399 of the stability polynomial that
+    # Table 1's error constant fixes)
+    for p, cm, fracs in ((3, 1.62589, (0.5, 0.7, 0.85, 0.95, 0.99)), (5, 1.9399, (0.3, 0.5, 0.6, 0.7, 0.8))):
+        for frac in fracs:
+            case(pkg.ERK, p, frac * cm, 4, pkg.SL_CORRECTED, 1, max_iter=30)
     line = {"metric": "two-level MGRIT convergence factor, measured vs LFA", "unit": "factor", "n_gpus": 1,
             "steps": args.steps, "higher_is_better": False, "data": "synthetic",
             "config": {"workload": "advection1d_coarse_operator_comparison", "nx": nx, "nt": nt, "levels": 2,

@@ -263,3 +263,23 @@ def test_lfa_factors_of_the_workloads():
     mu = ops.coarse_operator(5, "sdirk", 3, 4.0, 16, 1, 2).symbol(om)
     assert abs(lfa.rho(lam, mu, 16, 1) - 0.353) < 3e-3
     assert lfa.rho(lam, lfa.corrected_sl_symbol(5, "sdirk", 4.0, 16, om, q=3), 16, 1) > 1.0
+
+
+def test_convergence_degrades_near_the_cfl_limit():
+    """Sec. 6.3.3: for ERK3+U3 and ERK5+U5 the two-level factor (m = 4,
+    corrected operator) grows as c approaches c_max; near the limit the
+    worst mode is an oscillatory one (the mode whose |lambda| approaches one
+    sets the CFL limit), not a smooth one; for ERK5+U5 the growth starts
+    near 60% of c_max and the coarse operator fails (factor > 1) by 80%,
+    while ERK3+U3 is still at its best there."""
+    f3 = {f: lfa.two_level_factor(3, "erk", f * co.cfl_limit(3), 4, omit=10) for f in (0.7, 0.95, 0.99)}
+    assert f3[0.99] > 3 * f3[0.7] and f3[0.95] > 2 * f3[0.7]
+    om = lfa.omega_samples(2048, 10)
+    c = 0.99 * co.cfl_limit(3)
+    lam = ops.FineOperator(3, "erk", 3, c).symbol(om)
+    mu = lfa.corrected_sl_symbol(3, "erk", c, 4, om)
+    per_mode = np.abs(lam) ** 4 * np.abs(lam ** 4 - mu) / (1 - np.abs(mu))
+    assert abs(om[np.argmax(per_mode)]) > np.pi / 2
+    f5 = {f: lfa.two_level_factor(5, "erk", f * co.cfl_limit(5), 4, omit=10) for f in (0.3, 0.5, 0.6, 0.7, 0.8)}
+    assert abs(f5[0.5] - f5[0.3]) < 0.05 and f5[0.7] > f5[0.6] + 0.1 and f5[0.6] > f5[0.5]
+    assert f5[0.8] > 1.0 > lfa.two_level_factor(3, "erk", 0.8 * co.cfl_limit(3), 4, omit=10)
