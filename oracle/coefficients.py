@@ -392,34 +392,71 @@ def diff_taps(order, p_for_bias=None):
 # ----------------------------------------------------------------------------
 
 
+def level_factors(m, levels):
+    """Coarsening factors m_1 .. m_{levels-1} (m_l: fine steps of level l-1
+    per step of level l).  ``m`` is one factor for every level, or the list
+    of them (the paper's parallel runs coarsen by 16 once and by 4 below,
+    Sec. 6.3.2)."""
+    if np.isscalar(m):
+        return [int(m)] * (levels - 1)
+    ms = [int(x) for x in m]
+    if len(ms) != levels - 1:
+        raise ValueError("need one coarsening factor per coarse level")
+    return ms
+
+
+def level_steps(m, levels):
+    """Time step of level l in units of dt: m_1 m_2 .. m_l (l = 1..levels-1)."""
+    out, t = [], 1
+    for f in level_factors(m, levels):
+        t *= f
+        out.append(t)
+    return out
+
+
+def level_step(m, level):
+    """Time step of level ``level`` in units of dt: m^level for one factor,
+    else the product of the first ``level`` factors."""
+    if np.isscalar(m):
+        return int(m) ** level
+    t = 1
+    for f in list(m)[:level]:
+        t *= int(f)
+    return t
+
+
 def level_shifts(c, m, levels):
-    """(k_l, eps_l) of the SL step on level l = 1..levels-1 (step m^l dt, so
-    the departure offset is m^l c grid cells)."""
-    return [sl_shift(c * m ** l) for l in range(1, levels)]
+    """(k_l, eps_l) of the SL step on level l = 1..levels-1 (step
+    m_1 .. m_l dt, so the departure offset is m_1 .. m_l c grid cells)."""
+    return [sl_shift(c * t) for t in level_steps(m, levels)]
 
 
 def phi_levels(p, kind, c, m, levels):
-    """phi^{(m^l dt)}_{p+1} for l = 1..levels-1 (index 0 of the result is l=1).
+    """phi_{p+1} of level l = 1..levels-1 (index 0 of the result is l=1).
 
-    l = 1:  m [c e_FD + (-c)^{p+1} e_RK] + (-1)^{p+1} f_{p+1}(eps_1)
+    l = 1:  m_1 [c e_FD + (-c)^{p+1} e_RK] + (-1)^{p+1} f_{p+1}(eps_1)
             (Lemma 6.1, Eq. varphi-constant-MOL-SL)
-    l > 1:  (-1)^{p+1} [ -m f_{p+1}(eps_{l-1}) + f_{p+1}(eps_l) ] + m phi_{l-1}
-            (Sec. 6.2, the phi recursion below Eq. MOL-SL-corrected-multilevel).
+    l > 1:  (-1)^{p+1} [ -m_l f_{p+1}(eps_{l-1}) + f_{p+1}(eps_l) ] + m_l phi_{l-1}
+            (Sec. 6.2, the phi recursion below Eq. MOL-SL-corrected-multilevel,
+            written there for one factor m; with level factors m_l the same
+            argument -- level l matches m_l steps of level l-1 -- gives m_l in
+            place of m).
     q = p is assumed, as in the paper.
     """
     q = p
     efd = float(e_fd(p))
     erk = e_rk(kind, q)
     sgn = (-1) ** (p + 1)
+    ms = level_factors(m, levels)
     shifts = level_shifts(c, m, levels)
     out = []
     for idx, (_, eps) in enumerate(shifts):
         f_l = f_poly(p, eps)
         if idx == 0:
-            phi = m * (c * efd + (-c) ** (p + 1) * erk) + sgn * f_l
+            phi = ms[0] * (c * efd + (-c) ** (p + 1) * erk) + sgn * f_l
         else:
             f_prev = f_poly(p, shifts[idx - 1][1])
-            phi = sgn * (-m * f_prev + f_l) + m * out[-1]
+            phi = sgn * (-ms[idx] * f_prev + f_l) + ms[idx] * out[-1]
         out.append(phi)
     return out
 
@@ -439,16 +476,17 @@ def phi_levels_general(p, kind, q, c, m, levels):
     efd = float(e_fd(p))
     erk = e_rk(kind, q)
     sgn = (-1) ** (p + 1)
+    ms = level_factors(m, levels)
     shifts = level_shifts(c, m, levels)
     out = []
     for idx, (_, eps) in enumerate(shifts):
         f_l = f_poly(p, eps)
         if idx == 0:
-            fp = m * c * efd + sgn * f_l
-            fq = m * (-c) ** (q + 1) * erk
+            fp = ms[0] * c * efd + sgn * f_l
+            fq = ms[0] * (-c) ** (q + 1) * erk
         else:
             f_prev = f_poly(p, shifts[idx - 1][1])
-            fp = sgn * (-m * f_prev + f_l) + m * out[-1][0]
-            fq = m * out[-1][1]
+            fp = sgn * (-ms[idx] * f_prev + f_l) + ms[idx] * out[-1][0]
+            fq = ms[idx] * out[-1][1]
         out.append((fp, fq))
     return out

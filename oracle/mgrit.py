@@ -23,6 +23,7 @@ solve             Sec. 5.3 / 6.3 setup: random initial iterate except    converg
 """
 import numpy as np
 
+from . import coefficients as co
 from . import operators as ops
 from . import rng
 
@@ -74,7 +75,10 @@ class Hierarchy:
     the corrected operators approximately by GMRES (Sec. 6.3)."""
 
     def __init__(self, p, kind, q, c, m, levels, coarse=None, coarse_op="sl_corrected", gmres=None):
-        self.m, self.levels = m, levels
+        # ms[l]: fine steps of level l per step of level l+1 (one factor, or
+        # one per coarse level)
+        self.ms = co.level_factors(m, levels) if levels > 1 else []
+        self.m, self.levels = (self.ms[0] if self.ms else m), levels
         self.fine = ops.FineOperator(p, kind, q, c)
         self.ops = [self.fine]
         for l in range(1, levels):
@@ -97,7 +101,7 @@ def vcycle(h, level, u, g, nu):
     if level == h.levels - 1:
         u[:] = sequential(op, g)
         return
-    m = h.m
+    m = h.ms[level]
     f_relax(op, u, g, m)
     for _ in range(nu):
         c_relax(op, u, g, m)

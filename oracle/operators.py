@@ -226,7 +226,7 @@ def coarse_operator(p, kind, q, c, m, level, levels, gmres=None):
     """Level-``level`` (>= 1) corrected SL operator of a ``levels``-level
     hierarchy with uniform coarsening m (Eq. MOL-SL-corrected-multilevel and the Sec. 6.2 phi recursion);
     ``gmres`` = (rtol, maxit) solves its correction systems by GMRES."""
-    s = c * m ** level
+    s = c * co.level_step(m, level)
     if q == p:
         phi = co.phi_levels(p, kind, c, m, levels)[level - 1]
         return CoarseOperator(p, s, [(phi, p + 1)], gmres)
@@ -247,7 +247,7 @@ def direct_operator(p, kind, q, c, m, level, coarse_op):
                       R_q(-m^l c L_p) (Sec. 2.2 and the Sec. 1 footnote;
                       analysed in Sec. 5).
     """
-    s = c * m ** level
+    s = c * co.level_step(m, level)
     if coarse_op == "sl":
         return SLOperator(p, s)
     if coarse_op == "redisc":

@@ -229,6 +229,47 @@ def test_multilevel_phi_recursion_order():
     assert errs_wrong[1] > 4 * errs[1]
 
 
+@pytest.mark.parametrize("p,kind,c,ms", [(3, "erk", 0.85, (4, 2)), (3, "erk", 0.85, (2, 4)),
+                                         (3, "sdirk", 2.0, (4, 2)), (1, "erk", 0.85, (4, 2))])
+def test_multilevel_phi_recursion_with_level_factors(p, kind, c, ms):
+    """The Sec. 6.2 recursion with a factor per level (the paper's parallel
+    runs coarsen by 16, then by 4): the level-2 operator (step m_1 m_2 dt)
+    matches (level-1 operator)^{m_2} to O(h^{p+2}) with m_2 in the
+    recursion; the recursion taken with m_1 instead (one factor for all
+    levels) loses the order."""
+    m1, m2 = ms
+    errs, errs_wrong = [], []
+    for nx in [64, 128]:
+        x = mesh(nx)
+        u = _smooth(x)
+        psi1 = ops.coarse_operator(p, kind, p, c, list(ms), 1, 3)
+        assert psi1.sl.k + psi1.sl.eps == pytest.approx(c * m1)
+        ideal = u
+        for _ in range(m2):
+            ideal = psi1.apply(ideal)
+        psi2 = ops.coarse_operator(p, kind, p, c, list(ms), 2, 3)
+        assert psi2.sl.k + psi2.sl.eps == pytest.approx(c * m1 * m2)
+        errs.append(np.max(np.abs(ideal - psi2.apply(u))))
+        # the uniform recursion with m_1 at level 2, on the same step
+        shifts = co.level_shifts(c, list(ms), 3)
+        f1, f2 = co.f_poly(p, shifts[0][1]), co.f_poly(p, shifts[1][1])
+        phi1 = co.phi_levels(p, kind, c, list(ms), 3)[0]
+        phi_wrong = (-1) ** (p + 1) * (-m1 * f1 + f2) + m1 * phi1
+        psi_w = ops.CoarseOperator(p, c * m1 * m2, [(phi_wrong, p + 1)])
+        errs_wrong.append(np.max(np.abs(ideal - psi_w.apply(u))))
+    assert np.log2(errs[0] / errs[1]) > p + 1.6, np.log2(errs[0] / errs[1])
+    assert errs_wrong[1] > 4 * errs[1]
+
+
+def test_level_factors_reduce_to_uniform_coarsening():
+    """One factor for every level and the list of equal factors give the
+    same operators (the recursion is the paper's for uniform m)."""
+    a = co.phi_levels(3, "erk", 0.85, 4, 4)
+    b = co.phi_levels(3, "erk", 0.85, [4, 4, 4], 4)
+    assert a == b
+    assert co.level_shifts(1.3, 8, 3) == co.level_shifts(1.3, [8, 8], 3)
+
+
 # --------------------------------------------------------------------------
 # Operators: Fourier symbols, equivalences, conservation, solve convention
 # --------------------------------------------------------------------------

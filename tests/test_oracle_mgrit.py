@@ -283,3 +283,18 @@ def test_convergence_degrades_near_the_cfl_limit():
     f5 = {f: lfa.two_level_factor(5, "erk", f * co.cfl_limit(5), 4, omit=10) for f in (0.3, 0.5, 0.6, 0.7, 0.8)}
     assert abs(f5[0.5] - f5[0.3]) < 0.05 and f5[0.7] > f5[0.6] + 0.1 and f5[0.6] > f5[0.5]
     assert f5[0.8] > 1.0 > lfa.two_level_factor(3, "erk", 0.8 * co.cfl_limit(3), 4, omit=10)
+
+
+def test_vcycle_with_level_factors_converges_to_sequential_stepping():
+    """A V-cycle coarsening by 4 and then by 2 (and by 2, then 4) converges
+    to sequential stepping; the coarse levels step m_1 m_2 .. m_l dt."""
+    nx, nt = 64, 64
+    u0 = ic_sin4(nx)
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = mgrit.sequential(ops.FineOperator(3, "erk", 3, 0.85), g)
+    for ms in ([4, 2], [2, 4], [2, 2, 4]):
+        h = mgrit.Hierarchy(3, "erk", 3, 0.85, ms, len(ms) + 1)
+        res = mgrit.solve(h, u0, nt, tol=1e-12, max_iter=40)
+        assert res["converged"], ms
+        assert np.max(np.abs(res["u"] - seq)) < 1e-10
