@@ -73,7 +73,7 @@ extern "C" {
 /* ---- parameters -------------------------------------------------------- */
 typedef struct mgrit_params {
   int64_t nx;       /* grid points, 32 <= nx, nx % 8 == 0                       */
-  int64_t nt;       /* time steps; nt % m^(levels-1) == 0                       */
+  int64_t nt;       /* time steps; nt % (m m_coarse^(levels-2)) == 0            */
   double cfl;       /* c = alpha dt / h, absolute (not a fraction of c_max)     */
   double alpha;     /* wave speed > 0 (only c enters the discrete operators)    */
   int order_p;      /* upwind order p in 1..5: odd p dissipative (Sec. 6.3),    */
@@ -106,6 +106,10 @@ typedef struct mgrit_params {
                     /* (Sec. 6.1, Sec. 6.3); SL_CORRECTED only, n_x <= 32768    */
   int gmres_maxit;  /* 1..32; 0: 10 for p = 1, 20 otherwise (Sec. 6.3)         */
   double gmres_rtol;/* in (0, 1); 0: 1e-2 (Sec. 6.3)                           */
+  int m_coarse;     /* coarsening factor below level 1 (level l >= 1 takes      */
+                    /* m_coarse steps per step of level l+1); 0: m.  The        */
+                    /* paper's parallel runs use m = 16, m_coarse = 4           */
+                    /* (Sec. 6.3.2); level l steps m m_coarse^(l-1) dt          */
 } mgrit_params;
 
 /* ---- statistics -------------------------------------------------------- */
@@ -279,7 +283,8 @@ int mgrit_output_all(mgrit_handle* h, double* d_all);
  * mgrit_level_info -- host-side derived data of a level (no GPU work):
  * out[0] = steps N_l, out[1] = SL shift k_l, out[2] = eps_l, out[3] = phi_l
  * (phi_p for q != p), out[4] = phi_q (0 when q = p), out[5] = composite
- * stencil taps (level 0, ERK), out[6] = chunk length of the in-block solves
+ * stencil taps (level 0, ERK) or the level's time step in units of dt
+ * (coarse levels: m m_coarse^(l-1)), out[6] = chunk length of the in-block solves
  * (level 0, ERK: outputs per thread of the composite-stencil kernel, and
  * out[4] = 1 when its persistent form runs),
  * out[7] = CTAs per vector (thread-block cluster size) of the level's step

@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
         ("nu", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
         ("precision", ctypes.c_int), ("seed", ctypes.c_uint64), ("inner_cycles", ctypes.c_int),
         ("coarse_op", ctypes.c_int), ("coarse_solve", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-        ("gmres_rtol", ctypes.c_double),
+        ("gmres_rtol", ctypes.c_double), ("m_coarse", ctypes.c_int),
     ]
 
 
@@ -162,11 +162,11 @@ def _check(code, what):
 
 def make_params(nx, nt, cfl, p, kind=ERK, q=0, m=4, levels=2, nu=1, tol=1e-10, max_iter=30,
                 precision=FP64, seed=0, alpha=1.0, inner_cycles=0, coarse_op=SL_CORRECTED,
-                coarse_solve=DIRECT, gmres_maxit=0, gmres_rtol=0.0):
+                coarse_solve=DIRECT, gmres_maxit=0, gmres_rtol=0.0, m_coarse=0):
     return Params(nx=nx, nt=nt, cfl=cfl, alpha=alpha, order_p=p, rk_kind=kind, rk_order_q=q, m=m,
                   levels=levels, nu=nu, tol=tol, max_iter=max_iter, precision=precision, seed=seed,
                   inner_cycles=inner_cycles, coarse_op=coarse_op, coarse_solve=coarse_solve,
-                  gmres_maxit=gmres_maxit, gmres_rtol=gmres_rtol)
+                  gmres_maxit=gmres_maxit, gmres_rtol=gmres_rtol, m_coarse=m_coarse)
 
 
 class Solver:

@@ -37,7 +37,9 @@ namespace {
 
 struct LevelData {
   int64_t N = 0;  // steps on the level
-  int64_t K = 0;  // CF-intervals (N / m); 0 on the coarsest level
+  int64_t K = 0;  // CF-intervals (N / m_l); 0 on the coarsest level
+  int m = 0;              // m_l: steps of this level per step of the next (its interval length)
+  long long tstep = 1;    // this level's time step in units of dt (m_0 m_1 .. m_{l-1})
   double* uC[2] = {nullptr, nullptr};
   int cur = 0;
   double* g = nullptr;
@@ -385,9 +387,12 @@ static void phi_recursion(const mgrit_params& P, int L, std::vector<double>* php
   phq->assign(L, 0.0);
   ks->assign(L, 0);
   es->assign(L, 0.0);
+  // level l steps m_1 .. m_l dt (m_1 = m, m_l = m_coarse below); the
+  // recursion of Sec. 6.2 with the factor m_l of the level in place of m
   double mpow = 1.0;
   for (int l = 1; l < L; ++l) {
-    mpow *= P.m;
+    const double ml = (l == 1 || P.m_coarse <= 0) ? P.m : P.m_coarse;
+    mpow *= ml;
     long long k;
     double eps;
     sl_shift(c * mpow, &k, &eps);
@@ -396,12 +401,12 @@ static void phi_recursion(const mgrit_params& P, int L, std::vector<double>* php
     double f = f_poly(p, eps);
     double cq = std::pow(-c, q + 1) * erk;
     if (l == 1) {
-      (*php)[l] = P.m * c * efd + sgn * f;
-      (*phq)[l] = P.m * cq;
+      (*php)[l] = ml * c * efd + sgn * f;
+      (*phq)[l] = ml * cq;
     } else {
       double fprev = f_poly(p, (*es)[l - 1]);
-      (*php)[l] = sgn * (-P.m * fprev + f) + P.m * (*php)[l - 1];
-      (*phq)[l] = P.m * (*phq)[l - 1];
+      (*php)[l] = sgn * (-ml * fprev + f) + ml * (*php)[l - 1];
+      (*phq)[l] = ml * (*phq)[l - 1];
     }
   }
   if (q == p) {  // single correction constant phi = phi_p + phi_q (Eq. varphi-constant-MOL-SL)
@@ -467,7 +472,7 @@ static int coarse_with_geom(mgrit_handle* h, int l, const GeomC& g) {
   }
   cp.c.Mt = Lv.Mt_dev[0];
   cp.a.Mt = Lv.Mt_dev[1];
-  cp.m = h->m;
+  cp.m = Lv.m;
   if (is_mixed(P.precision)) {
     auto geom = [&](auto& q) {
       std::memset((void*)&q, 0, sizeof(q));
@@ -555,7 +560,7 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
 static int build_redisc(mgrit_handle* h, int l, bool buffers, std::string* why) {
   LevelData& Lv = h->lev[l];
   const bool coarsest = (l == h->L - 1);
-  const double cl = h->prm.cfl * std::pow((double)h->m, (double)l);
+  const double cl = h->prm.cfl * (double)Lv.tstep;
   for (int d = 0; d < 2; ++d) {
     dev_free(h, Lv.rd_Mt[d]);
     Lv.rd_Mt[d] = nullptr;
@@ -1230,7 +1235,7 @@ static int tune_coarse(mgrit_handle* h, int l) {
   if (cand.size() <= 1 || geom_forced(&fc, &fp)) return MGRIT_OK;
   char keyb[160];
   std::snprintf(keyb, sizeof(keyb), "coarse:n=%lld:K=%lld:N=%lld:m=%d:p=%d:b=%d:s=%d:gm=%d", (long long)h->nx,
-                (long long)Lv.K, (long long)(coarsest ? Lv.N : 0), h->m, h->prm.order_p, f32 ? 4 : 8,
+                (long long)Lv.K, (long long)(coarsest ? Lv.N : 0), Lv.m, h->prm.order_p, f32 ? 4 : 8,
                 f32 ? (Lv.solve64 ? 8 : 4) : 8, gm ? h->prm.gmres_maxit : 0);
   const std::string key(keyb);
   Geom cg;
@@ -1287,7 +1292,7 @@ static int tune_coarse(mgrit_handle* h, int l) {
         cp.sub = nullptr;
         cp.partial = nullptr;
         cp.g = gg;
-        cp.nsteps = h->m - 1;
+        cp.nsteps = Lv.m - 1;
         cp.K = Kt;
       };
       if (!f32) {
@@ -1509,7 +1514,7 @@ static int redisc_launch(mgrit_handle* h, int l, const SdirkParams<T>& base, int
   sp.sub = sub;
   sp.rhs = nullptr;
   sp.g = g;
-  sp.m = h->m;
+  sp.m = h->lev[l].m;
   sp.nsteps = nsteps;
   sp.K = K;
   sp.traj = nullptr;
@@ -1577,22 +1582,22 @@ static int level_pre_and_residual(mgrit_handle* h, int l, bool zero_guess) {
   if (nu == 0) {
     if (zero_guess) {
       CUDA_TRY(cudaMemsetAsync(Lv.uC[Lv.cur], 0, sizeof(double) * (Lv.K + 1) * h->nx, h->st));
-      rc = coarse_launch(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].g, nullptr, nullptr, h->m, Lv.K, Lv.g);
+      rc = coarse_launch(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].g, nullptr, nullptr, Lv.m, Lv.K, Lv.g);
     } else {
       rc = coarse_launch(h, l, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[l + 1].g, Lv.uC[Lv.cur],
-                         nullptr, h->m, Lv.K, Lv.g);
+                         nullptr, Lv.m, Lv.K, Lv.g);
     }
     return rc;
   }
   for (int s = 0; s < nu; ++s) {
     bool zs = zero_guess && s == 0;
     rc = coarse_launch(h, l, kModeCF, zs ? 1 : 0, zs ? nullptr : Lv.uC[Lv.cur], Lv.uC[1 - Lv.cur],
-                       nullptr, nullptr, h->m, Lv.K, Lv.g);
+                       nullptr, nullptr, Lv.m, Lv.K, Lv.g);
     if (rc) return rc;
     Lv.cur = 1 - Lv.cur;
   }
   rc = coarse_launch(h, l, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[l + 1].g, Lv.uC[Lv.cur], nullptr,
-                     h->m, Lv.K, Lv.g);
+                     Lv.m, Lv.K, Lv.g);
   return rc;
 }
 
@@ -1610,7 +1615,7 @@ static int coarse_correct(mgrit_handle* h, int l) {
     if (rc) return rc;
     rc = coarse_correct(h, l + 1);
     if (rc) return rc;
-    rc = coarse_launch(h, l, kModeFOUT, 0, Lv.uC[Lv.cur], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.g);
+    rc = coarse_launch(h, l, kModeFOUT, 0, Lv.uC[Lv.cur], nullptr, nullptr, parent, Lv.m - 1, Lv.K, Lv.g);
   }
   if (rc) return rc;
   // the kernel left this level's values at all its points in its RHS rows:
@@ -1792,22 +1797,22 @@ static int coarse_correct_f(mgrit_handle* h, int l) {
   const size_t rowf = sizeof(float) * (size_t)h->nx;
   if (nu == 0) {
     CUDA_TRY(cudaMemsetAsync(Lv.uCf[Lv.curf], 0, rowf * (Lv.K + 1), h->st));
-    rc = coarse_launch_f(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].gf, nullptr, nullptr, h->m, Lv.K, Lv.gf);
+    rc = coarse_launch_f(h, l, kModeFRES, 1, nullptr, h->lev[l + 1].gf, nullptr, nullptr, Lv.m, Lv.K, Lv.gf);
   } else {
     for (int s = 0; s < nu; ++s) {
       bool zs = s == 0;
       rc = coarse_launch_f(h, l, kModeCF, zs ? 1 : 0, zs ? nullptr : Lv.uCf[Lv.curf], Lv.uCf[1 - Lv.curf],
-                           nullptr, nullptr, h->m, Lv.K, Lv.gf);
+                           nullptr, nullptr, Lv.m, Lv.K, Lv.gf);
       if (rc) return rc;
       Lv.curf = 1 - Lv.curf;
     }
-    rc = coarse_launch_f(h, l, kModeFRES, 0, Lv.uCf[Lv.curf], h->lev[l + 1].gf, Lv.uCf[Lv.curf], nullptr, h->m,
+    rc = coarse_launch_f(h, l, kModeFRES, 0, Lv.uCf[Lv.curf], h->lev[l + 1].gf, Lv.uCf[Lv.curf], nullptr, Lv.m,
                          Lv.K, Lv.gf);
   }
   if (rc) return rc;
   rc = coarse_correct_f(h, l + 1);
   if (rc) return rc;
-  rc = coarse_launch_f(h, l, kModeFOUT, 0, Lv.uCf[Lv.curf], nullptr, nullptr, parent, h->m - 1, Lv.K, Lv.gf);
+  rc = coarse_launch_f(h, l, kModeFOUT, 0, Lv.uCf[Lv.curf], nullptr, nullptr, parent, Lv.m - 1, Lv.K, Lv.gf);
   if (rc) return rc;
   launch_convert(kAddF2F, nullptr, parent + h->nx, Lv.N * h->nx, h->st, nullptr, Lv.gf + h->nx);
   ++h->launches;
@@ -2241,13 +2246,17 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   if (P.rk_kind == MGRIT_SDIRK && P.rk_order_q != P.order_p &&
       (P.order_p % 2 == 0 || P.rk_order_q > P.order_p || P.rk_order_q % 2 == 0))
     return MGRIT_ERR_UNSUPPORTED;
+  if (P.m_coarse == 0) P.m_coarse = P.m;
+  if (P.m_coarse < 2) return MGRIT_ERR_INVALID_ARG;
   if (P.nt % P.m) return MGRIT_ERR_INVALID_ARG;
+  // m from level 0 to 1, m_coarse below
+  auto factor = [&](int l) { return l == 0 ? P.m : P.m_coarse; };
   int L = P.levels;
   if (L == 0) {  // coarsen until fewer than two time points would result
     L = 1;
     int64_t N = P.nt;
-    while (N % P.m == 0 && N / P.m >= 2) {
-      N /= P.m;
+    while (N % factor(L - 1) == 0 && N / factor(L - 1) >= 2) {
+      N /= factor(L - 1);
       ++L;
     }
     if (L < 2) L = 2;
@@ -2256,8 +2265,8 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   {
     int64_t N = P.nt;
     for (int l = 1; l < L; ++l) {
-      if (N % P.m) return MGRIT_ERR_INVALID_ARG;
-      N /= P.m;
+      if (N % factor(l - 1)) return MGRIT_ERR_INVALID_ARG;
+      N /= factor(l - 1);
     }
     if (N < 1) return MGRIT_ERR_INVALID_ARG;
   }
@@ -2282,10 +2291,14 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
   cudaGetDevice(&h->device);
   h->lev.resize(L);
   int64_t N = P.nt;
+  long long tstep = 1;
   for (int l = 0; l < L; ++l) {
     h->lev[l].N = N;
-    h->lev[l].K = (l < L - 1) ? N / P.m : 0;
-    N /= P.m;
+    h->lev[l].m = factor(l);
+    h->lev[l].tstep = tstep;
+    h->lev[l].K = (l < L - 1) ? N / factor(l) : 0;
+    N /= factor(l);
+    tstep *= factor(l);
   }
   // level-0 operators
   int rc = MGRIT_OK;
@@ -2431,7 +2444,7 @@ int mgrit_relax(mgrit_handle* h, int level, int nu) {
       rc = l0_cf(h);
     } else {
       LevelData& Lv = h->lev[level];
-      rc = coarse_launch(h, level, kModeCF, 0, Lv.uC[Lv.cur], Lv.uC[1 - Lv.cur], nullptr, nullptr, h->m,
+      rc = coarse_launch(h, level, kModeCF, 0, Lv.uC[Lv.cur], Lv.uC[1 - Lv.cur], nullptr, nullptr, Lv.m,
                          Lv.K, Lv.g);
       Lv.cur = 1 - Lv.cur;
     }
@@ -2448,7 +2461,7 @@ int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
   } else {
     LevelData& Lv = h->lev[level];
     rc = coarse_launch(h, level, kModeFRES, 0, Lv.uC[Lv.cur], h->lev[level + 1].g, Lv.uC[Lv.cur],
-                       nullptr, h->m, Lv.K, Lv.g);
+                       nullptr, Lv.m, Lv.K, Lv.g);
     if (!rc) {
       launch_reduce_sum(h->partials, Lv.K * (Lv.redisc ? Lv.rd->csize : Lv.cp.csize), h->dnorm, h->st);
       ++h->launches;
@@ -2822,6 +2835,7 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   out[2] = Lv.eps;
   out[3] = Lv.phi;
   out[4] = Lv.phi_q;
+  out[5] = (double)Lv.tstep;
   out[6] = (double)(Lv.redisc ? Lv.rd->P : Lv.cp.P);
   out[7] = (double)(Lv.redisc ? Lv.rd->csize : Lv.cp.csize);
   return MGRIT_OK;

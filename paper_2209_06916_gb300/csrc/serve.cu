@@ -22,11 +22,14 @@
 
 namespace {
 
+// coarsening factor from level l to level l+1
+int factor_of(const mgrit_params& p, int64_t l) { return (l == 0 || p.m_coarse <= 0) ? p.m : p.m_coarse; }
+
 int64_t levels_of(const mgrit_params& p) {
   if (p.levels > 0) return p.levels;
   int64_t L = 1, N = p.nt;
-  while (N % p.m == 0 && N / p.m >= 2) {
-    N /= p.m;
+  while (N % factor_of(p, L - 1) == 0 && N / factor_of(p, L - 1) >= 2) {
+    N /= factor_of(p, L - 1);
     ++L;
   }
   return std::max<int64_t>(L, 2);
@@ -43,11 +46,12 @@ extern "C" int64_t mgrit_estimate_bytes(const mgrit_params* p) {
   int64_t rows = 0, N = p->nt;
   const int64_t gm_it = p->coarse_solve == MGRIT_SOLVE_GMRES ? (p->gmres_maxit > 0 ? p->gmres_maxit : 20) : -1;
   for (int64_t l = 0; l < L; ++l) {
-    int64_t K = (l < L - 1) ? N / p->m : 0;
+    const int64_t f = factor_of(*p, l);
+    int64_t K = (l < L - 1) ? N / f : 0;
     if (l < L - 1) rows += 2 * (K + 1);  // C-point double buffer
     if (l >= 1) rows += N + 1;           // RHS
     if (l >= 1 && gm_it > 0) rows += std::max<int64_t>(K, 1) * (gm_it + 1);  // GMRES Krylov basis
-    N /= p->m;
+    N /= f;
   }
   int64_t bytes = rows * p->nx * 8;
   if (p->precision == MGRIT_MIXED || p->precision == MGRIT_MIXED_FAST) bytes += rows * p->nx * 4 + (N + 2) * p->nx * 8;

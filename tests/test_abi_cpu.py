@@ -114,3 +114,18 @@ def test_estimate_counts_the_gmres_basis(lib):
     g = pkg.make_params(256, 1024, 0.85, 3, m=4, levels=3, coarse_solve=pkg.GMRES, gmres_maxit=20)
     extra = lib.mgrit_estimate_bytes(ctypes.byref(g)) - lib.mgrit_estimate_bytes(ctypes.byref(d))
     assert extra == (64 + 1) * 21 * 256 * 8  # level 1: 64 intervals; level 2 (coarsest): one vector
+
+
+def test_level_factor_validated_and_estimated(lib):
+    """m_coarse: 0 means m; below 2 is rejected; n_t must divide by
+    m m_coarse^(levels-2); the admission estimate follows the level sizes."""
+    h = ctypes.c_void_p()
+    bad = pkg.make_params(64, 128, 0.85, 3, m=4, levels=3, m_coarse=1)
+    assert lib.mgrit_setup(ctypes.byref(bad), None, ctypes.byref(h)) == -1
+    bad = pkg.make_params(64, 96, 0.85, 3, m=4, levels=3, m_coarse=16)   # 96 = 4 * 24, 24 % 16 != 0
+    assert lib.mgrit_setup(ctypes.byref(bad), None, ctypes.byref(h)) == -1
+    lib.mgrit_estimate_bytes.restype = ctypes.c_int64
+    a = pkg.make_params(256, 1024, 0.85, 3, m=16, levels=3, m_coarse=4)
+    # levels: 1024 steps (K 64), 64 steps (K 16), 16 steps (coarsest)
+    rows = 2 * 65 + (65 + 2 * 17) + 17
+    assert lib.mgrit_estimate_bytes(ctypes.byref(a)) == rows * 256 * 8 + (4 << 20)

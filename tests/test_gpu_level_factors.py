@@ -1,0 +1,106 @@
+"""A coarsening factor per level on the GPU (the paper's parallel runs
+coarsen by m = 16 and then by 4, Sec. 6.3.2): the coarse operators of
+every level against the oracle's (step m_1 .. m_l dt, the Sec. 6.2
+recursion with the level's factor), and solves iteration for iteration."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2209_06916_gb300 as pkg
+from oracle import mgrit as omg
+from oracle import operators as oops
+from workloads import ic_fourier, ic_sin4
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _solver(nx, nt, c, p, m, mc, levels, kind=pkg.ERK, q=0, precision=pkg.FP64, coarse_op=pkg.SL_CORRECTED,
+            seed=0):
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, m_coarse=mc, levels=levels, nu=1, tol=1e-10,
+                          max_iter=40, seed=seed, precision=precision, coarse_op=coarse_op)
+    return pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("kind,p,q,c,m,mc,levels,nx", [
+    (pkg.ERK, 3, 3, 1.38, 16, 4, 4, 1024),
+    (pkg.ERK, 1, 1, 0.85, 4, 2, 4, 256),
+    (pkg.SDIRK, 3, 3, 5.0, 16, 4, 3, 512),
+    (pkg.SDIRK, 5, 3, 4.0, 4, 8, 3, 2048),
+])
+def test_level_operators_match_oracle(kind, p, q, c, m, mc, levels, nx):
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    ms = [m] + [mc] * (levels - 2)
+    nt = m * mc ** (levels - 2) * 2
+    s = _solver(nx, nt, c, p, m, mc, levels, kind, q)
+    x = np.random.default_rng(4).standard_normal((5, nx))
+    y = torch.empty((5, nx), dtype=torch.float64, device="cuda")
+    step = 1
+    for lev in range(1, levels):
+        step *= ms[lev - 1]
+        assert s.level_info(lev)[5] == step
+        s.coarse_apply(lev, dev(x), y, 5)
+        want = oops.coarse_operator(p, kname, q, c, ms, lev, levels).apply(x)
+        torch.cuda.synchronize()
+        assert _rel(y.cpu().numpy(), want) < 1e-12, lev
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p,q,c,m,mc,levels,nx,nt,coarse_op", [
+    (pkg.ERK, 3, 3, 1.38, 16, 4, 3, 64, 512, pkg.SL_CORRECTED),
+    (pkg.ERK, 3, 3, 1.38, 4, 8, 3, 128, 256, pkg.SL_CORRECTED),
+    (pkg.SDIRK, 3, 3, 5.0, 16, 4, 3, 64, 512, pkg.SL_CORRECTED),
+    (pkg.SDIRK, 1, 1, 1.0, 8, 2, 4, 64, 256, pkg.REDISC),
+])
+def test_solve_matches_oracle(kind, p, q, c, m, mc, levels, nx, nt, coarse_op):
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    ms = [m] + [mc] * (levels - 2)
+    u0 = ic_sin4(nx)
+    s = _solver(nx, nt, c, p, m, mc, levels, kind, q, coarse_op=coarse_op, seed=3)
+    out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+    st = s.solve(dev(u0), out, allow_unconverged=True)
+    name = {pkg.SL_CORRECTED: "sl_corrected", pkg.REDISC: "redisc"}[coarse_op]
+    ref = omg.solve(omg.Hierarchy(p, kname, q, c, ms, levels, coarse_op=name), u0, nt, tol=1e-10, max_iter=40,
+                    seed=3)
+    assert st["iterations"] == ref["iterations"]
+    hist, href = np.array(st["history"]), np.array(ref["history"])
+    big = href > 1e-8 * href[0]
+    assert np.max(np.abs(hist[big] - href[big]) / href[big]) < 1e-6
+    if ref["converged"]:
+        torch.cuda.synchronize()
+        assert np.max(np.abs(out.cpu().numpy() - ref["u"][::m])) < 1e-10 * max(1.0, np.max(np.abs(u0)))
+    s.close()
+
+
+def test_paper_parallel_configuration_small():
+    """m = 16, m_coarse = 4, coarsening until fewer than two time points
+    (levels = 0): 4096 steps give levels of 4096, 256, 64, 16, 4 steps;
+    MIXED converges to sequential stepping."""
+    nx, nt = 256, 4096
+    s = _solver(nx, nt, 1.38, 3, 16, 4, 0, precision=pkg.MIXED, seed=1)
+    u0 = ic_fourier(nx, seed=5)
+    out = torch.empty((nt // 16 + 1, nx), dtype=torch.float64, device="cuda")
+    st = s.solve(dev(u0), out)
+    assert st["converged"] and st["levels"] == 5
+    assert [s.level_info(l)[0] for l in range(5)] == [4096, 256, 64, 16, 4]
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = omg.sequential(oops.FineOperator(3, "erk", 3, 1.38), g)[::16]
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy(), seq) < 1e-9
+    s.close()
