@@ -104,3 +104,59 @@ def test_paper_parallel_configuration_small():
     torch.cuda.synchronize()
     assert _rel(out.cpu().numpy(), seq) < 1e-9
     s.close()
+
+
+def test_level_factors_with_gmres_correction_solves():
+    """GMRES correction solves on levels of steps 16 dt and 64 dt: the same
+    iterate and iteration counts as the oracle's GMRES on those levels."""
+    from oracle import gmres as ogm
+    nx, m, mc, levels = 512, 16, 4, 3
+    prm = pkg.make_params(nx, m * mc * 2, 1.38, 3, m=m, m_coarse=mc, levels=levels,
+                          coarse_solve=pkg.GMRES)
+    s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+    x = np.random.default_rng(8).standard_normal((4, nx))
+    y = torch.empty((4, nx), dtype=torch.float64, device="cuda")
+    for lev in (1, 2):
+        s.coarse_apply(lev, dev(x), y, 4)
+        op = oops.coarse_operator(3, "erk", 3, 1.38, [m, mc], lev, levels, gmres=(1e-2, ogm.default_maxit(3)))
+        want = op.apply(x)
+        torch.cuda.synchronize()
+        assert _rel(y.cpu().numpy(), want) < 1e-12
+        assert s.gmres_stats(lev)[0] == sum(op.gmres_its)
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p,c", [(pkg.ERK, 4, 0.3), (pkg.SDIRK, 2, 1.0)])
+def test_level_factors_with_even_p(kind, p, c):
+    kname = "erk" if kind == pkg.ERK else "sdirk"
+    nx, m, mc, levels = 1024, 8, 2, 4
+    s = _solver(nx, m * mc * mc * 2, c, p, m, mc, levels, kind, p)
+    x = np.random.default_rng(p).standard_normal((3, nx))
+    y = torch.empty((3, nx), dtype=torch.float64, device="cuda")
+    for lev in range(1, levels):
+        s.coarse_apply(lev, dev(x), y, 3)
+        want = oops.coarse_operator(p, kname, p, c, [m, mc, mc], lev, levels).apply(x)
+        torch.cuda.synchronize()
+        assert _rel(y.cpu().numpy(), want) < 1e-12, lev
+    s.close()
+
+
+def test_batch_with_level_factors_equals_standalone():
+    """A batch whose solves coarsen differently (uniform and 16 then 4,
+    different depths) gives every solve's standalone result bit for bit."""
+    from workloads import ic_sin4_noise
+    cases = [(256, 1024, 16, 4, pkg.FP64), (512, 2048, 8, 2, pkg.MIXED), (256, 512, 4, 4, pkg.FP64),
+             (1024, 4096, 16, 4, pkg.MIXED)]
+    prms = [pkg.make_params(nx, nt, 1.2, 3, m=m, m_coarse=mc, levels=0, tol=1e-10, max_iter=60, seed=i,
+                            precision=prec) for i, (nx, nt, m, mc, prec) in enumerate(cases)]
+    u0s = [ic_sin4_noise(nx, seed=i) for i, (nx, *_rest) in enumerate(cases)]
+    b = pkg.Batch(prms, nstreams=2)
+    stats = b.solve(u0s, allow_unconverged=True)
+    for i, (prm, u0) in enumerate(zip(prms, u0s)):
+        s = pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
+        want = np.zeros((prm.nt // prm.m + 1, prm.nx))
+        st = s.solve(u0, want, allow_unconverged=True)
+        s.close()
+        assert st["converged"] and stats[i]["iterations"] == st["iterations"]
+        assert np.array_equal(b.get(i), want), i
+    b.close()
