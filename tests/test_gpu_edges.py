@@ -153,3 +153,21 @@ def test_even_p_degenerate_hierarchies(kind, p, c, nx, nt, m, levels, nu):
     ref = omg.solve(omg.Hierarchy(p, kname, p, c, m, levels), u0, nt, nu=nu, tol=1e-10, max_iter=60, seed=4)
     assert st["converged"] and st["iterations"] == ref["iterations"]
     assert np.max(np.abs(out.cpu().numpy() - ref["u"][::m])) < 1e-10 * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("kind,p,q,c,nx,nt,m,levels,precision", [
+    (pkg.ERK, 3, 3, 1.38, 4096, 16384, 8, 4, pkg.FP64),
+    (pkg.SDIRK, 5, 3, 4.0, 16384, 65536, 16, 5, pkg.MIXED),
+])
+def test_full_size_mass_conservation(kind, p, q, c, nx, nt, m, levels, precision):
+    """Every step and coarse operator here preserves sum_i u_i (upwind
+    stencil, SL weights and correction rows sum to the identity's), so every
+    C-point row of the converged full-size solution carries the initial mass
+    to rounding and to the stop tolerance."""
+    u0 = ic_fourier(nx, seed=4) + 0.5
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, tol=1e-10, max_iter=40,
+                          seed=0, precision=precision)
+    out, st = _solve(prm, u0)
+    assert st["converged"]
+    mass = out.sum(dim=1).cpu().numpy()
+    assert np.max(np.abs(mass - u0.sum())) < 1e-9 * np.abs(u0).sum()
