@@ -26,9 +26,9 @@ diff_taps(p)                 Eq. (Dp+1_def); s = 2 symmetric for    moments: (p+
                              left bias for even p (Sec. 6.4)
 phi_levels(...)              Lemma 6.1 Eq. (varphi-constant-MOL-SL) Lemma 6.1 O(h^{p+2}) order test
                              and the Sec. 6.2 multilevel recursion
-phi_levels_general(...)      builder reading for q != p: Lemma 4.2   parity unpinned against the paper
-                             carries both D^{(p+1)} and D^{(q+1)}     (only an O(h) order test)
-                             terms; App. B steps applied to each
+phi_levels_general(...)      builder reading for q != p: Lemma 4.2   order tests: the dominant term's
+                             carries both D^{(p+1)} and D^{(q+1)}     constant gains an order in h on
+                             terms; App. B steps applied to each      level 1; level 2 vs (level 1)^m
 
 ERK5: the tableau is not printed.  The stability polynomial is taken as the
 degree-5 Taylor polynomial plus beta_6 z^6 with beta_6 = 1/1280, which is what
@@ -462,7 +462,8 @@ def phi_levels(p, kind, c, m, levels):
 
 
 def phi_levels_general(p, kind, q, c, m, levels):
-    """Builder reading for q != p (not in the paper; parity unpinned).
+    """Builder reading for q != p (the paper derives the correction for q = p
+    only; this extends it).
 
     Lemma 4.2 gives the one-step error -[c e_FD D^{(p+1)} + (-c)^{q+1} e_RK
     D^{(q+1)}] u.  Repeating the App. B argument keeps the two terms apart:
@@ -472,6 +473,13 @@ def phi_levels_general(p, kind, q, c, m, levels):
       phi_q(l=1) = m (-c)^{q+1} e_RK,   phi_q(l>1) = m phi_q(l-1).
     For q = p the two constants add up to phi_levels(...).
     Returns a list of (phi_p, phi_q) pairs.
+
+    Pinned by truncation order (tests/test_oracle_coefficients.py): on level
+    1 the constant of the dominant error term gains one order in h over a
+    zero or sign-flipped constant (phi_q for q < p, phi_p for q > p); on
+    level 2 the U5 + SDIRK3 operator matches (level 1)^m to O(h^7), while a
+    phi_q recursion without its factor m leaves O(h^4) and a phi_p one
+    without m leaves O(h^6).
     """
     efd = float(e_fd(p))
     erk = e_rk(kind, q)

@@ -261,6 +261,99 @@ def test_multilevel_phi_recursion_with_level_factors(p, kind, c, ms):
     assert errs_wrong[1] > 4 * errs[1]
 
 
+# --------------------------------------------------------------------------
+# Two-term correction for q != p (phi_levels_general): order pins.
+# Lemma 4.2 splits the one-step error into an FD term c e_FD D^{(p+1)} of
+# size O(h^{p+1}) and an RK term (-c)^{q+1} e_RK D^{(q+1)} of size
+# O(h^{q+1}); the corrected operator with both constants must cancel the
+# larger of the two, so against Phi^m it gains one order over a zero or
+# sign-flipped constant of that term.  On level 2 the recursion must also
+# reproduce (level-1 operator)^m to the order of the SL remainder.
+# --------------------------------------------------------------------------
+
+
+def _two_term_level1(p, q, c, m, nx, fp_mul=1.0, fq_mul=1.0):
+    x = mesh(nx)
+    Phi = ops.FineOperator(p, "sdirk", q, c)
+    u = _smooth(x)
+    ideal = u
+    for _ in range(m):
+        ideal = Phi.apply(ideal)
+    fp, fq = co.phi_levels_general(p, "sdirk", q, c, m, 2)[0]
+    Psi = ops.CoarseOperator(p, c * m, [(fp_mul * fp, p + 1), (fq_mul * fq, q + 1)])
+    return np.max(np.abs(ideal - Psi.apply(u)))
+
+
+@pytest.mark.parametrize("p,q,c,m", [(5, 3, 1.0, 4), (5, 3, 2.0, 4), (3, 1, 1.0, 4), (5, 1, 1.0, 4)])
+def test_two_term_correction_rk_constant_order(p, q, c, m):
+    """q < p (the 16384 x 65536 SDIRK3+U5 workload's pairing): the RK term
+    O(h^{q+1}) dominates; with phi_q the mismatch with Phi^m falls as
+    h^{q+2}, with phi_q = 0 or -phi_q only as h^{q+1}."""
+    nxs = (64, 128, 256)
+    good = [_two_term_level1(p, q, c, m, n) for n in nxs]
+    assert np.log2(good[1] / good[2]) > q + 1.7, good
+    for mul in (0.0, -1.0):
+        bad = [_two_term_level1(p, q, c, m, n, fq_mul=mul) for n in nxs]
+        assert np.log2(bad[1] / bad[2]) < q + 1.2, bad
+        assert bad[2] > 8 * good[2]
+
+
+@pytest.mark.parametrize("p,q,c,m", [(1, 3, 0.8, 4), (3, 5, 0.8, 4), (1, 3, 1.3, 4)])
+def test_two_term_correction_fd_constant_order(p, q, c, m):
+    """q > p: the FD term O(h^{p+1}) dominates, which pins the level-1
+    phi_p of the two-term form (it falls below the RK remainder when
+    q < p): phi_p gains an order over 0 and -phi_p."""
+    nxs = (64, 128, 256)
+    good = [_two_term_level1(p, q, c, m, n) for n in nxs]
+    assert np.log2(good[1] / good[2]) > p + 1.7, good
+    for mul in (0.0, -1.0):
+        bad = [_two_term_level1(p, q, c, m, n, fp_mul=mul) for n in nxs]
+        assert np.log2(bad[1] / bad[2]) < p + 1.2, bad
+        assert bad[2] > 8 * good[2]
+
+
+@pytest.mark.parametrize("c,m", [(1.0, 4), (0.7, 4), (1.0, 2)])
+def test_two_term_correction_level2_recursion_order(c, m):
+    """U5 + SDIRK3 on level 2 (step m^2 dt) against (level-1 operator)^m:
+    with the recursions phi_q(2) = m phi_q(1) and the Sec. 6.2 recursion
+    for phi_p the mismatch falls at least as h^7; phi_q(2) = phi_q(1), 0 or
+    -phi_q(2) leave O(h^4), and a phi_p recursion without its factor m
+    (or phi_p(2) = 0) leaves O(h^6)."""
+    p, q = 5, 3
+    nxs = (64, 128, 256)
+
+    def mismatch(nx, mode):
+        x = mesh(nx)
+        u = _smooth(x)
+        psi1 = ops.coarse_operator(p, "sdirk", q, c, m, 1, 3)
+        ideal = u
+        for _ in range(m):
+            ideal = psi1.apply(ideal)
+        (fp1, fq1), (fp2, fq2) = co.phi_levels_general(p, "sdirk", q, c, m, 3)
+        if mode == "q_nom":
+            fq2 = fq1
+        elif mode == "q_zero":
+            fq2 = 0.0
+        elif mode == "q_flip":
+            fq2 = -fq2
+        elif mode == "p_nom":
+            shifts = co.level_shifts(c, m, 3)
+            f1, f2 = co.f_poly(p, shifts[0][1]), co.f_poly(p, shifts[1][1])
+            fp2 = (-1) ** (p + 1) * (-m * f1 + f2) + fp1
+        elif mode == "p_zero":
+            fp2 = 0.0
+        psi2 = ops.CoarseOperator(p, c * m * m, [(fp2, p + 1), (fq2, q + 1)])
+        return np.max(np.abs(ideal - psi2.apply(u)))
+
+    good = [mismatch(n, "ok") for n in nxs]
+    assert np.log2(good[1] / good[2]) > 6.7, good
+    for mode, order in (("q_nom", q + 1), ("q_zero", q + 1), ("q_flip", q + 1), ("p_nom", p + 1),
+                        ("p_zero", p + 1)):
+        bad = [mismatch(n, mode) for n in nxs]
+        assert np.log2(bad[1] / bad[2]) < order + 0.3, (mode, bad)
+        assert bad[2] > 100 * good[2], mode
+
+
 def test_level_factors_reduce_to_uniform_coarsening():
     """One factor for every level and the list of equal factors give the
     same operators (the recursion is the paper's for uniform m)."""
