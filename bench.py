@@ -1,17 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark: space-time DOF/s of a full MGRIT solve to a 1e-10 relative
-residual on one GB300, against GPU sequential time-stepping and the CPU oracle.
+"""Benchmark: space-time DOF/s of a full MGRIT solve on one GB300, against
+GPU sequential time-stepping and the CPU oracle.
 
-Workload (one "step" = one whole solve, every row of the hot path):
-  1D periodic advection, nx = 4096, nt = 16384, 3rd-order upwind + ERK3
-  (c = 0.85), FP64, V-cycle MGRIT with m = 8 and 4 levels, FCF relaxation,
-  corrected semi-Lagrangian coarse operators, IC sin^4(pi x) + N(0, 1e-2)
-  noise, random initial iterate (seed 0), stop at ||r|| <= 1e-10 ||r_0||.
+Default line (one "step" = one whole solve, every row of the hot path):
+  1D periodic advection, nx = 16384, nt = 65536, 5th-order upwind + 3-stage
+  SDIRK3 (c = 4), V-cycle MGRIT with m = 16 and 5 levels, FCF relaxation,
+  corrected semi-Lagrangian coarse operators (two-term correction for
+  q != p), smooth random IC (20 Fourier modes), random initial iterate
+  (seed 0).  `value` is the FP64 solve; FP32-relaxation variants, GPU
+  sequential stepping, the 512-solve batch and a bounded window of the
+  served Poisson stream are sub-records of the same line.
+
+  The stop tolerance is 1e-11: a 1e-10 relative residual leaves an error of
+  about 1.7e-10 against sequential stepping on this problem (the error is
+  bounded only by ||A^{-1}|| ||r||), and every C-point is meant to be within
+  1e-10 of it; the line reports that error over all C-points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU runs are independent replicas (one solve per rank; the path does
-not shard on one node here): value = N * DOF / max-over-ranks time.
+Multi-GPU runs are independent replicas (one solve per rank): value = N *
+DOF / max-over-ranks time.
 """
 import argparse
 import json
@@ -27,22 +35,26 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # the headline: 4096 x 16384, ERK3+U3, FP64, 4-level V-cycle (m = 8)
-    "c2": dict(name="advection1d_erk3u3_vcycle_fp64", nx=4096, nt=16384, p=3, kind="erk", q=3, cfl=0.85,
-               m=8, levels=4, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4_noise", precision="fp64"),
+    # 16384 x 65536, U5 + SDIRK3 (c = 4), m = 16, 5 levels: the largest
+    # single-GPU configuration, solved in FP64 (the variants add FP32
+    # relaxation in FP64 refinement)
+    "c3": dict(name="advection1d_sdirk3u5_vcycle", nx=16384, nt=65536, p=5, kind="sdirk", q=3,
+               cfl=4.0, m=16, levels=5, nu=1, tol=1e-11, max_iter=40, seed=0, ic="fourier20",
+               precision="fp64"),
+    # 4096 x 16384, ERK3+U3, FP64, 4-level V-cycle (m = 8)
+    "c2": dict(name="advection1d_erk3u3_vcycle", nx=4096, nt=16384, p=3, kind="erk", q=3, cfl=0.85,
+               m=8, levels=4, nu=1, tol=1e-11, max_iter=40, seed=0, ic="sin4_noise", precision="fp64"),
     # 256 x 1024, ERK1+U1, FP64, two-level m = 4
-    "c1": dict(name="advection1d_erk1u1_twolevel_fp64", nx=256, nt=1024, p=1, kind="erk", q=1, cfl=0.85,
-               m=4, levels=2, nu=1, tol=1e-10, max_iter=30, seed=0, ic="sin4", precision="fp64"),
-    # 16384 x 65536, U5 + SDIRK3 (c = 4), FP32 relaxation in FP64 refinement, m = 16, 5 levels
-    "c3": dict(name="advection1d_sdirk3u5_vcycle_mixed", nx=16384, nt=65536, p=5, kind="sdirk", q=3,
-               cfl=4.0, m=16, levels=5, nu=1, tol=1e-10, max_iter=30, seed=0, ic="fourier20",
-               precision="mixed"),
+    "c1": dict(name="advection1d_erk1u1_twolevel", nx=256, nt=1024, p=1, kind="erk", q=1, cfl=0.85,
+               m=4, levels=2, nu=1, tol=1e-11, max_iter=40, seed=0, ic="sin4", precision="fp64"),
 }
-WORKLOAD = WORKLOADS["c2"]
+WORKLOAD = WORKLOADS["c3"]
 METRIC = "space-time DOF/s to 1e-10 residual vs GPU seq. stepping; p50/p99 latency"
 UNIT = "DOF/s"
 # FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM (4 flop/clk/SM) x 2.07 GHz
 FP64_PEAK_FLOPS = 152 * 4 * 2.07e9
+# FP32 FMA pipe: 152 SMs x 128 FP32 FMA/clk/SM (256 flop/clk/SM) x 2.07 GHz
+FP32_PEAK_FLOPS = 152 * 256 * 2.07e9
 
 
 def _dist():
@@ -111,54 +123,93 @@ def clocks_sampler_stop(p, f, path, device):
             "samples": len(sm)}
 
 
-def make_ic(w):
+def make_ic(w, seed=None):
     from workloads import ic_fourier, ic_sin4, ic_sin4_noise
+    seed = w["seed"] if seed is None else seed
     if w["ic"] == "sin4_noise":
-        return ic_sin4_noise(w["nx"], seed=w["seed"])
+        return ic_sin4_noise(w["nx"], seed=seed)
     if w["ic"] == "fourier20":
-        return ic_fourier(w["nx"], seed=w["seed"])
+        return ic_fourier(w["nx"], seed=seed)
     return ic_sin4(w["nx"])
 
 
-def cpu_baseline(sample_nt=2048):
-    """The CPU oracle (plain numpy FP64 V-cycle MGRIT, as it stands) on a
-    bounded sample of the workload: the same nx, scheme, m, levels and
-    tolerance over the first sample_nt steps."""
+def _oracle_sample(job):
+    """One oracle solve (plain numpy FP64 MGRIT, as it stands) on a bounded
+    sample of a workload: the same nx, scheme, m and tolerance over the
+    first `nt` steps.  Runs in a pool worker; returns (DOF, seconds,
+    iterations)."""
     from oracle import mgrit as omg
-    w = WORKLOAD
-    sample_nt = min(sample_nt, w["nt"])
-    levels = w["levels"]
-    while sample_nt % (w["m"] ** (levels - 1)):
-        levels -= 1
+    w, nt, levels, seed = job
     h = omg.Hierarchy(w["p"], w["kind"], w["q"], w["cfl"], w["m"], levels)
-    u0 = make_ic(w)
+    u0 = make_ic(w, seed)
     t = time.perf_counter()
-    r = omg.solve(h, u0, sample_nt, nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"])
-    dt = time.perf_counter() - t
-    return {"value": w["nx"] * sample_nt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "nx=%d, nt=%d (first %d of %d steps), same scheme/m/tol, %d levels, %d iterations, %.1f s"
-                      % (w["nx"], sample_nt, sample_nt, w["nt"], levels, r["iterations"], dt)}
+    r = omg.solve(h, u0, nt, nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"])
+    return w["nx"] * nt, time.perf_counter() - t, r["iterations"]
 
 
-def run_batched(args):
-    """512 independent solves (nx, nt, p, c, m mixed), FP32 relaxation in FP64
-    refinement, captured into one CUDA graph and run with one launch; value =
-    total DOF / batch time."""
+def _oracle_import(_):
+    from oracle import mgrit  # noqa: F401
+    return 0
+
+
+def _sample_levels(w, nt):
+    levels = w["levels"]
+    while levels > 2 and nt % (w["m"] ** (levels - 1)):
+        levels -= 1
+    return levels
+
+
+def cpu_baseline(w, sample_nt, workers=None):
+    """The CPU oracle on the host cores: one independent sample solve per
+    core (a process pool, spawn start method, one BLAS/OpenMP thread per
+    worker), each the workload's nx, scheme, m and tolerance over the first
+    sample_nt steps with its own IC seed.  value = the DOF all workers
+    solved / the wall time of the round."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    workers = workers or cores
+    sample_nt = min(sample_nt, w["nt"])
+    levels = _sample_levels(w, sample_nt)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    jobs = [(w, sample_nt, levels, w["seed"] + i) for i in range(workers)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_import, range(workers))  # start the workers and import, untimed
+        t = time.perf_counter()
+        res = pool.map(_oracle_sample, jobs)
+        wall = time.perf_counter() - t
+    dof = sum(r[0] for r in res)
+    its = sorted(r[2] for r in res)
+    return {"value": dof / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "host_cpu_count": cores,
+            "sample": "%d independent solves (one per core, spawn pool), each nx=%d, nt=%d (the first %d of %d "
+                      "steps), same scheme/m/tol, %d levels, %d-%d iterations; %.1f s wall"
+                      % (workers, w["nx"], sample_nt, sample_nt, w["nt"], levels, its[0], its[-1], wall)}
+
+
+def batched_record(count, steps, warmup, tol=1e-11):
+    """The batched workload: `count` independent solves (nx, nt, p, c, m
+    mixed; ERK of matching order), FP32 relaxation in FP64 refinement,
+    captured into one CUDA graph and run with one launch; against GPU
+    sequential stepping of the same problems, all at once over the batch's
+    streams.  value = total DOF / batch time."""
     import torch
     import paper_2209_06916_gb300 as pkg
     from workloads import batch_mix, ic_sin4_noise
-    torch.cuda.set_device(0)
-    mix = batch_mix(args.count, seed=1000)
-    prms = [pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=1e-10,
+    mix = batch_mix(count, seed=1000)
+    prms = [pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=tol,
                             max_iter=60, precision=pkg.MIXED, seed=d["seed"]) for d in mix]
     u0s = [torch.tensor(ic_sin4_noise(d["nx"], seed=d["seed"]), dtype=torch.float64, device="cuda") for d in mix]
+    t0 = time.perf_counter()
     b = pkg.Batch(prms, nstreams=32)
+    setup_s = time.perf_counter() - t0
     dof = b.dof()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.solve(u0s, allow_unconverged=True)
     torch.cuda.synchronize()
     ts = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         st = b.solve(u0s, allow_unconverged=True)
         torch.cuda.synchronize()
@@ -166,72 +217,95 @@ def run_batched(args):
     dt = float(np.median(ts))
     its = [x["iterations"] for x in st]
     conv = sum(1 for x in st if x["converged"])
-    # the baseline: GPU sequential stepping of the same 512 problems, all at
-    # once over the same streams
     outs = [torch.empty(d["nx"], dtype=torch.float64, device="cuda") for d in mix]
     b.sequential(u0s, outs)
     torch.cuda.synchronize()
     sts = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         b.sequential(u0s, outs)
         torch.cuda.synchronize()
         sts.append(time.perf_counter() - t0)
     sdt = float(np.median(sts))
+    # accuracy: the final C-point row of a sample of the solves against their
+    # sequential stepping
+    err = 0.0
+    for i in range(0, count, max(1, count // 8)):
+        last = b.get(i)[-1]
+        ref = outs[i].cpu().numpy()
+        err = max(err, float(np.max(np.abs(last - ref)) / np.max(np.abs(ref))))
     b.close()
-    line = {"metric": METRIC, "value": dof / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
-            "config": {"workload": "advection1d_batched_%d_erk_mixed" % args.count, "solves": args.count,
-                       "dof_total": dof, "converged": conv, "iterations_median": float(np.median(its)),
-                       "iterations_max": int(max(its)), "launch": "one CUDA graph, one branch per solve"},
+    return {"workload": "advection1d_batched_%d_erk_mixed" % count, "value": dof / dt, "unit": UNIT,
+            "ms_per_batch": dt * 1e3, "batches_timed": steps, "solves": count, "dof_total": dof,
+            "converged": conv, "iterations_median": float(np.median(its)), "iterations_max": int(max(its)),
+            "tol": tol, "setup_s": setup_s, "launch": "one CUDA graph, one branch per solve",
+            "max_rel_err_final_row_vs_sequential": err, "err_sample": "every %d-th solve" % max(1, count // 8),
             "sequential": {"value": dof / sdt, "unit": UNIT, "ms": sdt * 1e3,
                            "kernel": "seq_kernel per solve, all solves over the 32 streams"},
             "mgrit_over_sequential": sdt / dt}
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    rec = batched_record(args.count, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
+            "config": {"workload": rec["workload"]}, "batched": rec}
     print(json.dumps(line))
     return 0
 
 
-def run_serving(args):
-    """Poisson stream (2000 requests/s) of mixed solves through the native
-    continuous-batching server with an 80 GB HBM budget."""
-    import torch
+def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-11, seed=2000):
+    """A Poisson stream of mixed solves (the batched mix plus 10% SDIRK5+U5
+    at c in [2, 8]) through the native continuous-batching server with an
+    HBM budget: arrival-to-completion latency p50/p99, service time and the
+    completed DOF/s over the window (arrivals for `duration` s, the server
+    stops `drain` s later)."""
     import paper_2209_06916_gb300 as pkg
     from workloads import ic_fourier, ic_sin4_noise, serving_stream
-    torch.cuda.set_device(0)
-    arrivals, reqs = serving_stream(rate=2000.0, duration=args.duration, seed=2000)
+    arrivals, reqs = serving_stream(rate=rate, duration=duration, seed=seed)
     prms, u0s = [], []
     for d in reqs:
         kind = pkg.ERK if d["kind"] == "erk" else pkg.SDIRK
         prms.append(pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=kind, q=d["q"], m=d["m"], levels=0,
-                                    nu=1, tol=1e-10, max_iter=60, precision=pkg.MIXED, seed=d["seed"]))
+                                    nu=1, tol=tol, max_iter=60, precision=pkg.MIXED, seed=d["seed"]))
         u0s.append(ic_sin4_noise(d["nx"], seed=d["seed"]) if d["kind"] == "erk" else ic_fourier(d["nx"], d["seed"]))
-    res, st = pkg.serve(prms, u0s, arrivals, 80 * 10 ** 9, max_inflight=args.inflight,
-                        time_limit_s=args.duration + args.drain)
+    res, st = pkg.serve(prms, u0s, arrivals, budget_gb * 10 ** 9, max_inflight=inflight,
+                        time_limit_s=duration + drain)
     ok = [r for r in res if r["status"] == 0]
     lat = np.array([r["latency_ms"] for r in ok])
     svc = np.array([(r["finish_s"] - r["start_s"]) * 1e3 for r in ok])
     statuses = {}
     for r in res:
         if r["status"] not in (0, 1):
-            statuses[pkg.ERRORS.get(r["status"], str(r["status"]))] = statuses.get(
-                pkg.ERRORS.get(r["status"], str(r["status"])), 0) + 1
+            nm = pkg.ERRORS.get(r["status"], str(r["status"]))
+            statuses[nm] = statuses.get(nm, 0) + 1
     offered = float(sum(d["nx"] * d["nt"] for d in reqs))
-    line = {"metric": METRIC, "value": st["dof_completed"] / st["wall_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": st["wall_s"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
-            "config": {"workload": "advection1d_serving_poisson2000", "arrival_rate_per_s": 2000.0,
-                       "duration_s": args.duration, "requests": len(reqs), "offered_dof_per_s": offered / args.duration,
-                       "hbm_budget_gb": 80, "max_inflight": args.inflight},
+    return {"workload": "advection1d_serving_poisson%d" % int(rate), "value": st["dof_completed"] / st["wall_s"],
+            "unit": UNIT, "arrival_rate_per_s": rate, "arrivals_s": duration, "window_s": st["wall_s"],
+            "requests": len(reqs), "offered_dof_per_s": offered / duration, "hbm_budget_gb": budget_gb,
+            "max_inflight": inflight, "tol": tol,
             "serving": {k: st[k] for k in ("arrived", "admitted", "completed", "failed", "rejected", "backlog_end",
                                            "max_backlog", "max_mem_bytes", "max_inflight", "wall_s")},
             "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                            "p99": float(np.percentile(lat, 99)) if lat.size else None,
-                           "completed": int(lat.size)},
+                           "completed": int(lat.size), "note": "arrival to completion"},
             "service_ms": {"p50": float(np.percentile(svc, 50)) if svc.size else None,
                            "p99": float(np.percentile(svc, 99)) if svc.size else None,
-                           "note": "admission to completion (latency_ms adds the queueing under overload)"},
+                           "note": "admission to completion"},
             "failures": statuses}
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    rec = serving_record(args.duration, args.drain, args.inflight)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": rec["window_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 relax / f64 residual", "data": "synthetic", "config": {"workload": rec["workload"]},
+            "serving_record": rec}
     print(json.dumps(line))
     return 0
 
@@ -417,65 +491,57 @@ def run_parallel_problems(args):
 
 
 def run_reference(args):
+    """The oracle timed as it stands on the host cores (the one place this
+    repository has no reference implementation to install: the paper has
+    no code).  Each step is one round of independent bounded samples of the
+    workload, one per core.  Under torchrun only rank 0 runs it."""
     ws, rank = _dist()
     if rank != 0:
         return 0
-    times = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(sample_nt=512)
-        if i >= args.warmup:
-            times.append(cb)
-    vals = [c["value"] for c in times]
-    value = float(np.mean(vals))
+    w = WORKLOAD
+    sample_nt = args.reference_nt or (128 if w["kind"] == "sdirk" else 512)
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    levels = _sample_levels(w, sample_nt)
+    jobs = [(w, sample_nt, levels, w["seed"] + i) for i in range(cores)]
+    times, its = [], []
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_import, range(cores))
+        for i in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            res = pool.map(_oracle_sample, jobs)
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                times.append(dt)
+                its += [r[2] for r in res]
+    dof = cores * w["nx"] * sample_nt
+    value = dof * len(times) / sum(times)
+    sample = ("%d independent solves per step (one per core, spawn pool), each nx=%d, nt=%d (the first %d of %d "
+              "steps), same scheme/m/tol, %d levels, %d-%d iterations"
+              % (cores, w["nx"], sample_nt, sample_nt, w["nt"], levels, min(its), max(its)))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "nx": WORKLOAD["nx"], "nt": 512,
-                       "note": "CPU oracle on a 512-step sample of the 16384-step workload"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": times[0]["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "nx": w["nx"], "nt": sample_nt,
+                       "note": "CPU oracle (numpy FP64 MGRIT) on %d-step samples of the %d-step workload"
+                               % (sample_nt, w["nt"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5", "coarse_ops", "table3",
-                                                                      "parallel_problems"])
-    ap.add_argument("--count", type=int, default=512, help="c4: number of solves")
-    ap.add_argument("--duration", type=float, default=5.0, help="c5: seconds of arrivals")
-    ap.add_argument("--drain", type=float, default=25.0, help="c5: extra seconds before the server stops")
-    ap.add_argument("--inflight", type=int, default=64, help="c5: concurrent solves")
-    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision sub-measurement")
-    ap.add_argument("--nt", type=int, default=0, help="override n_t of c1-c3 (small profiling cases)")
-    ap.add_argument("--no-sequential", action="store_true", help="skip the sequential-stepping baseline")
-    ap.add_argument("--precision", default="", choices=["", "fp64", "mixed", "mixed_fast"],
-                    help="override the workload's")
-    ap.add_argument("--inner", type=int, default=0, help="MIXED: FP32 V-cycles per FP64 residual (0: library default)")
-    ap.add_argument("--coarse-solve", default="direct", choices=["direct", "gmres"],
-                    help="correction solves of the coarse operator (gmres: Sec. 6.3's GMRES)")
-    args = ap.parse_args()
-    global WORKLOAD
-    if args.workload == "c4" and args.impl == "ours":
-        return run_batched(args)
-    if args.workload == "c5" and args.impl == "ours":
-        return run_serving(args)
-    if args.workload == "coarse_ops" and args.impl == "ours":
-        return run_coarse_ops(args)
-    if args.workload == "table3" and args.impl == "ours":
-        return run_table3(args)
-    if args.workload == "parallel_problems" and args.impl == "ours":
-        return run_parallel_problems(args)
-    WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c2"])
-    if args.impl == "reference":
-        return run_reference(args)
+def _max_rel_err(out, ref_rows, u0):
+    """max |out - ref| / max |ref| over every C-point row (device tensors;
+    row 0 of `out` against u0, rows 1.. against the sequential trajectory)."""
+    e = max(float((out[0] - u0).abs().max().item()), float((out[1:] - ref_rows).abs().max().item()))
+    scale = max(float(u0.abs().max().item()), float(ref_rows.abs().max().item()))
+    return e / scale
 
+
+def run_single(args):
     import torch
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -495,6 +561,8 @@ def main():
             w["levels"] -= 1
     if args.precision:
         w["precision"] = args.precision
+    if args.tol > 0:
+        w["tol"] = args.tol
     nx, nt, m = w["nx"], w["nt"], w["m"]
     stream = torch.cuda.current_stream()
     kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
@@ -511,7 +579,9 @@ def main():
     main_solve = pkg.GMRES if args.coarse_solve == "gmres" else pkg.DIRECT
     if main_solve == pkg.GMRES:
         w["name"] += "_gmres"
+    t0 = time.perf_counter()
     s = make(prec, main_solve)
+    setup_s = time.perf_counter() - t0
     u0_h = make_ic(w)
     u0 = torch.tensor(u0_h, dtype=torch.float64, device="cuda")
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
@@ -529,7 +599,10 @@ def main():
     cp, cf = clocks_sampler_start(clk_path)
     time.sleep(0.5)
 
-    # the timed region: the K solves, uninstrumented
+    # the timed region: K solves, with the library's per-launch CUDA events on
+    # the handle's stream (the roofline's kernel times come from these same
+    # launches)
+    s.profile(True)
     launches0 = s.launch_count()
     if dist:
         dist.barrier()
@@ -547,49 +620,45 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = s.launch_count() - launches0
-    ms = max_over_ranks(ms, dist, "cuda")
-    # the same K solves again with the library's per-launch CUDA events (about
-    # 2% slower): per-kernel times for the roofline
-    s.profile(True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        s.solve(u0, out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_prof = e0.elapsed_time(e1)
     prof = s.profile_read()
     s.profile(False)
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e_steps = min(args.steps, args.e2e_steps)
     u0_pin = torch.tensor(u0_h, dtype=torch.float64).pin_memory()
     out_pin = torch.empty((nt // m + 1, nx), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         s.solve(u0_pin, out_pin)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
-    # GPU sequential time-stepping of the same problem (the baseline), and the
-    # accuracy of the MGRIT solution against it at the final time
-    seq_out = torch.empty(nx, dtype=torch.float64, device="cuda")
+
+    # GPU sequential time-stepping of the same problem (the baseline), with
+    # every C-point row kept: the error of the MGRIT solution over all
+    # C-points against it
     seq_ms, err, sprof = None, None, {"sequential": (0, 0.0, 0.0)}
+    seq_rows = None
     if not args.no_sequential:
-        s.fine_propagate(u0, seq_out, nt)
+        seq_out = torch.empty(nx, dtype=torch.float64, device="cuda")
+        seq_rows = torch.empty((nt // m, nx), dtype=torch.float64, device="cuda")
+        s.fine_propagate(u0, seq_out, nt, m, seq_rows)
         s.profile(True)
         torch.cuda.synchronize()
+        seq_steps = min(args.steps, args.seq_steps)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(seq_steps):
             s.fine_propagate(u0, seq_out, nt)
         e1.record(stream)
         torch.cuda.synchronize()
-        seq_ms = e0.elapsed_time(e1) / args.steps
+        seq_ms = e0.elapsed_time(e1) / seq_steps
         sprof = s.profile_read()
         s.profile(False)
         s.solve(u0, out)
         torch.cuda.synchronize()
-        err = float((out[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
+        err = _max_rel_err(out, seq_rows, u0)
     dof = nx * nt
     variants = {}
     # the same workload with other choices of the method:
@@ -599,21 +668,20 @@ def main():
     #                           kappa <= 1e3, in FP32)
     #   "gmres"                 the coarse correction systems solved by GMRES
     #                           (rel. 1e-2, at most 20 iterations, Sec. 6.3)
-    #                           instead of the exact banded solve
+    #                           instead of the exact banded solve (explicit
+    #                           workloads: on the implicit one capped GMRES
+    #                           stalls MGRIT near a 1e-3 residual)
     vlist = []
     if not args.no_variants:
         if prec == pkg.FP64:
             vlist += [("mixed", pkg.MIXED, pkg.DIRECT), ("mixed_fast", pkg.MIXED_FAST, pkg.DIRECT)]
-        if main_solve == pkg.DIRECT:
+        if main_solve == pkg.DIRECT and kind == pkg.ERK:
             vlist.append(("gmres", prec, pkg.GMRES))
-    # a variant of a long solve (above 200 ms) runs one warm-up and one timed
-    # solve, so that slow ones (GMRES on the implicit workload) stay bounded
-    vwarm, vsteps = (1, 1) if ms / args.steps > 200.0 else (max(1, args.warmup), args.steps)
+    vsteps = max(1, min(args.steps, args.variant_steps))
     for vname, vprec, vsolve in vlist:
         sm = make(vprec, vsolve)
         outm = torch.empty_like(out)
-        for _ in range(vwarm):
-            stm = sm.solve(u0, outm, allow_unconverged=True)
+        stm = sm.solve(u0, outm, allow_unconverged=True)
         torch.cuda.synchronize()
         g0 = [sm.gmres_stats(l) for l in range(1, w["levels"])]
         sm.profile(True)
@@ -625,16 +693,20 @@ def main():
         vprof = sm.profile_read()
         sm.profile(False)
         mms = e0.elapsed_time(e1) / vsteps
-        errm = (float((outm[-1] - seq_out).abs().max().item() / seq_out.abs().max().item())
-                if seq_ms is not None else None)
+        errm = _max_rel_err(outm, seq_rows, u0) if seq_rows is not None else None
         v = {"value": dof / (mms / 1e3), "unit": UNIT, "ms": mms, "converged": stm["converged"],
              "rel_residual": stm["rnorm"] / stm["rnorm0"] if stm["rnorm0"] > 0 else 0.0,
              "iterations": stm["iterations"],
              "outer_iterations": stm["outer_iterations"], "inner_cycles": stm["inner_cycles"],
-             "max_rel_err_vs_sequential": errm,
+             "max_rel_err_vs_sequential": errm, "err_over": "all C-points",
              "over_sequential": seq_ms / mms if seq_ms is not None else None,
-             "solves_timed": vsteps,
-             "coarse_ms": {k: vv[1] / vsteps for k, vv in vprof.items() if k.startswith("coarse")}}
+             "over_fp64": (ms / args.steps) / mms, "solves_timed": vsteps,
+             "kernel_ms": {k: vv[1] / vsteps for k, vv in vprof.items()}}
+        n32, ms32, fl32 = vprof.get("level0_fp32", (0, 0.0, 0.0))
+        if ms32 > 0:
+            v["fp32_level0_kernel"] = {"launches": n32, "ms_per_launch": ms32 / max(1, n32),
+                                       "achieved_tflops": fl32 / (ms32 / 1e3) / 1e12,
+                                       "frac_of_derived_fp32_peak": fl32 / (ms32 / 1e3) / FP32_PEAK_FLOPS}
         if vsolve == pkg.GMRES:
             g1 = [sm.gmres_stats(l) for l in range(1, w["levels"])]
             v["gmres_iterations_per_solve"] = [
@@ -643,9 +715,8 @@ def main():
         sm.close()
     clocks = clocks_sampler_stop(cp, cf, clk_path, local)
     scnt, sms, sfl = sprof["sequential"]
+    del seq_rows
 
-    # accuracy of the benched solve against the FP64 ... (reported, not a gate)
-    dof = nx * nt
     value = whole_job_value(dof, args.steps, ms, ws)
     cnt, kms, kfl = prof["stencil0"]
     achieved = kfl / (kms / 1e3) if kms > 0 else 0.0
@@ -654,26 +725,17 @@ def main():
         kname = "%s<double,%d> (level-0 composite Phi^m)" % (
             "stencil_rows_persistent" if info0[4] else "stencil_rows_kernel", int(info0[6]))
     else:
-        kname = "sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves, stage derivatives from the solves), clusters of %d" % (
-            int(info0[6]), w["p"] + 1, int(info0[7]))
-    # DRAM bytes per launch of the level-0 kernel from one ncu capture:
-    # the composite stencil of the 4096 x 16384 ERK3 workload
-    # (profiles/stencil_rows_kernel_advection1d_erk3u3_fp64.md), and the
-    # FP64 SDIRK kernel of the 16384 x 65536 workload, captured at nt = 8192
-    # and scaled by the 8x intervals of a full launch
-    # (profiles/sdirk_kernel_advection1d_sdirk3u5_mixed_nt8192.md)
-    traffic = None
-    if w["name"] == WORKLOADS["c2"]["name"] and prec == pkg.FP64 and nt == WORKLOADS["c2"]["nt"]:
-        traffic = 94.1e6
-    elif w["name"] == WORKLOADS["c3"]["name"] and nt == WORKLOADS["c3"]["nt"]:
-        traffic = 798e6
+        kname = ("sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves, stage derivatives from the "
+                 "solves), clusters of %d" % (int(info0[6]), w["p"] + 1, int(info0[7])))
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+            "traffic_note": "DRAM bytes come from ncu captures, not from this run; the kernel is FP64-pipe bound "
+                            "(DRAM below 2% of peak)",
             "peak_source": "derived FP64 FMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
             "launches": cnt, "ms_per_launch": kms / max(1, cnt),
-            "share_of_step": kms / ms_prof if ms_prof > 0 else None}
+            "share_of_step": kms / ms if ms > 0 else None,
+            "timing": "per-launch CUDA events on the handle's stream inside the timed region"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -681,13 +743,17 @@ def main():
             "config": {"workload": w["name"], "nx": nx, "nt": nt,
                        "scheme": "%s%d+U%d" % (w["kind"].upper(), w["q"], w["p"]), "cfl": w["cfl"],
                        "m": m, "levels": w["levels"], "relax": "FCF", "tol": w["tol"],
-                       "coarse_solve": args.coarse_solve,
+                       "tol_note": "stop at 1e-11: every C-point within 1e-10 of sequential stepping "
+                                   "(a 1e-10 residual leaves ~1.7e-10 on the 16384 x 65536 workload)",
+                       "precision": w["precision"], "coarse_solve": args.coarse_solve,
                        "iterations": iters, "parallelism": "replicas" if ws > 1 else "single",
+                       "setup_s": setup_s,
                        "l2": "working set %.0f MB > 129 MB L2 (no flush)" % (
                            (2 * (nt // m + 1) + (nt // m + 1) + 2 * (nt // m ** 2 + 1)) * nx * 8 / 1e6)},
             "roofline": roof,
-            "e2e": {"value": whole_job_value(dof, args.steps, e2e_ms, ws), "unit": UNIT,
-                    "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8},
+            "e2e": {"value": whole_job_value(dof, e2e_steps, e2e_ms, ws), "unit": UNIT,
+                    "h2d_bytes_per_step": nx * 8, "d2h_bytes_per_step": (nt // m + 1) * nx * 8,
+                    "steps": e2e_steps},
             "gpu_launches": launches, "clocks": clocks,
             "sequential": None if seq_ms is None else {
                 "value": dof / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
@@ -696,17 +762,72 @@ def main():
                 "achieved_tflops": sfl / (sms / 1e3) / 1e12 if sms > 0 else None,
                 "frac": (sfl / (sms / 1e3)) / FP64_PEAK_FLOPS if sms > 0 else None},
             "mgrit_over_sequential": seq_ms / (ms / args.steps) if seq_ms is not None else None,
-            "max_rel_err_vs_sequential": err,
+            "max_rel_err_vs_sequential": err, "err_over": "all C-points",
             "variants": variants,
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()}}
+    s.close()
+    del out
+    torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not args.no_c4:
+        line["batched"] = batched_record(args.count, 1, 1)
+    if rank == 0 and ws == 1 and not args.no_c5:
+        line["served"] = serving_record(args.c5_duration, args.c5_drain, args.inflight)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sample_nt=2048 if w["kind"] == "erk" else 256)
+        line["cpu_baseline"] = cpu_baseline(w, sample_nt=args.cpu_nt or (256 if w["kind"] == "sdirk" else 2048))
     if rank == 0:
         print(json.dumps(line))
-    s.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["c4", "c5", "coarse_ops", "table3",
+                                                                      "parallel_problems"])
+    ap.add_argument("--count", type=int, default=512, help="c4: number of solves")
+    ap.add_argument("--duration", type=float, default=60.0, help="c5: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=30.0, help="c5: extra seconds before the server stops")
+    ap.add_argument("--inflight", type=int, default=64, help="c5: concurrent solves")
+    ap.add_argument("--no-c4", action="store_true", help="skip the batched sub-record")
+    ap.add_argument("--no-c5", action="store_true", help="skip the served sub-record")
+    ap.add_argument("--c5-duration", type=float, default=3.0, help="served sub-record: seconds of arrivals")
+    ap.add_argument("--c5-drain", type=float, default=12.0, help="served sub-record: seconds after the arrivals")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision sub-measurement")
+    ap.add_argument("--variant-steps", type=int, default=3, help="timed solves per variant")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="solves of the end-to-end measurement")
+    ap.add_argument("--seq-steps", type=int, default=2, help="timed runs of sequential stepping")
+    ap.add_argument("--nt", type=int, default=0, help="override n_t of c1-c3 (small profiling cases)")
+    ap.add_argument("--tol", type=float, default=0.0, help="override the stop tolerance")
+    ap.add_argument("--cpu-nt", type=int, default=0, help="time steps of the CPU baseline's sample")
+    ap.add_argument("--reference-nt", type=int, default=0, help="time steps of the reference arm's sample")
+    ap.add_argument("--no-sequential", action="store_true", help="skip the sequential-stepping baseline")
+    ap.add_argument("--precision", default="", choices=["", "fp64", "mixed", "mixed_fast"],
+                    help="override the workload's")
+    ap.add_argument("--inner", type=int, default=0, help="MIXED: FP32 V-cycles per FP64 residual (0: library default)")
+    ap.add_argument("--coarse-solve", default="direct", choices=["direct", "gmres"],
+                    help="correction solves of the coarse operator (gmres: Sec. 6.3's GMRES)")
+    args = ap.parse_args()
+    global WORKLOAD
+    if args.workload == "c4" and args.impl == "ours":
+        return run_batched(args)
+    if args.workload == "c5" and args.impl == "ours":
+        return run_serving(args)
+    if args.workload == "coarse_ops" and args.impl == "ours":
+        return run_coarse_ops(args)
+    if args.workload == "table3" and args.impl == "ours":
+        return run_table3(args)
+    if args.workload == "parallel_problems" and args.impl == "ours":
+        return run_parallel_problems(args)
+    WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c3"])
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_single(args)
 
 
 if __name__ == "__main__":

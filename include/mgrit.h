@@ -337,15 +337,22 @@ int mgrit_profile_read(mgrit_handle* h, double out[60]);
  * norm) lives in one static device array of 65536 + 32 doubles (512 KB) that
  * every GPU loading the library holds until the process exits.
  *   params  : host; fields nx, cfl, order_p, rk_order_q (0 or p), m are used;
- *             rk_kind must be MGRIT_ERK and precision MGRIT_FP64.
+ *             rk_kind must be MGRIT_ERK, precision MGRIT_FP64 and order_p
+ *             odd (1, 3 or 5); other orders return MGRIT_ERR_INVALID_ARG.
+ *             The composite stencil Phi^m is folded modulo nx; if it still
+ *             has more than 1024 taps the call returns MGRIT_ERR_UNSUPPORTED.
  *   d_uC    : device, rows * nx C-point values u_{k m}, k = 0..rows-1.
  *   rows    : >= 2; (rows - 1) * ceil(nx / 1024) must not exceed 65536
  *             (nx >= 1024; ceil(nx / 512) or ceil(nx / 256) below), else
  *             MGRIT_ERR_INVALID_ARG and nothing runs.
- *   d_r     : device, (rows - 1) * nx outputs r_k = Phi^m u_{(k-1)m} - u_{km},
- *             k = 1..rows-1 (Sec. 2.2); must not overlap d_uC.
+ *   d_r     : device, (rows - 1) * nx outputs r_k = Phi^m u_{(k-1)m} - u_{km}
+ *             (the fine map applied m times to the previous C-point, minus
+ *             the C-point), k = 1..rows-1; must not overlap d_uC.
  *   norm_out: host, receives ||r||_2; NULL skips the copy (the call is then
- *             fully asynchronous).  With norm_out the stream is synchronised.
+ *             fully asynchronous).  With norm_out the stream is synchronised,
+ *             which a stream capture does not allow: while the stream is
+ *             being captured pass NULL (d_r is still written; the norm is
+ *             then not returned).
  *   stream  : cudaStream_t as void*.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current) and may load the

@@ -65,20 +65,41 @@ struct FixedStencil {
   double a[kMaxTaps];
 };
 
-// z = x * y (composition, each tap accumulated in long double), false if
-// the result exceeds kMaxTaps taps.  z must not alias x or y.
-bool fixed_mul(const FixedStencil& x, const FixedStencil& y, FixedStencil* z) {
-  int n = x.n + y.n - 1;
-  if (n > kMaxTaps) return false;
+// z = x * y (composition of periodic stencils, each tap accumulated in long
+// double), folded modulo nx whenever the product is wider than nx (taps t
+// and t + nx act on the same grid point), as the handle path folds its
+// composite stencil; false if the folded result exceeds kMaxTaps taps.  z
+// must not alias x or y.
+bool fixed_mul(const FixedStencil& x, const FixedStencil& y, int64_t nx, FixedStencil* z) {
+  const int n = x.n + y.n - 1;  // <= 2 kMaxTaps - 1
+  const int nz = (int64_t)n > nx ? (int)nx : n;
+  if (nz > kMaxTaps) return false;
+  long double acc[2 * kMaxTaps];
+  for (int k = 0; k < nz; ++k) acc[k] = 0.0L;
+  for (int i = 0; i < x.n; ++i)
+    for (int j = 0; j < y.n; ++j) {
+      const int k = i + j;
+      acc[nz == n ? k : (int)((int64_t)k % nx)] += (long double)x.a[i] * (long double)y.a[j];
+    }
   z->lo = x.lo + y.lo;
-  z->n = n;
-  for (int k = 0; k < n; ++k) {
-    long double acc = 0.0L;
-    int i0 = k - (y.n - 1) > 0 ? k - (y.n - 1) : 0;
-    int i1 = k < x.n - 1 ? k : x.n - 1;
-    for (int i = i0; i <= i1; ++i) acc += (long double)x.a[i] * (long double)y.a[k - i];
-    z->a[k] = (double)acc;
+  z->n = nz;
+  for (int k = 0; k < nz; ++k) z->a[k] = (double)acc[k];
+  return true;
+}
+
+// z = b p + a for periodic stencils on the window of p (p's support holds
+// a's modulo nx); false if a tap of a falls outside it.
+bool fixed_axpy(long double b, const FixedStencil& p, const FixedStencil& a, int64_t nx, FixedStencil* z) {
+  long double acc[kMaxTaps];
+  for (int i = 0; i < p.n; ++i) acc[i] = b * (long double)p.a[i];
+  for (int i = 0; i < a.n; ++i) {
+    const int64_t d = ((int64_t)(a.lo + i - p.lo) % nx + nx) % nx;
+    if (d >= p.n) return false;
+    acc[d] += (long double)a.a[i];
   }
+  z->lo = p.lo;
+  z->n = p.n;
+  for (int i = 0; i < p.n; ++i) z->a[i] = (double)acc[i];
   return true;
 }
 
@@ -141,17 +162,12 @@ int composite_stencil(const mgrit_params& P, StencilParams<double>* sp) {
   pw.lo = 0;
   pw.n = 1;
   pw.a[0] = 1.0;
+  const int64_t nx = P.nx;
   for (int j = 1; j < nb; ++j) {
-    if (!fixed_mul(pw, Z, &tmp)) return MGRIT_ERR_UNSUPPORTED;
+    if (!fixed_mul(pw, Z, nx, &tmp)) return MGRIT_ERR_UNSUPPORTED;
     pw = tmp;
-    // acc <- beta_j pw + acc; pw's support contains acc's
-    for (int i = 0; i < pw.n; ++i) {
-      int t = pw.lo + i;
-      double prev = (t >= acc.lo && t < acc.lo + acc.n) ? acc.a[t - acc.lo] : 0.0;
-      tmp.a[i] = (double)(beta[j] * (long double)pw.a[i] + (long double)prev);
-    }
-    tmp.lo = pw.lo;
-    tmp.n = pw.n;
+    // acc <- beta_j pw + acc; pw's support contains acc's (modulo nx)
+    if (!fixed_axpy(beta[j], pw, acc, nx, &tmp)) return MGRIT_ERR_UNSUPPORTED;
     acc = tmp;
   }
   // res = acc^m by repeated squaring
@@ -161,30 +177,19 @@ int composite_stencil(const mgrit_params& P, StencilParams<double>* sp) {
   base = acc;
   for (int e = P.m; e > 0; e >>= 1) {
     if (e & 1) {
-      if (!fixed_mul(res, base, &tmp)) return MGRIT_ERR_UNSUPPORTED;
+      if (!fixed_mul(res, base, nx, &tmp)) return MGRIT_ERR_UNSUPPORTED;
       res = tmp;
     }
     if (e > 1) {
-      if (!fixed_mul(base, base, &tmp)) return MGRIT_ERR_UNSUPPORTED;
+      if (!fixed_mul(base, base, nx, &tmp)) return MGRIT_ERR_UNSUPPORTED;
       base = tmp;
     }
   }
-  // fold modulo nx
-  const int64_t nx = P.nx;
-  int n = res.n;
-  double folded[kMaxTaps];
-  int nt = n;
-  if (n > nx) {
-    nt = (int)nx;
-    for (int i = 0; i < nt; ++i) folded[i] = 0.0;
-    for (int i = 0; i < n; ++i) folded[i % nx] += res.a[i];
-  } else {
-    for (int i = 0; i < n; ++i) folded[i] = res.a[i];
-  }
+  const int nt = res.n;  // at most nx: every product above was folded
   sp->nx = nx;
   sp->lo = res.lo;
   sp->ntaps = nt;
-  for (int i = 0; i < nt; ++i) sp->taps[i] = folded[i];
+  for (int i = 0; i < nt; ++i) sp->taps[i] = res.a[i];
   return MGRIT_OK;
 }
 
@@ -196,6 +201,9 @@ extern "C" int mgrit_residual_noalloc(const mgrit_params* params, const double* 
   const mgrit_params& P = *params;
   if (P.rk_kind != MGRIT_ERK || P.precision != MGRIT_FP64 || P.m < 2 || P.cfl <= 0.0 || P.nx < 32 ||
       P.nx % 8)
+    return MGRIT_ERR_INVALID_ARG;
+  // odd upwind orders only, ERK of the same order
+  if ((P.order_p != 1 && P.order_p != 3 && P.order_p != 5) || (P.rk_order_q != 0 && P.rk_order_q != P.order_p))
     return MGRIT_ERR_INVALID_ARG;
   const int64_t K = rows - 1;
   if (K * (int64_t)mg::stencil_tiles(P.nx, 0) > kNoAllocSlots) return MGRIT_ERR_INVALID_ARG;

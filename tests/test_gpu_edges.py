@@ -1,5 +1,5 @@
 """Edge cases of the CUDA path against the oracle: the full-size C3
-configuration (sampled C-points against the Fourier closed form
+configuration (every C-point against the Fourier closed form
 u_n = F^{-1}[lambda(omega)^n F u_0], whose symbol the oracle pins against the
 operator's application), the longest vectors the kernels take, and the
 degenerate hierarchies the method has (one CF-interval, a one-step coarsest
@@ -41,21 +41,38 @@ def _solve(prm, u0):
     return out, st
 
 
-def test_full_size_c3_sampled_cpoints():
-    """16384 x 65536, U5 + SDIRK3 at c = 4, MIXED, m = 16, 5 levels (the
-    bench configuration): sampled C-points within 1e-8 of exact stepping."""
+def _closed_form_rows(op, u0, m, rows):
+    """C-point rows u_{k m}, k = 0..rows-1, of sequential stepping by the
+    Fourier symbol (one inverse FFT per row)."""
+    nx = u0.shape[0]
+    lam_m = op.symbol(2 * np.pi * np.fft.fftfreq(nx)) ** m
+    f = np.fft.fft(u0)
+    out = np.empty((rows, nx))
+    for k in range(rows):
+        out[k] = np.real(np.fft.ifft(f))
+        f = f * lam_m
+    return out
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64, pkg.MIXED])
+def test_full_size_c3_all_cpoints(precision):
+    """16384 x 65536, U5 + SDIRK3 at c = 4, m = 16, 5 levels (the bench
+    configuration), FP64 and MIXED: all 4097 C-point rows within 1e-10
+    relative of sequential stepping by the closed form.  A 1e-10 relative
+    residual leaves an error of ~1.7e-10 here (the error is bounded only by
+    ||A^{-1}|| ||r||), so the solves stop at 1e-11."""
     nx, nt, m = 16384, 65536, 16
     u0 = ic_fourier(nx, seed=0)
-    prm = pkg.make_params(nx, nt, 4.0, 5, kind=pkg.SDIRK, q=3, m=m, levels=5, tol=1e-10, max_iter=30,
-                          precision=pkg.MIXED, seed=0)
+    prm = pkg.make_params(nx, nt, 4.0, 5, kind=pkg.SDIRK, q=3, m=m, levels=5, tol=1e-11, max_iter=40,
+                          precision=precision, seed=0)
     out, st = _solve(prm, u0)
     assert st["converged"]
-    ks = (1, 7, 1000, 2048, 4095, 4096)
-    want = _closed_form(oops.FineOperator(5, "sdirk", 3, 4.0), u0, [k * m for k in ks])
-    scale = np.max(np.abs(u0))
-    rows = out[list(ks)].cpu().numpy()
-    for i, k in enumerate(ks):
-        assert np.max(np.abs(rows[i] - want[k * m])) < 1e-8 * scale, k
+    want = _closed_form_rows(oops.FineOperator(5, "sdirk", 3, 4.0), u0, m, nt // m + 1)
+    got = out.cpu().numpy()
+    err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    print("C3 precision %d: %d iterations, max relative error over all C-points %.3e"
+          % (precision, st["iterations"], err))
+    assert err < 1e-10, err
 
 
 @pytest.mark.parametrize("kind,p,q,c,nx,m,levels", [
@@ -73,7 +90,7 @@ def test_longest_vectors(kind, p, q, c, nx, m, levels):
     want = _closed_form(oops.FineOperator(p, kname, q, c), u0, [k * m for k in ks])
     got = out.cpu().numpy()
     scale = np.max(np.abs(u0))
-    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-9 * scale
+    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-10 * scale
 
 
 @pytest.mark.parametrize("kind,p,q,c,nx,nt,m,levels,nu", [
@@ -88,16 +105,16 @@ def test_degenerate_hierarchies(kind, p, q, c, nx, nt, m, levels, nu):
     kname = "erk" if kind == pkg.ERK else "sdirk"
     u0 = ic_sin4_noise(nx, seed=2)
     for prec in (pkg.FP64, pkg.MIXED):
-        prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, nu=nu, tol=1e-10,
+        prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, nu=nu, tol=1e-11,
                               max_iter=40, seed=4, precision=prec)
         out, st = _solve(prm, u0)
         g = np.zeros((nt + 1, nx))
         g[0] = u0
         seq = omg.sequential(oops.FineOperator(p, kname, q, c), g)[::m]
         assert st["converged"], (prec, st["iterations"])
-        assert np.max(np.abs(out.cpu().numpy() - seq)) < 1e-9 * np.max(np.abs(seq)), prec
+        assert np.max(np.abs(out.cpu().numpy() - seq)) < 1e-10 * np.max(np.abs(seq)), prec
         if prec == pkg.FP64:
-            ref = omg.solve(omg.Hierarchy(p, kname, q, c, m, levels), u0, nt, nu=nu, tol=1e-10, max_iter=40,
+            ref = omg.solve(omg.Hierarchy(p, kname, q, c, m, levels), u0, nt, nu=nu, tol=1e-11, max_iter=40,
                             seed=4)
             assert st["iterations"] == ref["iterations"]
 
@@ -137,7 +154,7 @@ def test_even_p_longest_vectors(kind, p, c, nx, m, levels):
     ks = list(range(nt // m + 1))
     want = _closed_form(oops.FineOperator(p, kname, p, c), u0, [k * m for k in ks])
     got = out.cpu().numpy()
-    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-9 * np.max(np.abs(u0))
+    assert max(np.max(np.abs(got[k] - want[k * m])) for k in ks) < 1e-10 * np.max(np.abs(u0))
 
 
 @pytest.mark.parametrize("kind,p,c,nx,nt,m,levels,nu", [
@@ -165,9 +182,9 @@ def test_full_size_mass_conservation(kind, p, q, c, nx, nt, m, levels, precision
     C-point row of the converged full-size solution carries the initial mass
     to rounding and to the stop tolerance."""
     u0 = ic_fourier(nx, seed=4) + 0.5
-    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, tol=1e-10, max_iter=40,
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, tol=1e-11, max_iter=40,
                           seed=0, precision=precision)
     out, st = _solve(prm, u0)
     assert st["converged"]
     mass = out.sum(dim=1).cpu().numpy()
-    assert np.max(np.abs(mass - u0.sum())) < 1e-9 * np.abs(u0).sum()
+    assert np.max(np.abs(mass - u0.sum())) < 1e-10 * np.abs(u0).sum()

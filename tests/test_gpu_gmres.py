@@ -48,8 +48,8 @@ def _rel(a, b):
 
 
 def _solver(nx, nt, c, p, m, levels, kind=pkg.ERK, q=0, nu=1, seed=0, precision=pkg.FP64, max_iter=40,
-            gmres_maxit=0, gmres_rtol=0.0, coarse_solve=pkg.GMRES):
-    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, nu=nu, tol=1e-10, max_iter=max_iter,
+            gmres_maxit=0, gmres_rtol=0.0, coarse_solve=pkg.GMRES, tol=1e-10):
+    prm = pkg.make_params(nx, nt, c, p, kind=kind, q=q, m=m, levels=levels, nu=nu, tol=tol, max_iter=max_iter,
                           seed=seed, precision=precision, coarse_solve=coarse_solve, gmres_maxit=gmres_maxit,
                           gmres_rtol=gmres_rtol)
     return pkg.Solver(prm, stream=torch.cuda.current_stream().cuda_stream)
@@ -110,11 +110,13 @@ def test_gmres_apply_beyond_the_scratch_runs_in_pieces():
 def test_gmres_solve_matches_oracle(kind, p, q, c, m, levels, nx, nt, nu):
     kname = "erk" if kind == pkg.ERK else "sdirk"
     u0 = ic_sin4(nx) if p < 5 else ic_fourier(nx, seed=1)
-    s = _solver(nx, nt, c, p, m, levels, kind, q, nu=nu, seed=7)
+    # stop at 1e-12: with the early-stopped GMRES solves a 1e-10 residual
+    # leaves errors up to 2.6e-10 against sequential stepping (oracle)
+    s = _solver(nx, nt, c, p, m, levels, kind, q, nu=nu, seed=7, tol=1e-12)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out, allow_unconverged=True)
     h = omg.Hierarchy(p, kname, q, c, m, levels, gmres=(1e-2, ogm.default_maxit(p)))
-    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-10, max_iter=40, seed=7)
+    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-12, max_iter=40, seed=7)
     assert ref["converged"] and st["converged"]
     assert abs(st["iterations"] - ref["iterations"]) <= 1
     assert abs(st["history"][0] - ref["history"][0]) < 1e-12 * ref["history"][0]
@@ -122,7 +124,7 @@ def test_gmres_solve_matches_oracle(kind, p, q, c, m, levels, nx, nt, nu):
     g = np.zeros((nt + 1, nx))
     g[0] = u0
     seq = omg.sequential(oops.FineOperator(p, kname, q, c), g)[::m]
-    assert _rel(host(out), seq) < 1e-9
+    assert _rel(host(out), seq) < 1e-10, _rel(host(out), seq)
     # the same GMRES work per level, up to the rare solve moved across the
     # threshold by rounding and the right-hand sides of converged intervals
     # that are exactly zero on one side and rounding noise on the other
@@ -178,14 +180,14 @@ def test_gmres_in_mixed_precision_reaches_fp64_accuracy(precision):
     correction matrix is well conditioned) inside FP64 refinement."""
     nx, nt, m, L = 512, 1024, 4, 4
     u0 = ic_sin4_noise(nx, seed=4)
-    s = _solver(nx, nt, 1.38, 3, m, L, seed=3, precision=precision)
+    s = _solver(nx, nt, 1.38, 3, m, L, seed=3, precision=precision, tol=1e-12)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out)
     assert st["converged"]
     g = np.zeros((nt + 1, nx))
     g[0] = u0
     seq = omg.sequential(oops.FineOperator(3, "erk", 3, 1.38), g)[::m]
-    assert _rel(host(out), seq) < 1e-9
+    assert _rel(host(out), seq) < 1e-10, _rel(host(out), seq)
     assert all(s.gmres_stats(l)[0] > 0 for l in range(1, L))
     s.close()
 
@@ -209,21 +211,26 @@ def test_gmres_graph_solve_equals_eager():
 def test_full_size_erk3_vcycle_with_gmres():
     """4096 x 16384 ERK3+U3, m = 8, 4 levels with GMRES on every coarse level
     (the paper's multilevel setting): converges in the exact solve's
-    iteration count (+-1) to sequential stepping within 1e-8."""
+    iteration count (+-1) to sequential stepping, every C-point within 1e-10
+    relative of the closed form (stop at 1e-12: the early-stopped GMRES
+    solves leave a larger error per unit residual than exact ones)."""
     nx, nt, m, L = 4096, 16384, 8, 4
     u0 = ic_sin4_noise(nx, seed=0)
-    s = _solver(nx, nt, 1.38, 3, m, L)
+    s = _solver(nx, nt, 1.38, 3, m, L, tol=1e-12)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out)
-    d = _solver(nx, nt, 1.38, 3, m, L, coarse_solve=pkg.DIRECT)
+    d = _solver(nx, nt, 1.38, 3, m, L, coarse_solve=pkg.DIRECT, tol=1e-12)
     std = d.solve(dev(u0), torch.empty_like(out))
     assert st["converged"] and abs(st["iterations"] - std["iterations"]) <= 1
-    ks = (1, 512, 2047, 2048)
-    lam = oops.FineOperator(3, "erk", 3, 1.38).symbol(2 * np.pi * np.fft.fftfreq(nx))
-    f0 = np.fft.fft(u0)
+    lam_m = oops.FineOperator(3, "erk", 3, 1.38).symbol(2 * np.pi * np.fft.fftfreq(nx)) ** m
+    f = np.fft.fft(u0)
     rows = host(out)
-    for k in ks:
-        want = np.real(np.fft.ifft(lam ** (k * m) * f0))
-        assert np.max(np.abs(rows[k] - want)) < 1e-8 * np.max(np.abs(u0)), k
+    want = np.empty_like(rows)
+    for k in range(nt // m + 1):
+        want[k] = np.real(np.fft.ifft(f))
+        f = f * lam_m
+    err = float(np.max(np.abs(rows - want)) / np.max(np.abs(want)))
+    print("full-size GMRES V-cycle: %d iterations, error %.3e" % (st["iterations"], err))
+    assert err < 1e-10, err
     s.close()
     d.close()

@@ -7,9 +7,11 @@ Tolerances (FP64 everywhere):
   * MGRIT iterates: identical algorithm and random initial iterate (the same
     SplitMix64 stream on both sides), so per-iteration C-point values agree
     to rounding (1e-10 absolute on O(1) data) and iteration counts are equal.
-  * converged solution vs sequential stepping: the solve stops at a 1e-10
-    relative residual; the error bound is ||A^{-1}|| ||r||, measured here as
-    <= 1e-8 relative (the tests state the value they see).
+  * converged solution vs sequential stepping: a relative residual does not
+    bound the error by itself (the error is at most ||A^{-1}|| ||r||), so the
+    solves stop at a 1e-11 relative residual and every C-point must be within
+    1e-10 relative (max over all C-points and grid points, over the largest
+    value of sequential stepping) of the oracle's sequential stepping.
 """
 import numpy as np
 import pytest
@@ -173,12 +175,12 @@ SOLVES = [  # p, c, m, levels, nu, nx, nt
 @pytest.mark.parametrize("p,c,m,levels,nu,nx,nt", SOLVES)
 def test_solve_matches_oracle_mgrit(p, c, m, levels, nu, nx, nt):
     u0 = ic_sin4(nx)
-    s = solver(nx, nt, c, p, m, levels, nu=nu, tol=1e-10, max_iter=40, seed=7)
+    s = solver(nx, nt, c, p, m, levels, nu=nu, tol=1e-11, max_iter=40, seed=7)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out, allow_unconverged=True)
     L = st["levels"]
     h = omg.Hierarchy(p, "erk", p, c, m, L)
-    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-10, max_iter=40, seed=7)
+    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-11, max_iter=40, seed=7)
     assert st["iterations"] == ref["iterations"]
     assert st["converged"] == ref["converged"]
     hist = np.array(st["history"])
@@ -191,7 +193,7 @@ def test_solve_matches_oracle_mgrit(p, c, m, levels, nu, nx, nt):
     g = np.zeros((nt + 1, nx))
     g[0] = u0
     seq = omg.sequential(h.fine, g)[::m]
-    assert _rel(got, seq) < 1e-8
+    assert _rel(got, seq) < 1e-10, _rel(got, seq)
 
 
 def test_two_level_f_relaxation_exactness_on_gpu():
@@ -243,21 +245,22 @@ def test_divergence_reported_above_cfl_limit():
 def test_full_size_vcycle_against_sequential_stepping():
     nx, nt, m, c, L = 4096, 16384, 8, 0.85, 4
     u0 = ic_sin4_noise(nx, seed=0)
-    s = solver(nx, nt, c, 3, m, L, tol=1e-10, max_iter=30, seed=0)
+    s = solver(nx, nt, c, 3, m, L, tol=1e-11, max_iter=30, seed=0)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out)
     assert st["converged"]
     got = host(out)
     fine = oops.FineOperator(3, "erk", 3, c)
     u = u0.copy()
-    err = 0.0
+    err = float(np.max(np.abs(got[0] - u0)))
     scale = np.max(np.abs(u0))
     for n in range(1, nt + 1):
         u = fine.apply(u)
         if n % m == 0:
             err = max(err, float(np.max(np.abs(got[n // m] - u))))
+            scale = max(scale, float(np.max(np.abs(u))))
     print("full-size: iterations=%d rel err vs sequential=%.3e" % (st["iterations"], err / scale))
-    assert err / scale < 1e-8
+    assert err / scale < 1e-10
     # the V-cycle converges as fast as the two-level LFA predicts (Sec. 6.3:
     # little deterioration from two levels to V-cycles)
     assert st["conv_factor"] < 1.2 * lfa.two_level_factor(3, "erk", c, m), st["conv_factor"]
@@ -361,7 +364,7 @@ def test_output_all_time_points(kind, p, q, c, m, levels, nx, nt):
     g = np.zeros((nt + 1, nx))
     g[0] = u0
     seq = omg.sequential(fine, g)
-    assert np.max(np.abs(got - seq)) < 1e-8 * np.max(np.abs(seq))
+    assert np.max(np.abs(got - seq)) < 1e-10 * np.max(np.abs(seq))
     s.close()
 
 

@@ -79,17 +79,22 @@ def test_sdirk_coarse_operators_match_oracle(p, q, c, m, levels, nx):
 ])
 def test_sdirk_solve_matches_oracle_mgrit(p, q, c, m, levels, nu, nx, nt):
     u0 = ic_sin4(nx) if p < 5 else ic_fourier(nx, seed=1)
-    s = solver(nx, nt, c, p, q, m, levels, nu=nu, seed=5)
+    s = solver(nx, nt, c, p, q, m, levels, nu=nu, seed=5, tol=1e-11)
     out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
     st = s.solve(dev(u0), out, allow_unconverged=True)
     h = omg.Hierarchy(p, "sdirk", q, c, m, st["levels"])
-    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-10, max_iter=40, seed=5)
+    ref = omg.solve(h, u0, nt, nu=nu, tol=1e-11, max_iter=40, seed=5)
     assert st["iterations"] == ref["iterations"]
     hist, href = np.array(st["history"]), np.array(ref["history"])
     big = href > 1e-8 * href[0]
     assert np.max(np.abs(hist[big] - href[big]) / href[big]) < 1e-6
     got = host(out)
     assert np.max(np.abs(got - ref["u"][::m])) < 1e-10 * max(1.0, np.max(np.abs(u0)))
+    # converged solution against the oracle's sequential stepping, every C-point
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = omg.sequential(h.fine, g)[::m]
+    assert _rel(got, seq) < 1e-10, _rel(got, seq)
 
 
 @pytest.mark.parametrize("p,q,c,nx,nsteps,every", [(3, 3, 5.0, 256, 100, 10), (5, 3, 4.0, 4096, 40, 0),
