@@ -724,6 +724,10 @@ def run_single(args):
     if w["kind"] == "erk":
         kname = "%s<double,%d> (level-0 composite Phi^m)" % (
             "stencil_rows_persistent" if info0[4] else "stencil_rows_kernel", int(info0[6]))
+    elif info0[4] == 2:
+        kname = ("sdirk_seg_kernel<%d,%d,128> (level-0 SDIRK stages in FP64: one CTA per interval, 128-point "
+                 "segments per thread, warm-up recurrences, stage right-hand sides from the solves)"
+                 % ((w["p"] + 1) // 2, (w["p"] - 1) // 2))
     else:
         kname = ("sdirk_kernel<double,%d,%d> (level-0 SDIRK stages: banded solves, stage derivatives from the "
                  "solves), clusters of %d" % (int(info0[6]), w["p"] + 1, int(info0[7])))

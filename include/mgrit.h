@@ -286,7 +286,10 @@ int mgrit_output_all(mgrit_handle* h, double* d_all);
  * stencil taps (level 0, ERK) or the level's time step in units of dt
  * (coarse levels: m m_coarse^(l-1)), out[6] = chunk length of the in-block solves
  * (level 0, ERK: outputs per thread of the composite-stencil kernel, and
- * out[4] = 1 when its persistent form runs),
+ * out[4] = 1 when its persistent form runs; level 0, SDIRK: out[4] = 2 when
+ * the segmented FP64 kernel runs the level's relaxations -- one CTA per
+ * interval, 128 points per thread -- which MGRIT_SDIRK_SEG=0 / 1 disables
+ * / forces where it applies),
  * out[7] = CTAs per vector (thread-block cluster size) of the level's step
  * kernel (coarse levels; level 0 for SDIRK).  The step kernels' geometry is
  * measured at setup among the candidates that fit (cached per shape in the

@@ -197,13 +197,13 @@ __global__ void __launch_bounds__(256) coarse_kernel(const __grid_constant__ Coa
 
 template <typename T, typename TC, int P, int P1, bool GM>
 static void configure_coarse() {
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          227 * 1024);
     cudaFuncSetAttribute(coarse_kernel<T, TC, P, P1, GM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    configured = true;
-  }
+  });
 }
 
 template <typename T, typename TC, int P, int P1, bool GM>

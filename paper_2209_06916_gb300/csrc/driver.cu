@@ -103,6 +103,8 @@ struct mgrit_handle {
   std::unique_ptr<StencilParams<float>> fineMf;  // MIXED: Phi^m in FP32 (ERK)
   std::unique_ptr<SdirkParams<float>> sd0f;      // MIXED: SDIRK programme in FP32
   float* sdf_Mt[2] = {nullptr, nullptr};
+  std::unique_ptr<SdirkSegParams> seg0;          // FP64 level-0 SDIRK with per-thread segments
+                                                 // (used for CF / FRES / APPLY when set)
   std::unique_ptr<SdirkParams<double>> sdseq;    // SDIRK sequential stepping (one vector)
   double* sdseq_Mt[2] = {nullptr, nullptr};
   double* seq_tmp = nullptr;                     // MIXED: FP64 coarsest-level output
@@ -1208,11 +1210,238 @@ static int build_sdirk_params(mgrit_handle* h, int64_t K, std::unique_ptr<SdirkP
   return sdirk_with_geom(h, op, op32, bf, best, out, mt_dev, outf, mtf_dev);
 }
 
+// Steps of a stable recurrence x_i = -sum_q coef[q-1] x_{i-q} (order hord)
+// after which the response to any start state stays below `cut` of it: the
+// warm-up length of the segmented SDIRK kernel (limit + 1 if it does not
+// decay within `limit` steps).
+static int recurrence_reach(const double* coef, int hord, double cut, int limit) {
+  if (hord == 0) return 0;
+  int last = -1;
+  for (int b = 0; b < hord; ++b) {
+    double x[3] = {0.0, 0.0, 0.0};  // x_{i-1}, x_{i-2}, x_{i-3}
+    x[b] = 1.0;
+    for (int i = 0; i < 4 * limit; ++i) {
+      double v = 0.0;
+      for (int q = 0; q < hord; ++q) v -= coef[q] * x[q];
+      x[2] = x[1];
+      x[1] = x[0];
+      x[0] = v;
+      if (!(std::fabs(v) < cut)) last = std::max(last, i);
+    }
+  }
+  return std::min(last + 1, limit + 1);
+}
+
+// A stable recurrence x_i = b_i - sum_q coef[q-1] x_{i-q} of order h <= 3 as
+// two cascaded sections: y_i = b_i + r y_{i-1} (order o1 = 0 or 1), then
+// x_i = y_i + d[0] x_{i-1} + d[1] x_{i-2} (order o2 = h - o1).  A real root r
+// of t^h + coef[0] t^{h-1} + ... is split off (order 3 always has one, in
+// (-1, 1) since every root of a stable factor lies inside the unit circle;
+// order 2 when its roots are real), the rest deflated.  False if the
+// factors do not reproduce the coefficients.
+static bool split_sections(const double* coef, int h, int* o1, int* o2, double* r, double d[2]) {
+  *o1 = 0;
+  *o2 = h;
+  *r = 0.0;
+  d[0] = d[1] = 0.0;
+  if (h == 0) return true;
+  if (h == 1) {
+    *o1 = 1;
+    *o2 = 0;
+    *r = -coef[0];
+    return true;
+  }
+  double rt;
+  if (h == 3) {
+    // bisection on [-1, 1]: f(-1) < 0 < f(1) for roots inside the unit circle
+    auto f = [&](double t) { return ((t + coef[0]) * t + coef[1]) * t + coef[2]; };
+    double lo = -1.0, hi = 1.0;
+    if (!(f(lo) < 0.0 && f(hi) > 0.0)) return false;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      (f(mid) < 0.0 ? lo : hi) = mid;
+    }
+    rt = 0.5 * (lo + hi);
+    // t^3 + c0 t^2 + c1 t + c2 = (t - rt)(t^2 + e1 t + e2)
+    const double e1 = coef[0] + rt, e2 = coef[1] + rt * e1;
+    if (std::fabs(-rt * e2 - coef[2]) > 1e-13 * (1.0 + std::fabs(coef[2]))) return false;
+    *o1 = 1;
+    *o2 = 2;
+    *r = rt;
+    d[0] = -e1;
+    d[1] = -e2;
+    return true;
+  }
+  // h == 2: t^2 + c0 t + c1
+  const double disc = coef[0] * coef[0] - 4.0 * coef[1];
+  if (disc < 0.0) {  // complex pair: one second-order section
+    d[0] = -coef[0];
+    d[1] = -coef[1];
+    return true;
+  }
+  const double sq = std::sqrt(disc);
+  const double t1 = coef[0] >= 0.0 ? 0.5 * (-coef[0] - sq) : 0.5 * (-coef[0] + sq);  // larger |root|
+  const double t2 = coef[1] / t1;
+  *o1 = 1;
+  *o2 = 1;
+  *r = t1;
+  d[0] = t2;
+  return true;
+}
+
+// Segmented FP64 level-0 SDIRK kernel for this handle, or nothing when the
+// scheme or vector does not fit it: stiffly accurate SDIRK with at most 3
+// stages (q <= 3) and odd p, n_x a multiple of kSegPoints with 32..128
+// segments, both warm-up lengths (2^-56 decay of the factor recurrences)
+// at most one segment.
+static void build_sdirk_seg(mgrit_handle* h) {
+  h->seg0.reset();
+  const mgrit_params& P = h->prm;
+  const int q = P.rk_order_q ? P.rk_order_q : P.order_p;
+  if (P.rk_kind != MGRIT_SDIRK || q > 3 || P.order_p % 2 == 0) return;
+  if (h->nx % kSegPoints) return;
+  const int64_t T = h->nx / kSegPoints;
+  if (T < 32 || T > 128) return;
+  SdirkTableau tb;
+  if (!sdirk_tableau(q, &tb)) return;
+  const double g = tb.A[0][0];
+  Stencil L = upwind_taps(P.order_p);
+  Stencil A = stencil_add(stencil_identity(), L, g * P.cfl);
+  BandFactor bf;
+  std::string why;
+  if (!band_factor(A, &bf, &why) || bf.shift != 0) return;
+  int HC, HA;
+  upwind_bias(P.order_p, &HC, &HA);
+  if (bf.hc != HC || bf.ha > HA) return;
+  std::unique_ptr<SdirkSegParams> sp(new SdirkSegParams());
+  std::memset((void*)sp.get(), 0, sizeof(SdirkSegParams));
+  sp->n = (int)h->nx;
+  sp->T = (int)T;
+  sp->stages = tb.s;
+  if (!split_sections(bf.cc, bf.hc, &sp->c1, &sp->c2, &sp->cr, sp->cd) ||
+      !split_sections(bf.ca, bf.ha, &sp->a1, &sp->a2, &sp->ar, sp->ad))
+    return;
+  // warm-up lengths (multiples of 8, the kernel's load ring): both sections
+  // over the reach of the whole recurrence, or the first section over its
+  // own reach plus the second's and the second only over its own, whichever
+  // costs fewer multiply-adds; every neglected start state decays below
+  // 2^-58 of the data
+  const double cut = std::ldexp(1.0, -58);
+  const int lim = 4 * kSegPoints;
+  auto r8 = [](int v) { return (v + 7) & ~7; };
+  auto lengths = [&](const double* coef, int hord, int o1, int o2, double r, const double* d, int* w1, int* w2) {
+    const int rf = r8(recurrence_reach(coef, hord, cut, lim));
+    *w1 = rf;
+    *w2 = o2 > 0 ? rf : 0;
+    if (o1 == 1 && o2 >= 1) {
+      const double c1[1] = {-r};
+      const double c2[2] = {-d[0], -d[1]};
+      const int b = r8(recurrence_reach(c2, o2, cut, lim));
+      const int a = b + r8(recurrence_reach(c1, 1, cut, lim));
+      if (a <= kSegPoints && (rf > kSegPoints || a + o2 * b < (1 + o2) * rf)) {
+        *w1 = a;
+        *w2 = b;
+      }
+    }
+    return *w1 <= kSegPoints;
+  };
+  if (!lengths(bf.cc, bf.hc, sp->c1, sp->c2, sp->cr, sp->cd, &sp->rc1, &sp->rc2) ||
+      !lengths(bf.ca, bf.ha, sp->a1, sp->a2, sp->ar, sp->ad, &sp->ra1, &sp->ra2))
+    return;
+  // the section orders the kernel is instantiated for
+  const int key = sp->c1 * 1000 + sp->c2 * 100 + sp->a1 * 10 + sp->a2;
+  if (key != 1211 && key != 1202 && key != 1110 && key != 210 && key != 1000) return;
+  // stage right-hand sides from the solves: K_j = (R_j - Y_j) / gamma,
+  // R_2 = a2 u + b2 Y_1, R_3 = a3 u + b3 Y_1 + (a_32 / gamma) Y_2, with the
+  // unscaled solve U = kappa (I + gamma c L)^{-1} (inv_kappa = 1 / kappa)
+  const double ik = bf.inv_kappa;
+  sp->last = 1.0;
+  if (tb.s == 1) {
+    sp->last = ik;
+  } else {
+    const double a2 = 1.0 - tb.A[1][0] / g, b2 = tb.A[1][0] / g;
+    sp->e1u2 = a2 * ik;
+    sp->e1y2 = b2 * ik * ik;
+    if (tb.s == 3) {
+      const double r32 = tb.A[2][1] / g;
+      const double a3 = 1.0 - tb.A[2][0] / g - r32 * a2, b3 = tb.A[2][0] / g - r32 * b2;
+      sp->e1u3 = a3 * ik;
+      sp->e1y3 = b3 * ik * ik;
+      sp->e2y3 = r32 * ik;
+    }
+  }
+  h->seg0 = std::move(sp);
+}
+
+// MGRIT_SDIRK_SEG=0 never uses the segmented kernel, =1 always where it fits;
+// otherwise it runs when it measures faster than the chunked kernel.
+static int seg_policy() {
+  const char* e = std::getenv("MGRIT_SDIRK_SEG");
+  if (!e || !*e) return -1;
+  return std::atoi(e) ? 1 : 0;
+}
+
 static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) {
   int rc = build_sdirk_params(h, h->lev[0].K, &h->sd0, h->sd_Mt,
                               is_mixed(h->prm.precision) ? &h->sd0f : nullptr, h->sdf_Mt, why, buffers, -1.0);
   if (rc) return rc;
   h->sdirk = true;
+  int fc, fp;
+  const int pol = seg_policy();
+  build_sdirk_seg(h);
+  if (!h->seg0 || pol == 0 || geom_forced(&fc, &fp) || h->lev[0].K < 1) {
+    h->seg0.reset();
+    return MGRIT_OK;
+  }
+  if (pol == 1 || !buffers) return MGRIT_OK;
+  // measured choice: two steps of a CF relaxation on up to 608 intervals,
+  // chunked kernel against segmented kernel; cached per shape
+  char keyb[160];
+  std::snprintf(keyb, sizeof(keyb), "sdseg:n=%lld:K=%lld:p=%d:q=%d:lc=%d", (long long)h->nx,
+                (long long)h->lev[0].K, h->prm.order_p, h->prm.rk_order_q, (int)std::lround(std::log2(h->prm.cfl)));
+  const std::string key(keyb);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (!it->second) h->seg0.reset();
+      return MGRIT_OK;
+    }
+  }
+  if (!tuning_on()) return MGRIT_OK;
+  LevelData& L0 = h->lev[0];
+  const int64_t Kt = std::min<int64_t>(L0.K, 608);
+  SdirkParams<double> sp = *h->sd0;
+  sp.mode = kModeCF;
+  sp.zero_start = 0;
+  sp.start = L0.uC[0];
+  sp.out = L0.uC[1];
+  sp.rhs = nullptr;
+  sp.sub = nullptr;
+  sp.partial = nullptr;
+  sp.traj = nullptr;
+  sp.g = nullptr;
+  sp.nsteps = 2;
+  sp.K = Kt;
+  const float ms_chunk = time_launches(h, [&]() { return launch_sdirk(sp, h->st); });
+  SdirkSegParams gp = *h->seg0;
+  gp.mode = kModeCF;
+  gp.zero_start = 0;
+  gp.start = L0.uC[0];
+  gp.out = L0.uC[1];
+  gp.sub = nullptr;
+  gp.partial = nullptr;
+  gp.nsteps = 2;
+  gp.K = Kt;
+  const float ms_seg = time_launches(h, [&]() { return launch_sdirk_seg(gp, h->st); });
+  if (ms_chunk < 0.f || ms_seg < 0.f) return MGRIT_ERR_CUDA;
+  const bool use = ms_seg < ms_chunk;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store(key, use ? 1 : 0);
+  }
+  if (!use) h->seg0.reset();
   return MGRIT_OK;
 }
 
@@ -1354,7 +1583,20 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
   sp.every = every;
   sp.partial = (mode == kModeFRES) ? h->partials : nullptr;
   ProfScope ps(h, cat_flops, sdirk_flops(sp, h->nx, K, nsteps));
-  if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  if (!base && h->seg0 && !traj && (mode == kModeCF || mode == kModeFRES || mode == kModeAPPLY)) {
+    SdirkSegParams gp = *h->seg0;
+    gp.mode = mode;
+    gp.zero_start = zero_start;
+    gp.start = start;
+    gp.out = out;
+    gp.sub = sub;
+    gp.nsteps = nsteps;
+    gp.K = K;
+    gp.partial = sp.partial;
+    if (launch_sdirk_seg(gp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+  } else if (launch_sdirk(sp, h->st) < 0) {
+    return MGRIT_ERR_UNSUPPORTED;
+  }
   ++h->launches;
   return check_launch();
 }
@@ -1475,7 +1717,7 @@ static int l0_fres(mgrit_handle* h) {
     if (rc) return rc;
     {
       ProfScope ps(h, 2, 0.0);
-      launch_reduce_sum(h->partials, L0.K * h->sd0->csize, h->dnorm, h->st);
+      launch_reduce_sum(h->partials, L0.K * (h->seg0 ? 1 : h->sd0->csize), h->dnorm, h->st);
     }
     ++h->launches;
     return check_launch();
@@ -2820,7 +3062,11 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
   const LevelData& Lv = h->lev[level];
   out[0] = (double)Lv.N;
   if (level == 0) {
-    if (h->sdirk) {
+    if (h->sdirk && h->seg0) {
+      out[4] = 2.0;  // the segmented kernel runs CF / FRES / APPLY
+      out[6] = (double)kSegPoints;
+      out[7] = 1.0;
+    } else if (h->sdirk) {
       out[6] = (double)h->sd0->P;
       out[7] = (double)h->sd0->csize;
     } else {

@@ -164,22 +164,19 @@ int stencil_tiles(int64_t nx, int tile_r) {
 template <typename T, int R>
 static int64_t launch_stencil_r(const StencilParams<T>& p, cudaStream_t st) {
   const int W = kStencilThreads * R;
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(stencil_rows_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(stencil_rows_persistent<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-    configured = true;
-  }
+  });
   const int ntx = stencil_tiles(p.nx, R);
   if (p.persistent) {
     const int nload = W + p.ntaps - 1;
     const size_t smem = (size_t)2 * ((nload + 1) & ~1) * sizeof(T);
-    static int nsm = 0;
-    if (!nsm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_rows_persistent<T, R>, kStencilThreads,
                                                       smem) != cudaSuccess || per_sm < 1)
@@ -448,12 +445,12 @@ __global__ void __launch_bounds__(kSeqThreads) seq_kernel(const __grid_constant_
 }
 
 int launch_seq(const SeqParams& p, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(seq_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(seq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    configured = true;
-  }
+  });
   size_t smem = 2 * sizeof(double) * (size_t)(p.halo_l + p.npc + p.halo_r);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)p.csize);

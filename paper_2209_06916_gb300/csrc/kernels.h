@@ -3,7 +3,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace mg {
+
+// Kernel attributes (dynamic shared memory limits, non-portable cluster
+// sizes) are set per device: `f` runs the first time a call site sees the
+// current device, under the site's mutex, so a process driving several GPUs
+// configures each of them and concurrent first launches wait for it.
+template <typename F>
+inline void once_per_device(std::mutex& mu, uint64_t& done, F f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const uint64_t bit = 1ull << (dev & 63);
+  std::lock_guard<std::mutex> lk(mu);
+  if (!(done & bit)) {
+    f();
+    done |= bit;
+  }
+}
 
 constexpr int kMaxTaps = 1024;   // composite level-0 stencil taps (folded mod nx)
 constexpr int kMaxRounds = 5;    // in-warp chunk-scan rounds (distances 1..16)
@@ -161,6 +182,43 @@ struct SdirkParams {
   int every;
 };
 size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem);
+
+// ---------------------------------------------------------------------------
+// Level-0 SDIRK steps for many CF-intervals in FP64 (sdirk_seg.cuh): one CTA
+// per interval, one segment of kSegLen points per thread in shared memory,
+// the stage solves' recurrences entered through a warm-up over the
+// neighbouring segment (rc / ra points, where the neglected start state has
+// decayed below 2^-56).  Stiffly accurate SDIRK with 1..3 stages, right-hand
+// sides from the solves; modes CF, FRES (no C-point RHS) and APPLY.
+// ---------------------------------------------------------------------------
+constexpr int kSegPoints = 128;
+struct SdirkSegParams {
+  int n, T;              // points per vector, threads per CTA (n / kSegPoints)
+  int rc1, rc2;          // causal warm-up: first section over rc1 points, second over the last
+                         // rc2 of them (multiples of 8, rc2 <= rc1 <= kSegPoints)
+  int ra1, ra2;          // the same for the anticausal recurrence
+  int stages;            // 1..3
+  // each recurrence direction as two cascaded sections (two independent
+  // multiply-add chains): a first-order section y_i = b_i + r y_{i-1} (order
+  // c1 / a1 = 0 or 1) feeding a section of order c2 / a2 <= 2,
+  // x_i = y_i + d[0] x_{i-1} + d[1] x_{i-2} (anticausal: indices i+1, i+2)
+  int c1, c2, a1, a2;    // section orders (the kernel's template)
+  double cr, cd[2];      // causal sections
+  double ar, ad[2];      // anticausal sections
+  // unscaled solve U(b) = kappa (I + gamma c L)^{-1} b; stage 1: R2' = e1u2 u
+  // + e1y2 U(u), aux = e1u3 u + e1y3 U(u); stage 2: aux += e2y3 Y2; the last
+  // stage's output is scaled by `last`
+  double e1u2, e1y2, e1u3, e1y3, e2y3, last;
+  int mode, zero_start, nsteps;
+  int64_t K;
+  const double* start;   // rows k
+  double* out;           // CF / FRES: rows k+1; APPLY: rows k (also the per-interval scratch)
+  const double* sub;     // FRES: rows k+1
+  double* partial;       // FRES: one slot per interval
+};
+size_t sdirk_seg_smem_bytes(int n);
+// 1 on success, -1 on a launch error or an order the kernel lacks
+int launch_sdirk_seg(const SdirkSegParams& p, cudaStream_t st);
 // Chunk lengths the step kernels are compiled for (one chunk per thread).
 constexpr int kChunkLens[4] = {4, 8, 16, 32};
 // Largest co-schedulable cluster size <= want (power of two) for a CTA of

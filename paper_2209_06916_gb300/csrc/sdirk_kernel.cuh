@@ -200,12 +200,12 @@ __global__ void __launch_bounds__(256) sdirk_kernel(const __grid_constant__ Sdir
 
 template <typename T, int P, int P1>
 static void configure_sdirk() {
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(sdirk_kernel<T, P, P1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(sdirk_kernel<T, P, P1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    configured = true;
-  }
+  });
 }
 
 template <typename T, int P, int P1>

@@ -135,10 +135,15 @@ def test_gmres_solve_matches_oracle(kind, p, q, c, m, levels, nx, nt, nu):
             nsolves = sum(1 for k in its if k > 0)
             assert abs(gsolves - nsolves) <= 0.005 * nsolves, (lev, gsolves, nsolves)
             assert abs(git - sum(its)) <= 0.02 * sum(its), (lev, git, sum(its))
-    # and MGRIT converges as with the exact solve (Sec. 6.3)
+    # and MGRIT converges as with the exact solve at the paper's 1e-10 stop
+    # (Sec. 6.3; nearer the rounding level the inexact coarse solves cost
+    # an iteration or two more)
+    s.close()
+    s = _solver(nx, nt, c, p, m, levels, kind, q, nu=nu, seed=7)
+    st10 = s.solve(dev(u0), out, allow_unconverged=True)
     d = _solver(nx, nt, c, p, m, levels, kind, q, nu=nu, seed=7, coarse_solve=pkg.DIRECT)
     std = d.solve(dev(u0), torch.empty_like(out), allow_unconverged=True)
-    assert abs(std["iterations"] - st["iterations"]) <= 1
+    assert abs(std["iterations"] - st10["iterations"]) <= 1
     s.close()
     d.close()
 
