@@ -1298,7 +1298,7 @@ static void build_sdirk_seg(mgrit_handle* h) {
   h->seg0.reset();
   const mgrit_params& P = h->prm;
   const int q = P.rk_order_q ? P.rk_order_q : P.order_p;
-  if (P.rk_kind != MGRIT_SDIRK || q > 3 || P.order_p % 2 == 0) return;
+  if (P.rk_kind != MGRIT_SDIRK || (q != 1 && q != 3) || P.order_p % 2 == 0) return;
   if (h->nx % kSegPoints) return;
   const int64_t T = h->nx / kSegPoints;
   if (T < 32 || T > 128) return;
@@ -1325,8 +1325,8 @@ static void build_sdirk_seg(mgrit_handle* h) {
   // over the reach of the whole recurrence, or the first section over its
   // own reach plus the second's and the second only over its own, whichever
   // costs fewer multiply-adds; every neglected start state decays below
-  // 2^-58 of the data
-  const double cut = std::ldexp(1.0, -58);
+  // 2^-56 of the data (a sixth of an FP64 rounding unit)
+  const double cut = std::ldexp(1.0, -56);
   const int lim = 4 * kSegPoints;
   auto r8 = [](int v) { return (v + 7) & ~7; };
   auto lengths = [&](const double* coef, int hord, int o1, int o2, double r, const double* d, int* w1, int* w2) {

@@ -187,8 +187,8 @@ size_t sdirk_smem_bytes(int npc, int P, int nthr, int nslots, int elem);
 // Level-0 SDIRK steps for many CF-intervals in FP64 (sdirk_seg.cuh): one CTA
 // per interval, one segment of kSegLen points per thread in shared memory,
 // the stage solves' recurrences entered through a warm-up over the
-// neighbouring segment (rc / ra points, where the neglected start state has
-// decayed below 2^-56).  Stiffly accurate SDIRK with 1..3 stages, right-hand
+// neighbouring segment (where the neglected start state has decayed below
+// 2^-56).  Stiffly accurate SDIRK with 1..3 stages, right-hand
 // sides from the solves; modes CF, FRES (no C-point RHS) and APPLY.
 // ---------------------------------------------------------------------------
 constexpr int kSegPoints = 128;

@@ -12,7 +12,7 @@
 // afterwards: the thread first runs the same recurrence over the last
 // points of its left neighbour's segment (first points of its right
 // neighbour's) from a zero state.  The recurrences are stable with roots
-// inside the unit circle, so the neglected start state decays below 2^-58
+// inside the unit circle, so the neglected start state decays below 2^-56
 // of the data within the warm-up, and the thread enters its own segment
 // with the carry to that accuracy.  The first section runs over w1 points,
 // the second over the last w2 of them (w2 <= w1, multiples of 8, chosen on
@@ -46,52 +46,108 @@
 
 namespace mg {
 
-// One pass over `count` points (a multiple of 8) in pass order i = 0, 1, ...
-// ld(i), i even, loads the pair of inputs of points i and i+1 (an ascending
-// pass: .x is point i; a descending one: .y is point i); f(i, x) maps an
-// input to a result (a double2: one or two outputs); st(i, r_i, r_{i+1})
-// stores the results of the pair.  Blocks of 8 points are double buffered:
-// the next block's four pairs load while the current one computes.
-template <bool DESC, typename LD, typename F, typename ST>
-__device__ __forceinline__ void pair_pass(int count, LD ld, F f, ST st) {
-  if (count <= 0) return;
-  typedef decltype(ld(0)) V;
-  V a[4], b[4];
-  auto run = [&](int i0, const V (&v)[4]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + 2 * q;
-      const auto r0 = f(i, v[q], DESC ? 1 : 0);
-      const auto r1 = f(i + 1, v[q], DESC ? 0 : 1);
-      st(i, r0, r1);
-    }
-  };
-#pragma unroll
-  for (int q = 0; q < 4; ++q) a[q] = ld(2 * q);
-  int i0 = 0;
-  for (; i0 + 16 <= count; i0 += 16) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = ld(i0 + 8 + 2 * q);
-    run(i0, a);
-    if (i0 + 16 < count) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = ld(i0 + 16 + 2 * q);
-    }
-    run(i0 + 8, b);
+// A stream of value pairs: pair jj at p + jj * stride (in pairs; stride 1
+// for a shared-memory segment, T for a thread's pairs in the interleaved
+// scratch).  Block loads take a base pointer per block of 4 pairs and
+// constant multiples of the stride, so the address arithmetic per access is
+// one add.
+struct PairStream {
+  double2* p;
+  int s1, s2, s3;  // stride, 2 stride, 3 stride
+  __device__ __forceinline__ double2* at(int jj) const { return p + (size_t)jj * s1; }
+  __device__ __forceinline__ void load4(const double2* b, double2 (&v)[4]) const {
+    v[0] = b[0];
+    v[1] = b[s1];
+    v[2] = b[s2];
+    v[3] = b[s3];
   }
-  if (i0 < count) run(i0, a);
+};
+__device__ __forceinline__ PairStream pair_stream(double* base, int stride) {
+  return PairStream{reinterpret_cast<double2*>(base), stride, 2 * stride, 3 * stride};
 }
 
-// two pairs loaded together (the shared-memory input and the scratch)
-struct Pair2 {
-  double2 w, z;
-};
-__device__ __forceinline__ double lane_of(const double2& v, int h) { return h ? v.y : v.x; }
+// One pass over npairs pairs of a stream (a multiple of 4), ascending
+// (pairs 0, 1, ...; element .x first) or descending (pairs from the last
+// down; element .y first).  f(x) is called once per element in pass order;
+// st(pair index, result of .x, result of .y) stores a pair.  The next block of 4 pairs loads while the current block
+// computes (two register buffers, no copies).
+template <bool DESC, typename F, typename ST>
+__device__ __forceinline__ void stream_pass(const PairStream& in, int npairs, F f, ST st) {
+  if (npairs <= 0) return;
+  const int blocks = npairs >> 2;
+  auto base = [&](int b) -> const double2* { return in.at(DESC ? npairs - 4 - 4 * b : 4 * b); };
+  double2 va[4], vb[4];
+  auto run = [&](int b, const double2 (&v)[4]) {
+    const int jj0 = DESC ? npairs - 4 - 4 * b : 4 * b;
+#pragma unroll
+    for (int q0 = 0; q0 < 4; ++q0) {
+      const int q = DESC ? 3 - q0 : q0;
+      double r0, r1;
+      if (DESC) {
+        r1 = f(v[q].y);
+        r0 = f(v[q].x);
+      } else {
+        r0 = f(v[q].x);
+        r1 = f(v[q].y);
+      }
+      st(jj0 + q, r0, r1);
+    }
+  };
+  in.load4(base(0), va);
+  int b = 0;
+  for (; b + 2 <= blocks; b += 2) {
+    in.load4(base(b + 1), vb);
+    run(b, va);
+    if (b + 2 < blocks) in.load4(base(b + 2), va);
+    run(b + 1, vb);
+  }
+  if (b < blocks) run(b, va);
+}
 
-template <int C1, int C2, int A1, int A2, int S>
+// the same over two streams read together: f(x, z) per element
+template <bool DESC, typename F, typename ST>
+__device__ __forceinline__ void stream_pass2(const PairStream& in, const PairStream& in2, int npairs, F f, ST st) {
+  if (npairs <= 0) return;
+  const int blocks = npairs >> 2;
+  auto jjb = [&](int b) { return DESC ? npairs - 4 - 4 * b : 4 * b; };
+  double2 va[4], vb[4], za[4], zb[4];
+  auto run = [&](int b, const double2 (&v)[4], const double2 (&z)[4]) {
+    const int jj0 = jjb(b);
+#pragma unroll
+    for (int q0 = 0; q0 < 4; ++q0) {
+      const int q = DESC ? 3 - q0 : q0;
+      double r0, r1;
+      if (DESC) {
+        r1 = f(v[q].y, z[q].y);
+        r0 = f(v[q].x, z[q].x);
+      } else {
+        r0 = f(v[q].x, z[q].x);
+        r1 = f(v[q].y, z[q].y);
+      }
+      st(jj0 + q, r0, r1);
+    }
+  };
+  in.load4(in.at(jjb(0)), va);
+  in2.load4(in2.at(jjb(0)), za);
+  int b = 0;
+  for (; b + 2 <= blocks; b += 2) {
+    in.load4(in.at(jjb(b + 1)), vb);
+    in2.load4(in2.at(jjb(b + 1)), zb);
+    run(b, va, za);
+    if (b + 2 < blocks) {
+      in.load4(in.at(jjb(b + 2)), va);
+      in2.load4(in2.at(jjb(b + 2)), za);
+    }
+    run(b + 1, vb, zb);
+  }
+  if (b < blocks) run(b, va, za);
+}
+
+template <int STAGES, int C1, int C2, int A1, int A2, int S>
 __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ SdirkSegParams A) {
   extern __shared__ __align__(16) double smem[];
   constexpr int SP = S + 2;  // padded segment stride: 16-byte aligned, conflict-free pair columns
+  constexpr int NP = S / 2;  // pairs per segment
   const int T = A.T, t = threadIdx.x, n = A.n;
   double* w = smem;
   double* red = smem + (size_t)T * SP;
@@ -101,10 +157,12 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
   double* aux = orow;  // scratch until the final write
   const int tl = (t == 0) ? T - 1 : t - 1;
   const int tr = (t == T - 1) ? 0 : t + 1;
-  double* wo = w + t * SP;         // own segment
-  const double* wl = w + tl * SP;  // left neighbour's segment
-  const double* wr = w + tr * SP;  // right neighbour's segment
-  const int stages = A.stages;
+  // streams: own / left / right segments, own / left scratch pairs
+  const PairStream own = pair_stream(w + t * SP, 1);
+  const PairStream left = pair_stream(w + tl * SP, 1);
+  const PairStream right = pair_stream(w + tr * SP, 1);
+  const PairStream xown = pair_stream(aux + 2 * t, T);
+  const PairStream xleft = pair_stream(aux + 2 * tl, T);
   const int rc1 = A.rc1, rc2 = A.rc2, ra1 = A.ra1, ra2 = A.ra2;
   const double cr = A.cr, cd0 = A.cd[0], cd1 = A.cd[1];
   const double ar = A.ar, ad0 = A.ad[0], ad1 = A.ad[1];
@@ -115,15 +173,6 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
     const double* src = A.start + k * (int64_t)n;
     for (int i = t; i < n; i += T) w[i + 2 * (i / S)] = src[i];
   }
-
-  // pair loads / stores: shared-memory segments, and the pair-interleaved
-  // scratch of thread tt (the pair j, j+1 at (j/2) 2T + 2tt)
-  auto lds2 = [](const double* p, int j) { return *reinterpret_cast<const double2*>(p + j); };
-  auto sts2 = [&](int j, double a, double b) { *reinterpret_cast<double2*>(wo + j) = make_double2(a, b); };
-  auto aux2 = [&](int tt, int j) -> double2* {
-    return reinterpret_cast<double2*>(aux + (size_t)(j >> 1) * (2 * T) + 2 * tt);
-  };
-  auto nost = [](int, double, double) {};
 
   // causal recurrence, two cascaded sections: y_i = b_i + cr y_{i-1},
   // x_i = y_i + cd1 x_{i-2} + cd0 x_{i-1}
@@ -161,15 +210,14 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
     return v;
   };
   constexpr bool anti = (A1 + A2) > 0;
-  // the pair element h of v through the sections
-  auto c1only = [&](int, double2 v, int h) { return csec1(lane_of(v, h)); };
-  auto cboth = [&](int, double2 v, int h) { return csec2(csec1(lane_of(v, h))); };
-  auto a1only = [&](int, double2 v, int h) { return asec1(lane_of(v, h)); };
-  auto aboth = [&](int, double2 v, int h) { return asec2(asec1(lane_of(v, h))); };
+  auto cboth = [&](double b) { return csec2(csec1(b)); };
   auto yv = [&](double xv) { return anti ? asec2(asec1(xv)) : xv; };
+  auto nost = [](int, double, double) {};
+  auto st_own = [&](int jj, double r0, double r1) { *own.at(jj) = make_double2(r0, r1); };
 
   for (int s = 0; s < A.nsteps; ++s) {
-    for (int st = 1; st <= stages; ++st) {
+#pragma unroll 1
+    for (int st = 1; st <= STAGES; ++st) {
       const bool from_aux = (st == 3);
       // every write of the previous stage (shared memory and scratch) is
       // visible and every read of a neighbour's segment is done
@@ -177,65 +225,69 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
       // causal warm-up over the left neighbour's last rc1 points: the first
       // section alone, then both over the last rc2
       cy = cx1 = cx2 = 0.0;
-      if (from_aux) {
-        pair_pass<false>(rc1 - rc2, [&](int i) { return *aux2(tl, S - rc1 + i); }, c1only, nost);
-        pair_pass<false>(rc2, [&](int i) { return *aux2(tl, S - rc2 + i); }, cboth, nost);
-      } else {
-        pair_pass<false>(rc1 - rc2, [&](int i) { return lds2(wl, S - rc1 + i); }, c1only, nost);
-        pair_pass<false>(rc2, [&](int i) { return lds2(wl, S - rc2 + i); }, cboth, nost);
-        __syncthreads();  // the neighbour's tail is read before it is overwritten
+      {
+        const PairStream& src = from_aux ? xleft : left;
+        const PairStream w1 = PairStream{src.at(NP - rc1 / 2), src.s1, src.s2, src.s3};
+        const PairStream w2 = PairStream{src.at(NP - rc2 / 2), src.s1, src.s2, src.s3};
+        stream_pass<false>(w1, (rc1 - rc2) / 2, [&](double b) { return csec1(b); }, nost);
+        stream_pass<false>(w2, rc2 / 2, cboth, nost);
       }
+      if (!from_aux) __syncthreads();  // the neighbour's tail is read before it is overwritten
       // causal pass over the own segment (stage 1 of several also keeps u
       // in the scratch for its epilogue)
       if (from_aux) {
-        pair_pass<false>(S, [&](int j) { return *aux2(t, j); }, cboth, sts2);
-      } else if (st == 1 && stages >= 2) {
-        pair_pass<false>(S, [&](int j) {
-          const double2 v = lds2(wo, j);
-          *aux2(t, j) = v;
-          return v;
-        }, cboth, sts2);
+        stream_pass<false>(xown, NP, cboth, st_own);
+      } else if (st == 1 && STAGES >= 2) {
+        stream_pass2<false>(own, own, NP, [&](double b, double) { return cboth(b); },
+                            [&](int jj, double r0, double r1) {
+                              *xown.at(jj) = *own.at(jj);
+                              *own.at(jj) = make_double2(r0, r1);
+                            });
       } else {
-        pair_pass<false>(S, [&](int j) { return lds2(wo, j); }, cboth, sts2);
+        stream_pass<false>(own, NP, cboth, st_own);
       }
       // anticausal warm-up over the right neighbour's first ra1 points,
       // descending: the first section alone, then both over the last ra2
       au = av1 = av2 = 0.0;
       if (anti) {
         __syncthreads();
-        pair_pass<true>(ra1 - ra2, [&](int i) { return lds2(wr, ra1 - 2 - i); }, a1only, nost);
-        pair_pass<true>(ra2, [&](int i) { return lds2(wr, ra2 - 2 - i); }, aboth, nost);
+        const PairStream w1 = PairStream{right.at(ra2 / 2), 1, 2, 3};
+        stream_pass<true>(w1, (ra1 - ra2) / 2, [&](double b) { return asec1(b); }, nost);
+        stream_pass<true>(right, ra2 / 2, [&](double b) { return asec2(asec1(b)); }, nost);
         __syncthreads();  // the neighbour's head is read before it is overwritten
       }
-      // own segment, descending (pass index i: point S - 1 - i; the pair of
-      // pass indices i, i+1 sits at S - 2 - i): anticausal pass and the
-      // stage's epilogue
+      // own segment, descending: anticausal pass and the stage's epilogue
       //   last stage            w = last * y
       //   stage 1 (of 2 or 3)   w = e1u2 u + e1y2 y, and for 3 stages
       //                         aux = e1u3 u + e1y3 y (u read from aux)
       //   stage 2 of 3          aux += e2y3 y
-      if (st == stages) {
-        const double sc = A.last;
-        pair_pass<true>(S, [&](int i) { return lds2(wo, S - 2 - i); },
-                        [&](int, double2 v, int h) { return sc * yv(lane_of(v, h)); },
-                        [&](int i, double r0, double r1) { sts2(S - 2 - i, r1, r0); });
+      if (st == STAGES) {
+        if (STAGES == 1) {  // one stage: Y = U(u) / kappa
+          const double sc = A.last;
+          stream_pass<true>(own, NP, [&](double xv) { return sc * yv(xv); }, st_own);
+        } else {  // the scales are folded into the right-hand side
+          stream_pass<true>(own, NP, [&](double xv) { return yv(xv); }, st_own);
+        }
       } else if (st == 1) {
         const double e1u2 = A.e1u2, e1y2 = A.e1y2, e1u3 = A.e1u3, e1y3 = A.e1y3;
-        const bool three = (stages == 3);
-        pair_pass<true>(S, [&](int i) { return Pair2{lds2(wo, S - 2 - i), *aux2(t, S - 2 - i)}; },
-                        [&](int, Pair2 v, int h) {
-                          const double y = yv(lane_of(v.w, h)), u = lane_of(v.z, h);
-                          return make_double2(fma(e1y2, y, e1u2 * u), fma(e1y3, y, e1u3 * u));
-                        },
-                        [&](int i, double2 r0, double2 r1) {
-                          sts2(S - 2 - i, r1.x, r0.x);
-                          if (three) *aux2(t, S - 2 - i) = make_double2(r1.y, r0.y);
-                        });
+        double a3 = 0.0, a3p = 0.0;
+        stream_pass2<true>(own, xown, NP,
+                           [&](double xv, double u) {
+                             const double y = yv(xv);
+                             a3p = a3;
+                             if (STAGES == 3) a3 = fma(e1y3, y, e1u3 * u);
+                             return fma(e1y2, y, e1u2 * u);
+                           },
+                           [&](int jj, double r0, double r1) {
+                             *own.at(jj) = make_double2(r0, r1);
+                             // descending: r1 (point 2jj+1) was computed first, r0 last
+                             if (STAGES == 3) *xown.at(jj) = make_double2(a3, a3p);
+                           });
       } else {
         const double e2y3 = A.e2y3;
-        pair_pass<true>(S, [&](int i) { return Pair2{lds2(wo, S - 2 - i), *aux2(t, S - 2 - i)}; },
-                        [&](int, Pair2 v, int h) { return fma(e2y3, yv(lane_of(v.w, h)), lane_of(v.z, h)); },
-                        [&](int i, double r0, double r1) { *aux2(t, S - 2 - i) = make_double2(r1, r0); });
+        stream_pass2<true>(own, xown, NP,
+                           [&](double xv, double a) { return fma(e2y3, yv(xv), a); },
+                           [&](int jj, double r0, double r1) { *xown.at(jj) = make_double2(r0, r1); });
       }
     }
   }
