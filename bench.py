@@ -19,7 +19,8 @@ Default line (one "step" = one whole solve, every row of the hot path):
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Multi-GPU runs are independent replicas (one solve per rank): value = N *
-DOF / max-over-ranks time.
+DOF / max-over-ranks time; with --sharded, one solve is time-sharded over
+the ranks (strong scaling).
 """
 import argparse
 import json
@@ -533,6 +534,55 @@ def run_reference(args):
     return 0
 
 
+def run_sharded(args):
+    """One solve of the workload time-sharded over the torchrun ranks (one
+    GPU each, NCCL): the level-0 CF-intervals in contiguous blocks per rank,
+    one boundary row per C-relaxation, the residual norm all-reduced, the
+    coarse levels on rank 0.  Strong scaling: the whole job is one solve."""
+    import torch
+    import torch.distributed as dist
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if ws > 1 else "gloo")
+    import paper_2209_06916_gb300 as pkg
+    from paper_2209_06916_gb300.sharded import ShardedSolver
+    w = dict(WORKLOAD)
+    if args.nt > 0:
+        w["nt"] = args.nt
+    kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
+    prm = pkg.make_params(w["nx"], w["nt"], w["cfl"], w["p"], kind=kind, q=w["q"], m=w["m"], levels=w["levels"],
+                          nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=pkg.FP64)
+    s = ShardedSolver(prm, comm_device="cuda" if ws > 1 else "cpu")
+    u0 = make_ic(w)
+    for _ in range(args.warmup):
+        s.solve(u0)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(args.steps):
+        out, st = s.solve(u0)
+        its.append(st["iterations"])
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = (time.perf_counter() - t0) * 1e3
+    ms = max_over_ranks(ms, dist, "cuda" if ws > 1 else "cpu")
+    dof = w["nx"] * w["nt"]
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": dof * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                          "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": w["name"] + "_time_sharded", "nx": w["nx"], "nt": w["nt"],
+                                     "parallelism": "time-sharded x%d (level-0 CF-interval blocks per rank, "
+                                                    "coarse levels on rank 0)" % ws, "iterations": its,
+                                     "timing": "host clock around the solves, max over ranks"}}))
+    s.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def _max_rel_err(out, ref_rows, u0):
     """max |out - ref| / max |ref| over every C-point row (device tensors;
     row 0 of `out` against u0, rows 1.. against the sequential trajectory)."""
@@ -811,6 +861,8 @@ def main():
     ap.add_argument("--cpu-nt", type=int, default=0, help="time steps of the CPU baseline's sample")
     ap.add_argument("--reference-nt", type=int, default=0, help="time steps of the reference arm's sample")
     ap.add_argument("--no-sequential", action="store_true", help="skip the sequential-stepping baseline")
+    ap.add_argument("--sharded", action="store_true",
+                    help="under torchrun: one time-sharded solve over the ranks (default: independent replicas)")
     ap.add_argument("--precision", default="", choices=["", "fp64", "mixed", "mixed_fast"],
                     help="override the workload's")
     ap.add_argument("--inner", type=int, default=0, help="MIXED: FP32 V-cycles per FP64 residual (0: library default)")
@@ -831,6 +883,8 @@ def main():
     WORKLOAD = WORKLOADS.get(args.workload, WORKLOADS["c3"])
     if args.impl == "reference":
         return run_reference(args)
+    if args.sharded:
+        return run_sharded(args)
     return run_single(args)
 
 

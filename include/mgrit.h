@@ -238,6 +238,30 @@ int mgrit_solve_wait_for(mgrit_handle* h, double timeout_s, double* u_out, mgrit
 int mgrit_vcycle(mgrit_handle* h, double* norm_out);
 
 /*
+ * mgrit_level_rows -- rows row0 .. row0+nrows-1 of a level buffer (field 0:
+ * the C-point unknowns, field 1: the RHS, as in mgrit_level_io) against the
+ * caller's ptr (nrows * nx doubles): op 0 copies them to ptr (host or
+ * device), op 1 copies ptr into them (host or device), op 2 adds ptr
+ * (device) to them.  Asynchronous on the handle's stream for device
+ * pointers; a host pointer synchronises it.  Unlike mgrit_level_io, op 1 on
+ * row 0 of level 0 changes the current buffer only.  Used by time-sharded
+ * solves (blocks of CF-intervals on several GPUs, Sec. 6.3.2) to exchange
+ * boundary rows and corrections.  Errors: INVALID_ARG (rows outside the
+ * buffer, op 2 with a host pointer), CUDA.
+ */
+int mgrit_level_rows(mgrit_handle* h, int level, int field, int64_t row0, int64_t nrows, double* ptr, int op);
+
+/*
+ * mgrit_coarse_correct -- the coarse-grid correction of one MGRIT iteration
+ * (Sec. 2.2): solve the level-1 error equation e_{k+1} = Psi e_k + r_{k+1}
+ * with the current level-1 RHS (zero initial guess, one cycle over levels
+ * >= 1, the coarsest solved sequentially) and add e to the level-0 C-point
+ * unknowns (rows 1..nt/m).  Asynchronous.  FP64 handles only (MIXED:
+ * MGRIT_ERR_UNSUPPORTED); INVALID_ARG for a one-level handle.
+ */
+int mgrit_coarse_correct(mgrit_handle* h);
+
+/*
  * mgrit_level_io -- copy a level buffer to or from the caller.
  *   field 0: C-point unknowns of the level (level 0: (nt/m+1) rows; level l:
  *            N_{l+1}+1 rows, N_l = nt/m^l), field 1: RHS g of the level

@@ -108,6 +108,8 @@ def load_library(path=LIB_PATH):
     lib.mgrit_vcycle.argtypes = [P, dp]
     lib.mgrit_level_io.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.mgrit_level_rows.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int]
+    lib.mgrit_coarse_correct.argtypes = [P]
     lib.mgrit_fine_propagate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int64, P]
     lib.mgrit_fine_propagate_async.argtypes = [P, P, P, ctypes.c_int64]
     lib.mgrit_output_all.argtypes = [P, P]
@@ -265,6 +267,22 @@ class Solver:
         r = ctypes.c_int64()
         _check(self.lib.mgrit_level_io(self.h, level, field, _ptr(arr), 1, ctypes.byref(r)),
                "mgrit_level_io")
+
+    def rows_io(self, level, field, row0, nrows, arr, op):
+        """Rows row0 .. row0 + nrows - 1 of a level buffer against arr (numpy
+        or device tensor, nrows x nx): op 0 get, 1 set, 2 add (device)."""
+        _check(self.lib.mgrit_level_rows(self.h, level, field, row0, nrows, _ptr(arr), op), "mgrit_level_rows")
+
+    def level_put(self, level, field, arr):
+        """Set a whole level buffer from arr (numpy or device tensor): as
+        level_set, and for level 0 row 0 goes into both C-point buffers."""
+        r = ctypes.c_int64()
+        _check(self.lib.mgrit_level_io(self.h, level, field, _ptr(arr), 1, ctypes.byref(r)), "mgrit_level_io")
+
+    def coarse_correct(self):
+        """One coarse-grid correction from the current level-1 RHS into the
+        level-0 C-points."""
+        _check(self.lib.mgrit_coarse_correct(self.h), "mgrit_coarse_correct")
 
     def level_info(self, level):
         out = (ctypes.c_double * 8)()

@@ -2738,6 +2738,50 @@ int mgrit_coarse_apply(mgrit_handle* h, int level, const double* d_in, double* d
   return coarse_launch(h, level, kModeAPPLY, 0, d_in, d_out, nullptr, nullptr, 1, nvec, nullptr);
 }
 
+int mgrit_coarse_correct(mgrit_handle* h) {
+  if (!h || h->L < 2) return MGRIT_ERR_INVALID_ARG;
+  if (h->mixed) return MGRIT_ERR_UNSUPPORTED;
+  return coarse_correct(h, 1);
+}
+
+int mgrit_level_rows(mgrit_handle* h, int level, int field, int64_t row0, int64_t nrows, double* ptr, int op) {
+  if (!h || level < 0 || level >= h->L || !ptr || row0 < 0 || nrows < 0 || op < 0 || op > 2)
+    return MGRIT_ERR_INVALID_ARG;
+  LevelData& Lv = h->lev[level];
+  double* buf = nullptr;
+  int64_t rows = 0;
+  if (field == 0) {
+    if (level == h->L - 1) return MGRIT_ERR_INVALID_ARG;
+    buf = Lv.uC[Lv.cur];
+    rows = Lv.K + 1;
+  } else if (field == 1) {
+    if (level == 0) return MGRIT_ERR_INVALID_ARG;
+    buf = Lv.g;
+    rows = Lv.N + 1;
+  } else {
+    return MGRIT_ERR_INVALID_ARG;
+  }
+  if (row0 + nrows > rows) return MGRIT_ERR_INVALID_ARG;
+  if (nrows == 0) return MGRIT_OK;
+  double* at = buf + row0 * h->nx;
+  const size_t bytes = sizeof(double) * (size_t)h->nx * (size_t)nrows;
+  int rc = MGRIT_OK;
+  if (op == 0) {
+    rc = copy_any(ptr, at, bytes, h->st);
+    if (!rc && !is_device_ptr(ptr)) CUDA_TRY(cudaStreamSynchronize(h->st));
+  } else if (op == 1) {
+    rc = copy_any(at, ptr, bytes, h->st);
+    if (!rc && !is_device_ptr(ptr)) CUDA_TRY(cudaStreamSynchronize(h->st));
+  } else {
+    if (!is_device_ptr(ptr)) return MGRIT_ERR_INVALID_ARG;
+    launch_convert(kAddD2D, at, nullptr, nrows * h->nx, h->st, ptr);
+    ++h->launches;
+    rc = check_launch();
+  }
+  if (!rc && level == 0 && field == 0 && op != 0) h->have_initial = true;
+  return rc;
+}
+
 int mgrit_vcycle(mgrit_handle* h, double* norm_out) {
   if (!h) return MGRIT_ERR_INVALID_ARG;
   int rc = coarse_correct(h, 1);
