@@ -550,6 +550,8 @@ def run_sharded(args):
     w = dict(WORKLOAD)
     if args.nt > 0:
         w["nt"] = args.nt
+        while w["levels"] > 2 and args.nt % (w["m"] ** (w["levels"] - 1)):
+            w["levels"] -= 1
     kind = pkg.ERK if w["kind"] == "erk" else pkg.SDIRK
     prm = pkg.make_params(w["nx"], w["nt"], w["cfl"], w["p"], kind=kind, q=w["q"], m=w["m"], levels=w["levels"],
                           nu=w["nu"], tol=w["tol"], max_iter=w["max_iter"], seed=w["seed"], precision=pkg.FP64)
