@@ -444,17 +444,22 @@ typedef struct mgrit_serve_stats {
   int max_inflight, pad;
   double dof_completed;  /* sum of nx * nt over completed requests           */
   double wall_s;
+  double setup_s;        /* host time spent setting up admitted requests    */
 } mgrit_serve_stats;
 
 /*
  * mgrit_serve -- replay a stream of solve requests with continuous batching:
  * request i (params[i], initial condition u0s[i] on the host) arrives at
  * arrival_s[i] seconds (non-decreasing) after the call starts; arrived
- * requests are admitted first come, first served while fewer than
- * max_inflight solves run and the estimated device memory of the running
- * solves stays within hbm_budget_bytes; each admitted request gets its own
- * hierarchy (set up on admission, freed on completion) and runs as a
- * graph-resident solve overlapping the others on the GPU.  Returns when all
+ * requests are admitted while fewer than max_inflight solves run and the
+ * estimated device memory of the running solves stays within
+ * hbm_budget_bytes -- the first that fits among the 64 oldest waiting
+ * requests, except that a request waiting longer than 2 s is not overtaken
+ * -- and each admitted request gets its own hierarchy (set up on admission,
+ * freed on completion) and runs as a graph-resident solve overlapping the
+ * others on the GPU.  No launch geometry is timed while serving: setups
+ * use geometries measured earlier in the process (mgrit_setup of the same
+ * shapes before the call, on an idle GPU) or the best-scored candidate.  Returns when all
  * requests finished or after time_limit_s (running solves are drained,
  * unadmitted ones keep status 1).  u_outs (may be NULL, as may each
  * u_outs[i]) receives request i's C-points ((nt/m + 1) * nx values, host or

@@ -69,7 +69,7 @@ class ServeStats(ctypes.Structure):
                 ("failed", ctypes.c_int64), ("rejected", ctypes.c_int64), ("backlog_end", ctypes.c_int64),
                 ("max_backlog", ctypes.c_int64), ("max_mem_bytes", ctypes.c_int64),
                 ("max_inflight", ctypes.c_int), ("pad", ctypes.c_int), ("dof_completed", ctypes.c_double),
-                ("wall_s", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("setup_s", ctypes.c_double)]
 
 
 class MgritError(RuntimeError):

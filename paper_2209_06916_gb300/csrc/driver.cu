@@ -917,7 +917,14 @@ static std::vector<Geom> chunk_geometries(int64_t n, int64_t minpts, int elem, F
   return out;
 }
 
+// Measured tuning is off inside a running server (no candidate is timed
+// while other solves share the GPU; cached decisions still apply, else the
+// best-scored candidate): set for the serving thread by mgrit_serve.
+static thread_local bool g_no_measure = false;
+void set_measured_tuning(bool on) { g_no_measure = !on; }
+
 static bool tuning_on() {
+  if (g_no_measure) return false;
   const char* on = std::getenv("MGRIT_AUTOTUNE");
   return !(on && on[0] == '0');
 }

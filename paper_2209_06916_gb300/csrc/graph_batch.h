@@ -17,3 +17,5 @@ int batch_graph_run(mgrit_handle* const* hs, int64_t n, const double* const* u0s
                     cudaStream_t st);
 // Statistics of solve h after batch_graph_run; returns its status.
 int batch_graph_stats(const mgrit_handle* h, mgrit_stats* stats);
+// Measured geometry tuning on (default) or off for the calling thread.
+void set_measured_tuning(bool on);

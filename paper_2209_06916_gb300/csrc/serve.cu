@@ -22,6 +22,9 @@
 
 namespace {
 
+constexpr size_t kAdmitWindow = 64;  // pending requests considered per admission
+constexpr double kMaxSkipS = 2.0;    // wait after which the oldest request is not overtaken
+
 // coarsening factor from level l to level l+1
 int factor_of(const mgrit_params& p, int64_t l) { return (l == 0 || p.m_coarse <= 0) ? p.m : p.m_coarse; }
 
@@ -164,6 +167,13 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
   };
   std::vector<Slot> slots(max_inflight);
   std::deque<int64_t> pending;
+  // setups inside the serving loop take cached or best-scored geometries:
+  // candidates are timed only before serving starts (see the pre-tune in
+  // the binding's callers), never while other solves run
+  set_measured_tuning(false);
+  struct Restore {
+    ~Restore() { set_measured_tuning(true); }
+  } restore;
   for (int64_t i = 0; i < count; ++i) {
     std::memset(&results[i], 0, sizeof(results[i]));
     results[i].status = 1;  // not started
@@ -206,25 +216,48 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
       if (rc == MGRIT_ERR_CUDA) rc_fatal = rc;
     }
     if (rc_fatal) break;
-    // admissions (FIFO; a request larger than the whole budget is rejected)
+    // admissions: first fit among the oldest kAdmitWindow pending requests
+    // (a request that does not fit in the free budget does not block
+    // smaller ones behind it), except that once the oldest has waited
+    // kMaxSkipS seconds nothing overtakes it until it fits (no starvation);
+    // a request larger than the whole budget is rejected
     while (!pending.empty()) {
-      const int64_t req = pending.front();
-      const int64_t need = mgrit_estimate_bytes(&params[req]);
-      if (need > hbm_budget_bytes) {
-        results[req].status = MGRIT_ERR_OOM;
-        ++S.rejected;
-        ++finished;
-        pending.pop_front();
-        continue;
+      auto free_slot = std::find_if(slots.begin(), slots.end(), [](const Slot& s) { return s.h == nullptr; });
+      if (free_slot == slots.end()) break;
+      const bool head_starving = (now() - arrival_s[pending.front()]) > kMaxSkipS;
+      int64_t pick = -1;
+      size_t pos = 0;
+      for (size_t w = 0; w < pending.size() && w < kAdmitWindow; ++w) {
+        const int64_t req = pending[w];
+        const int64_t need = mgrit_estimate_bytes(&params[req]);
+        if (need > hbm_budget_bytes) {
+          results[req].status = MGRIT_ERR_OOM;
+          ++S.rejected;
+          ++finished;
+          pending.erase(pending.begin() + (std::ptrdiff_t)w);
+          pick = -2;
+          break;
+        }
+        if (mem + need <= hbm_budget_bytes) {
+          pick = req;
+          pos = w;
+          break;
+        }
+        if (head_starving) break;
       }
-      auto it = std::find_if(slots.begin(), slots.end(), [](const Slot& s) { return s.h == nullptr; });
-      if (it == slots.end() || mem + need > hbm_budget_bytes) break;
+      if (pick == -2) continue;
+      if (pick < 0) break;
+      const int64_t req = pick;
+      const int64_t need = mgrit_estimate_bytes(&params[req]);
+      auto it = free_slot;
       const int si = (int)(it - slots.begin());
       mgrit_handle* h = nullptr;
+      const double ts = now();
       int rc = mgrit_setup(&params[req], (void*)pool[si], &h);
       if (rc == MGRIT_OK) rc = mgrit_solve_async(h, u0s[req]);
-      results[req].start_s = now();
-      pending.pop_front();
+      results[req].start_s = ts;
+      S.setup_s += now() - ts;
+      pending.erase(pending.begin() + (std::ptrdiff_t)pos);
       if (rc) {
         if (h) mgrit_destroy(h);
         results[req].status = rc;
