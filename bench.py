@@ -236,7 +236,22 @@ def batched_record(count, steps, warmup, tol=1e-11):
         ref = outs[i].cpu().numpy()
         err = max(err, float(np.max(np.abs(last - ref)) / np.max(np.abs(ref))))
     b.close()
+    # FP64 floor: every refinement step needs one FP64 level-0 residual, the
+    # composite stencil Phi^m over all intervals; for ERKp+Up its flops per
+    # space-time point equal those of one explicit step (2 p^2 taps' worth,
+    # m p^2 + 1 taps per m steps), i.e. a residual sweep costs the flops of
+    # the whole sequential solve.  At the stencil kernel's 0.8 of the FP64
+    # peak this bounds the batch time from below whatever the FP32 and coarse
+    # work cost.
+    sweeps = [x["outer_iterations"] + 1 for x in st]
+    fl = [2.0 * min(d["m"] * d["p"] ** 2 + 1, d["nx"]) * d["nx"] * (d["nt"] // d["m"]) for d in mix]
+    floor_s = sum(k * f for k, f in zip(sweeps, fl)) / (0.8 * FP64_PEAK_FLOPS)
     return {"workload": "advection1d_batched_%d_erk_mixed" % count, "value": dof / dt, "unit": UNIT,
+            "fp64_residual_sweeps": {"median": float(np.median(sweeps)), "max": int(max(sweeps)),
+                                     "floor_ms": floor_s * 1e3,
+                                     "floor_over_sequential": (floor_s * 1e3) / (sdt * 1e3),
+                                     "note": "FP64 residual sweeps alone at 0.8 of the FP64 peak; each sweep has "
+                                             "the flops of the whole sequential solve"},
             "ms_per_batch": dt * 1e3, "batches_timed": steps, "solves": count, "dof_total": dof,
             "converged": conv, "iterations_median": float(np.median(its)), "iterations_max": int(max(its)),
             "tol": tol, "setup_s": setup_s, "launch": "one CUDA graph, one branch per solve",

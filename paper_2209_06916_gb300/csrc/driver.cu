@@ -2363,6 +2363,14 @@ static int build_solve_graph(mgrit_handle* h) {
   return rc;
 }
 
+// Capture and instantiate the handle's solve graph now (a later
+// mgrit_solve_async only launches it): lets a server prepare solves off its
+// serving thread.
+int solve_graph_prepare(mgrit_handle* h) {
+  if (!h) return MGRIT_ERR_INVALID_ARG;
+  return build_solve_graph(h);
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

@@ -19,3 +19,6 @@ int batch_graph_run(mgrit_handle* const* hs, int64_t n, const double* const* u0s
 int batch_graph_stats(const mgrit_handle* h, mgrit_stats* stats);
 // Measured geometry tuning on (default) or off for the calling thread.
 void set_measured_tuning(bool on);
+// Build a handle's graph-resident solve now (mgrit_solve_async then only
+// launches it).
+int solve_graph_prepare(mgrit_handle* h);

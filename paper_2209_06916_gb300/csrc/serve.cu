@@ -12,8 +12,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -144,13 +146,105 @@ extern "C" int64_t mgrit_batch_dof(const mgrit_batch* b) {
 
 // ---------------------------------------------------------------------------
 // server
+//
+// Two host threads.  The serving thread admits requests (slot and memory
+// budget), launches prepared solves and collects finished ones; a setup
+// worker builds each admitted request's hierarchy and solve graph
+// (mgrit_setup, graph capture and instantiation), so no setup holds up a
+// launch or the collection of a finished solve.  Neither thread times
+// launch candidates.
 // ---------------------------------------------------------------------------
+namespace {
+
+struct SetupJob {
+  int slot;
+  int64_t req;
+};
+struct SetupDone {
+  int slot;
+  int64_t req;
+  mgrit_handle* h;
+  int rc;
+  double secs;
+};
+
+class SetupWorker {
+ public:
+  SetupWorker(const mgrit_params* params, const std::vector<cudaStream_t>* pool, int device)
+      : params_(params), pool_(pool), device_(device), th_([this] { run(); }) {}
+  ~SetupWorker() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    th_.join();
+  }
+  void submit(int slot, int64_t req) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      jobs_.push_back(SetupJob{slot, req});
+    }
+    cv_.notify_all();
+  }
+  // finished setups (moved out)
+  std::vector<SetupDone> take() {
+    std::lock_guard<std::mutex> lk(mu_);
+    std::vector<SetupDone> out;
+    out.swap(done_);
+    return out;
+  }
+  bool idle() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return jobs_.empty() && !busy_;
+  }
+
+ private:
+  void run() {
+    cudaSetDevice(device_);
+    set_measured_tuning(false);
+    for (;;) {
+      SetupJob j;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [this] { return stop_ || !jobs_.empty(); });
+        if (jobs_.empty()) return;  // stop requested and nothing left
+        j = jobs_.front();
+        jobs_.pop_front();
+        busy_ = true;
+      }
+      const auto t0 = std::chrono::steady_clock::now();
+      mgrit_handle* h = nullptr;
+      int rc = mgrit_setup(&params_[j.req], (void*)(*pool_)[j.slot], &h);
+      if (rc == MGRIT_OK) rc = solve_graph_prepare(h);
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      std::lock_guard<std::mutex> lk(mu_);
+      done_.push_back(SetupDone{j.slot, j.req, h, rc, secs});
+      busy_ = false;
+    }
+  }
+  const mgrit_params* params_;
+  const std::vector<cudaStream_t>* pool_;
+  int device_;
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<SetupJob> jobs_;
+  std::vector<SetupDone> done_;
+  bool busy_ = false;
+  bool stop_ = false;
+  std::thread th_;
+};
+
+}  // namespace
+
 extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s, double* const* u_outs,
                            const double* arrival_s, int64_t count, int64_t hbm_budget_bytes, int max_inflight,
                            double time_limit_s, mgrit_request_result* results, mgrit_serve_stats* st) {
   if (!params || !u0s || !arrival_s || count < 0 || max_inflight <= 0 || !results) return MGRIT_ERR_INVALID_ARG;
   for (int64_t i = 1; i < count; ++i)
     if (arrival_s[i] < arrival_s[i - 1]) return MGRIT_ERR_INVALID_ARG;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return MGRIT_ERR_CUDA;
   std::vector<cudaStream_t> pool;
   for (int i = 0; i < max_inflight; ++i) {
     cudaStream_t s;
@@ -160,20 +254,16 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
     }
     pool.push_back(s);
   }
+  // slot states: free, setting up (the worker holds it), running
+  enum { kFree = 0, kSetup = 1, kRunning = 2 };
   struct Slot {
+    int state = kFree;
     mgrit_handle* h = nullptr;
     int64_t req = -1;
     int64_t bytes = 0;
   };
   std::vector<Slot> slots(max_inflight);
   std::deque<int64_t> pending;
-  // setups inside the serving loop take cached or best-scored geometries:
-  // candidates are timed only before serving starts (see the pre-tune in
-  // the binding's callers), never while other solves run
-  set_measured_tuning(false);
-  struct Restore {
-    ~Restore() { set_measured_tuning(true); }
-  } restore;
   for (int64_t i = 0; i < count; ++i) {
     std::memset(&results[i], 0, sizeof(results[i]));
     results[i].status = 1;  // not started
@@ -184,109 +274,11 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
   auto now = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   int64_t next = 0, finished = 0, mem = 0;
   int rc_fatal = MGRIT_OK;
-  while (finished < count) {
-    const double t = now();
-    if (t > time_limit_s) break;
-    while (next < count && arrival_s[next] <= t) pending.push_back(next++);
-    S.max_backlog = std::max<int64_t>(S.max_backlog, (int64_t)pending.size());
-    bool progress = false;
-    // completions
-    for (auto& sl : slots) {
-      if (!sl.h) continue;
-      int q = mgrit_solve_query(sl.h);
-      if (q == 1) continue;
-      mgrit_stats ms;
-      int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
-      mgrit_request_result& r = results[sl.req];
-      r.finish_s = now();
-      r.latency_ms = (r.finish_s - arrival_s[sl.req]) * 1e3;
-      r.iterations = ms.iterations;
-      r.status = rc;
-      if (rc == MGRIT_OK) {
-        ++S.completed;
-        S.dof_completed += (double)params[sl.req].nx * (double)params[sl.req].nt;
-      } else {
-        ++S.failed;
-      }
-      mgrit_destroy(sl.h);
-      mem -= sl.bytes;
-      sl = Slot();
-      ++finished;
-      progress = true;
-      if (rc == MGRIT_ERR_CUDA) rc_fatal = rc;
-    }
-    if (rc_fatal) break;
-    // admissions: first fit among the oldest kAdmitWindow pending requests
-    // (a request that does not fit in the free budget does not block
-    // smaller ones behind it), except that once the oldest has waited
-    // kMaxSkipS seconds nothing overtakes it until it fits (no starvation);
-    // a request larger than the whole budget is rejected
-    while (!pending.empty()) {
-      auto free_slot = std::find_if(slots.begin(), slots.end(), [](const Slot& s) { return s.h == nullptr; });
-      if (free_slot == slots.end()) break;
-      const bool head_starving = (now() - arrival_s[pending.front()]) > kMaxSkipS;
-      int64_t pick = -1;
-      size_t pos = 0;
-      for (size_t w = 0; w < pending.size() && w < kAdmitWindow; ++w) {
-        const int64_t req = pending[w];
-        const int64_t need = mgrit_estimate_bytes(&params[req]);
-        if (need > hbm_budget_bytes) {
-          results[req].status = MGRIT_ERR_OOM;
-          ++S.rejected;
-          ++finished;
-          pending.erase(pending.begin() + (std::ptrdiff_t)w);
-          pick = -2;
-          break;
-        }
-        if (mem + need <= hbm_budget_bytes) {
-          pick = req;
-          pos = w;
-          break;
-        }
-        if (head_starving) break;
-      }
-      if (pick == -2) continue;
-      if (pick < 0) break;
-      const int64_t req = pick;
-      const int64_t need = mgrit_estimate_bytes(&params[req]);
-      auto it = free_slot;
-      const int si = (int)(it - slots.begin());
-      mgrit_handle* h = nullptr;
-      const double ts = now();
-      int rc = mgrit_setup(&params[req], (void*)pool[si], &h);
-      if (rc == MGRIT_OK) rc = mgrit_solve_async(h, u0s[req]);
-      results[req].start_s = ts;
-      S.setup_s += now() - ts;
-      pending.erase(pending.begin() + (std::ptrdiff_t)pos);
-      if (rc) {
-        if (h) mgrit_destroy(h);
-        results[req].status = rc;
-        ++S.failed;
-        ++finished;
-        continue;
-      }
-      it->h = h;
-      it->req = req;
-      it->bytes = need;
-      mem += need;
-      S.max_mem_bytes = std::max(S.max_mem_bytes, mem);
-      ++S.admitted;
-      progress = true;
-    }
-    int inflight = 0;
-    for (auto& sl : slots) inflight += sl.h != nullptr;
-    S.max_inflight = std::max(S.max_inflight, inflight);
-    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
-  // drain whatever is still running at the time limit
-  for (auto& sl : slots) {
-    if (!sl.h) continue;
-    mgrit_stats ms;
-    int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
+  auto finish = [&](Slot& sl, int rc, const mgrit_stats* ms) {
     mgrit_request_result& r = results[sl.req];
     r.finish_s = now();
     r.latency_ms = (r.finish_s - arrival_s[sl.req]) * 1e3;
-    r.iterations = ms.iterations;
+    r.iterations = ms ? ms->iterations : 0;
     r.status = rc;
     if (rc == MGRIT_OK) {
       ++S.completed;
@@ -294,8 +286,119 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
     } else {
       ++S.failed;
     }
-    mgrit_destroy(sl.h);
+    if (sl.h) mgrit_destroy(sl.h);
+    mem -= sl.bytes;
     sl = Slot();
+    ++finished;
+    if (rc == MGRIT_ERR_CUDA) rc_fatal = rc;
+  };
+  {
+    SetupWorker worker(params, &pool, device);
+    while (finished < count) {
+      const double t = now();
+      if (t > time_limit_s) break;
+      while (next < count && arrival_s[next] <= t) pending.push_back(next++);
+      S.max_backlog = std::max<int64_t>(S.max_backlog, (int64_t)pending.size());
+      bool progress = false;
+      // prepared solves: launch
+      for (auto& d : worker.take()) {
+        Slot& sl = slots[d.slot];
+        sl.h = d.h;
+        S.setup_s += d.secs;
+        int rc = d.rc;
+        if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, u0s[sl.req]);
+        if (rc) {
+          finish(sl, rc, nullptr);
+        } else {
+          sl.state = kRunning;
+          results[sl.req].start_s = now();
+        }
+        progress = true;
+      }
+      // completions
+      for (auto& sl : slots) {
+        if (sl.state != kRunning) continue;
+        if (mgrit_solve_query(sl.h) == 1) continue;
+        mgrit_stats ms;
+        int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
+        finish(sl, rc, &ms);
+        progress = true;
+      }
+      if (rc_fatal) break;
+      // admissions: first fit among the oldest kAdmitWindow pending requests
+      // (a request that does not fit in the free budget does not block
+      // smaller ones behind it), except that once the oldest has waited
+      // kMaxSkipS seconds nothing overtakes it until it fits (no
+      // starvation); a request larger than the whole budget is rejected
+      while (!pending.empty()) {
+        auto free_slot = std::find_if(slots.begin(), slots.end(), [](const Slot& s) { return s.state == kFree; });
+        if (free_slot == slots.end()) break;
+        const bool head_starving = (now() - arrival_s[pending.front()]) > kMaxSkipS;
+        int64_t pick = -1;
+        size_t pos = 0;
+        for (size_t w = 0; w < pending.size() && w < kAdmitWindow; ++w) {
+          const int64_t req = pending[w];
+          const int64_t need = mgrit_estimate_bytes(&params[req]);
+          if (need > hbm_budget_bytes) {
+            results[req].status = MGRIT_ERR_OOM;
+            ++S.rejected;
+            ++finished;
+            pending.erase(pending.begin() + (std::ptrdiff_t)w);
+            pick = -2;
+            break;
+          }
+          if (mem + need <= hbm_budget_bytes) {
+            pick = req;
+            pos = w;
+            break;
+          }
+          if (head_starving) break;
+        }
+        if (pick == -2) continue;
+        if (pick < 0) break;
+        const int64_t need = mgrit_estimate_bytes(&params[pick]);
+        Slot& sl = *free_slot;
+        sl.state = kSetup;
+        sl.req = pick;
+        sl.bytes = need;
+        mem += need;
+        S.max_mem_bytes = std::max(S.max_mem_bytes, mem);
+        ++S.admitted;
+        pending.erase(pending.begin() + (std::ptrdiff_t)pos);
+        worker.submit((int)(free_slot - slots.begin()), pick);
+        progress = true;
+      }
+      int inflight = 0;
+      for (auto& sl : slots) inflight += sl.state != kFree;
+      S.max_inflight = std::max(S.max_inflight, inflight);
+      // idle: wait a millisecond (solves take far longer; polling every
+      // running solve in a tight loop would contend with the setup
+      // worker's CUDA calls)
+      if (!progress) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+    // the worker's remaining setups finish (its destructor waits); their
+    // solves are launched and drained below
+    while (!worker.idle()) std::this_thread::sleep_for(std::chrono::microseconds(200));
+    for (auto& d : worker.take()) {
+      Slot& sl = slots[d.slot];
+      sl.h = d.h;
+      S.setup_s += d.secs;
+      int rc = d.rc;
+      if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, u0s[sl.req]);
+      if (rc) {
+        finish(sl, rc, nullptr);
+      } else {
+        sl.state = kRunning;
+        results[sl.req].start_s = now();
+      }
+    }
+  }
+  // drain whatever is still running at the time limit
+  for (auto& sl : slots) {
+    if (sl.state != kRunning) continue;
+    mgrit_stats ms;
+    int rc = mgrit_solve_wait(sl.h, u_outs ? u_outs[sl.req] : nullptr, &ms);
+    finish(sl, rc, &ms);
   }
   S.arrived = next;
   S.backlog_end = (int64_t)pending.size() + (count - next);
