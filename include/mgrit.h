@@ -312,8 +312,9 @@ int mgrit_output_all(mgrit_handle* h, double* d_all);
  * (level 0, ERK: outputs per thread of the composite-stencil kernel, and
  * out[4] = 1 when its persistent form runs; level 0, SDIRK: out[4] = 2 when
  * the segmented FP64 kernel runs the level's relaxations -- one CTA per
- * interval, 128 points per thread -- which MGRIT_SDIRK_SEG=0 / 1 disables
- * / forces where it applies),
+ * interval, 128 points per thread -- and out[5] = 1 when MIXED inner
+ * cycles run the FP32 segmented kernel; MGRIT_SDIRK_SEG=0 / 1 disables /
+ * forces both where they apply),
  * out[7] = CTAs per vector (thread-block cluster size) of the level's step
  * kernel (coarse levels; level 0 for SDIRK).  The step kernels' geometry is
  * measured at setup among the candidates that fit (cached per shape in the

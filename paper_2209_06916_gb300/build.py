@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgrit.so")
 
 SOURCES = ["kernels.cu", "kernels_coarse.cu", "kernels_coarse_f.cu", "kernels_coarse_fd.cu", "kernels_sdirk.cu",
-           "kernels_sdirk_f.cu", "kernels_sdirk_seg.cu", "driver.cu", "coeffs.cpp", "noalloc.cu", "serve.cu"]
+           "kernels_sdirk_f.cu", "kernels_sdirk_seg.cu", "kernels_sdirk_seg32.cu", "driver.cu", "coeffs.cpp", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 

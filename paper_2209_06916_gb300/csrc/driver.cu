@@ -31,6 +31,10 @@
 
 using namespace mg;
 
+// sqrt of a sum of squares, NaN kept (a NaN residual must read as diverged,
+// not as zero)
+static inline double norm_of_sq(double s) { return s == s ? std::sqrt(s > 0.0 ? s : 0.0) : s; }
+
 static inline bool is_mixed(int precision) { return precision == MGRIT_MIXED || precision == MGRIT_MIXED_FAST; }
 
 namespace {
@@ -103,6 +107,7 @@ struct mgrit_handle {
   std::unique_ptr<StencilParams<float>> fineMf;  // MIXED: Phi^m in FP32 (ERK)
   std::unique_ptr<SdirkParams<float>> sd0f;      // MIXED: SDIRK programme in FP32
   float* sdf_Mt[2] = {nullptr, nullptr};
+  std::unique_ptr<SdirkSeg32Params> seg0f;       // MIXED: the FP32 segmented stage kernel
   std::unique_ptr<SdirkSegParams> seg0;          // FP64 level-0 SDIRK with per-thread segments
                                                  // (used for CF / FRES / APPLY when set)
   std::unique_ptr<SdirkParams<double>> sdseq;    // SDIRK sequential stepping (one vector)
@@ -1380,6 +1385,82 @@ static void build_sdirk_seg(mgrit_handle* h) {
   h->seg0 = std::move(sp);
 }
 
+// FP32 segmented stage kernel of MIXED inner cycles, or nothing when the
+// scheme or vector does not fit it: q = 1 or 3, odd p, n_x a multiple of
+// kSeg32Points with 32..256 segments, warm-ups (2^-27 decay) within one
+// segment.  The stages in mat-vec form: R_j += -c a_ji L_p Y_i.
+static void build_sdirk_seg32(mgrit_handle* h) {
+  h->seg0f.reset();
+  const mgrit_params& P = h->prm;
+  const int q = P.rk_order_q ? P.rk_order_q : P.order_p;
+  if (!is_mixed(P.precision) || P.rk_kind != MGRIT_SDIRK || (q != 1 && q != 3) || P.order_p % 2 == 0) return;
+  if (h->nx % kSeg32Points) return;
+  const int64_t T = h->nx / kSeg32Points;
+  if (T < 32 || T > 256) return;
+  SdirkTableau tb;
+  if (!sdirk_tableau(q, &tb)) return;
+  const double g = tb.A[0][0];
+  Stencil L = upwind_taps(P.order_p);
+  int HC, HA;
+  upwind_bias(P.order_p, &HC, &HA);
+  if (L.lo != -HC || L.hi != HA || L.width() > 8) return;
+  Stencil Am = stencil_add(stencil_identity(), L, g * P.cfl);
+  BandFactor bf;
+  std::string why;
+  if (!band_factor(Am, &bf, &why) || bf.shift != 0 || bf.hc != HC || bf.ha > HA) return;
+  int c1, c2, a1, a2;
+  double cr, cd[2], ar, ad[2];
+  if (!split_sections(bf.cc, bf.hc, &c1, &c2, &cr, cd) || !split_sections(bf.ca, bf.ha, &a1, &a2, &ar, ad)) return;
+  const int key = c1 * 1000 + c2 * 100 + a1 * 10 + a2;
+  if (key != 1211 && key != 1202 && key != 1110 && key != 210 && key != 1000) return;
+  const double cut = std::ldexp(1.0, -27);
+  const int lim = 4 * kSeg32Points;
+  auto r8 = [](int v) { return (v + 7) & ~7; };
+  auto lengths = [&](const double* coef, int hord, int o1, int o2, double r, const double* d, int* w1, int* w2) {
+    const int rf = r8(recurrence_reach(coef, hord, cut, lim));
+    *w1 = rf;
+    *w2 = o2 > 0 ? rf : 0;
+    if (o1 == 1 && o2 >= 1) {
+      const double k1[1] = {-r};
+      const double k2[2] = {-d[0], -d[1]};
+      const int b = r8(recurrence_reach(k2, o2, cut, lim));
+      const int a = b + r8(recurrence_reach(k1, 1, cut, lim));
+      if (a <= kSeg32Points && (rf > kSeg32Points || a + o2 * b < (1 + o2) * rf)) {
+        *w1 = a;
+        *w2 = b;
+      }
+    }
+    return *w1 <= kSeg32Points;
+  };
+  std::unique_ptr<SdirkSeg32Params> sp(new SdirkSeg32Params());
+  std::memset((void*)sp.get(), 0, sizeof(SdirkSeg32Params));
+  if (!lengths(bf.cc, bf.hc, c1, c2, cr, cd, &sp->rc1, &sp->rc2) ||
+      !lengths(bf.ca, bf.ha, a1, a2, ar, ad, &sp->ra1, &sp->ra2))
+    return;
+  sp->n = (int)h->nx;
+  sp->T = (int)T;
+  sp->c1 = c1;
+  sp->c2 = c2;
+  sp->a1 = a1;
+  sp->a2 = a2;
+  sp->p1 = L.width();
+  sp->stages = tb.s;
+  sp->cr = (float)cr;
+  sp->cd[0] = (float)cd[0];
+  sp->cd[1] = (float)cd[1];
+  sp->ar = (float)ar;
+  sp->ad[0] = (float)ad[0];
+  sp->ad[1] = (float)ad[1];
+  sp->ik = (float)bf.inv_kappa;
+  for (int i = 0; i < L.width(); ++i) sp->ltaps[i] = (float)L.a[i];
+  if (tb.s == 3) {
+    sp->g[0] = (float)(-P.cfl * tb.A[1][0]);
+    sp->g[1] = (float)(-P.cfl * tb.A[2][0]);
+    sp->g[2] = (float)(-P.cfl * tb.A[2][1]);
+  }
+  h->seg0f = std::move(sp);
+}
+
 // MGRIT_SDIRK_SEG=0 never uses the segmented kernel, =1 always where it fits;
 // otherwise it runs when it measures faster than the chunked kernel.
 static int seg_policy() {
@@ -1396,10 +1477,64 @@ static int build_sdirk(mgrit_handle* h, std::string* why, bool buffers = false) 
   int fc, fp;
   const int pol = seg_policy();
   build_sdirk_seg(h);
-  if (!h->seg0 || pol == 0 || geom_forced(&fc, &fp) || h->lev[0].K < 1) {
+  build_sdirk_seg32(h);
+  if (pol == 0 || geom_forced(&fc, &fp) || h->lev[0].K < 1) {
     h->seg0.reset();
+    h->seg0f.reset();
     return MGRIT_OK;
   }
+  if (h->seg0f && pol != 1 && buffers) {
+    // measured choice for the FP32 inner kernel, as for FP64 below
+    char kb[160];
+    std::snprintf(kb, sizeof(kb), "sdseg32:n=%lld:K=%lld:p=%d:q=%d:lc=%d", (long long)h->nx,
+                  (long long)h->lev[0].K, h->prm.order_p, h->prm.rk_order_q, (int)std::lround(std::log2(h->prm.cfl)));
+    const std::string key32(kb);
+    int cached = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load();
+      auto it = g_tune.find(key32);
+      if (it != g_tune.end()) cached = it->second;
+    }
+    if (cached == 0) {
+      h->seg0f.reset();
+    } else if (cached < 0 && tuning_on()) {
+      LevelData& L0 = h->lev[0];
+      const int64_t Kt = std::min<int64_t>(L0.K, 608);
+      SdirkParams<float> sp = *h->sd0f;
+      sp.mode = kModeCF;
+      sp.zero_start = 0;
+      sp.start = L0.uCf[0];
+      sp.out = L0.uCf[1];
+      sp.rhs = nullptr;
+      sp.sub = nullptr;
+      sp.partial = nullptr;
+      sp.traj = nullptr;
+      sp.g = nullptr;
+      sp.nsteps = 2;
+      sp.K = Kt;
+      const float ms_chunk = time_launches(h, [&]() { return launch_sdirk(sp, h->st); });
+      SdirkSeg32Params gp = *h->seg0f;
+      gp.mode = kModeCF;
+      gp.zero_start = 0;
+      gp.start = L0.uCf[0];
+      gp.out = L0.uCf[1];
+      gp.rhs = nullptr;
+      gp.sub = nullptr;
+      gp.partial = nullptr;
+      gp.nsteps = 2;
+      gp.K = Kt;
+      const float ms_seg = time_launches(h, [&]() { return launch_sdirk_seg32(gp, h->st); });
+      if (ms_chunk < 0.f || ms_seg < 0.f) return MGRIT_ERR_CUDA;
+      const bool use = ms_seg < ms_chunk;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_store(key32, use ? 1 : 0);
+      }
+      if (!use) h->seg0f.reset();
+    }
+  }
+  if (!h->seg0) return MGRIT_OK;
   if (pol == 1 || !buffers) return MGRIT_OK;
   // measured choice: two steps of a CF relaxation on up to 608 intervals,
   // chunked kernel against segmented kernel; cached per shape
@@ -1887,7 +2022,7 @@ static int level0_relax_residual(mgrit_handle* h, double* norm) {
   if (rc) return rc;
   CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(cudaStreamSynchronize(h->st));
-  *norm = std::sqrt(std::max(0.0, *h->hnorm));
+  *norm = norm_of_sq(*h->hnorm);
   return MGRIT_OK;
 }
 
@@ -1898,6 +2033,25 @@ static int level0_relax_residual(mgrit_handle* h, double* norm) {
 // with FP32 relaxation sweeps, FP64 correction solves on ill-conditioned
 // levels, and the coarsest level solved sequentially in FP64.
 // ---------------------------------------------------------------------------
+// One FP32 level-0 step launch of MIXED (CF / FRES): the segmented kernel
+// when it runs, else the chunked one; < 0 on a launch error.
+static int launch_l0_f32(mgrit_handle* h, const SdirkParams<float>& sp) {
+  if (h->seg0f && !sp.traj && !sp.g && (sp.mode == kModeCF || sp.mode == kModeFRES)) {
+    SdirkSeg32Params gp = *h->seg0f;
+    gp.mode = sp.mode;
+    gp.zero_start = sp.zero_start;
+    gp.start = sp.start;
+    gp.rhs = sp.rhs;
+    gp.out = sp.out;
+    gp.sub = sp.sub;
+    gp.partial = sp.partial;
+    gp.nsteps = sp.nsteps;
+    gp.K = sp.K;
+    return launch_sdirk_seg32(gp, h->st);
+  }
+  return launch_sdirk(sp, h->st);
+}
+
 static int l0f_cf(mgrit_handle* h, bool zero_start) {
   LevelData& L0 = h->lev[0];
   const size_t row = sizeof(float) * (size_t)h->nx;
@@ -1922,7 +2076,7 @@ static int l0f_cf(mgrit_handle* h, bool zero_start) {
     sp.K = L0.K;
     sp.traj = nullptr;
     ProfScope ps(h, kProfL0F32, sdirk_flops(sp, h->nx, L0.K, h->m));
-    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+    if (launch_l0_f32(h, sp) < 0) return MGRIT_ERR_UNSUPPORTED;
   } else {
     StencilParams<float>& sp = *h->fineMf;
     sp.in = L0.uCf[L0.curf];
@@ -1962,8 +2116,8 @@ static int l0f_fres(mgrit_handle* h, bool zero_guess, bool want_norm = false) {
     sp.K = L0.K;
     sp.traj = nullptr;
     ProfScope ps(h, kProfL0F32, sdirk_flops(sp, h->nx, L0.K, h->m));
-    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
-    if (want_norm) launch_reduce_sum(h->partials, L0.K * sp.csize, h->dnorm_f, h->st);
+    if (launch_l0_f32(h, sp) < 0) return MGRIT_ERR_UNSUPPORTED;
+    if (want_norm) launch_reduce_sum(h->partials, L0.K * (h->seg0f ? 1 : sp.csize), h->dnorm_f, h->st);
   } else {
     StencilParams<float>& sp = *h->fineMf;
     sp.in = L0.uCf[L0.curf];
@@ -2113,7 +2267,7 @@ static int l0_cf_fp32(mgrit_handle* h) {
     sp.K = K;
     sp.traj = nullptr;
     ProfScope ps(h, kProfL0F32, sdirk_flops(sp, nx, K, h->m));
-    if (launch_sdirk(sp, h->st) < 0) return MGRIT_ERR_UNSUPPORTED;
+    if (launch_l0_f32(h, sp) < 0) return MGRIT_ERR_UNSUPPORTED;
   } else {
     StencilParams<float> sp = *h->fineMf;
     sp.in = src;
@@ -2729,7 +2883,7 @@ int mgrit_residual(mgrit_handle* h, int level, double* norm_out) {
   if (norm_out) {
     CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
-    *norm_out = std::sqrt(std::max(0.0, *h->hnorm));
+    *norm_out = norm_of_sq(*h->hnorm);
   }
   return MGRIT_OK;
 }
@@ -2835,7 +2989,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
     if ((rc = l0_fres(h))) return rc;
     CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(cudaStreamSynchronize(h->st));
-    nrm = std::sqrt(std::max(0.0, *h->hnorm));
+    nrm = norm_of_sq(*h->hnorm);
     if (rc) return rc;
     while (true) {
       if (st.history_len < MGRIT_MAX_HISTORY) st.rnorm_history[st.history_len++] = nrm;
@@ -2878,7 +3032,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
           ++count;
           CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm_f, sizeof(double), cudaMemcpyDeviceToHost, h->st));
           CUDA_TRY(cudaStreamSynchronize(h->st));
-          const double rho = std::sqrt(std::max(0.0, *h->hnorm));
+          const double rho = norm_of_sq(*h->hnorm);
           go = inner_continue(rho, prev, rho0, count, kInnerMax, target);
           prev = rho;
         }
@@ -2890,7 +3044,7 @@ int mgrit_solve(mgrit_handle* h, const double* u0, double* u_out, mgrit_stats* s
       if (rc) return rc;
       CUDA_TRY(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->st));
       CUDA_TRY(cudaStreamSynchronize(h->st));
-      nrm = std::sqrt(std::max(0.0, *h->hnorm));
+      nrm = norm_of_sq(*h->hnorm);
       ++it;
       ++st.outer_iterations;
     }
@@ -3128,6 +3282,9 @@ int mgrit_level_info(const mgrit_handle* h, int level, double out[8]) {
     } else if (h->sdirk) {
       out[6] = (double)h->sd0->P;
       out[7] = (double)h->sd0->csize;
+    }
+    if (h->sdirk) {
+      out[5] = h->seg0f ? 1.0 : 0.0;  // MIXED: the FP32 segmented stage kernel runs
     } else {
       out[5] = (double)h->fineM->ntaps;
       out[4] = (double)h->fineM->persistent;

@@ -258,8 +258,12 @@ void launch_convert(int op, double* d, float* f, int64_t n, cudaStream_t st, con
   convert_kernel<<<blocks, 256, 0, st>>>(op, d, f, n, d2, f2);
 }
 
+// sqrt of a sum of squares with NaN kept: a NaN residual must stop the solve
+// as diverged, not read as zero (fmax would drop it)
+__device__ __forceinline__ double dev_norm_of_sq(double x) { return x == x ? sqrt(x > 0.0 ? x : 0.0) : x; }
+
 __global__ void solve_init_kernel(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd) {
-  const double nrm = sqrt(fmax(0.0, dnorm_sq[0]));
+  const double nrm = dev_norm_of_sq(dnorm_sq[0]);
   s->r0 = nrm;
   s->rnorm = nrm;
   s->it = 0;
@@ -281,7 +285,7 @@ __global__ void solve_init_kernel(DevSolveState* s, const double* dnorm_sq, cuda
 }
 
 __global__ void solve_check_kernel(DevSolveState* s, const double* dnorm_sq, cudaGraphConditionalHandle hnd) {
-  const double nrm = sqrt(fmax(0.0, dnorm_sq[0]));
+  const double nrm = dev_norm_of_sq(dnorm_sq[0]);
   s->it += 1;
   s->rnorm = nrm;
   if (s->hist_len < 128) s->hist[s->hist_len++] = nrm;
@@ -300,7 +304,7 @@ __global__ void solve_check_kernel(DevSolveState* s, const double* dnorm_sq, cud
 }
 
 __global__ void inner_init_kernel(DevSolveState* s, const double* dnorm64_sq, cudaGraphConditionalHandle hnd) {
-  const double rho0 = sqrt(fmax(0.0, dnorm64_sq[0]));
+  const double rho0 = dev_norm_of_sq(dnorm64_sq[0]);
   s->in_rho0 = rho0;
   s->in_prev = rho0;
   s->in_tol = inner_target(s->tol, s->r0, rho0, s->in_base);
@@ -310,7 +314,7 @@ __global__ void inner_init_kernel(DevSolveState* s, const double* dnorm64_sq, cu
 }
 
 __global__ void inner_check_kernel(DevSolveState* s, const double* dnormf_sq, cudaGraphConditionalHandle hnd) {
-  const double rho = sqrt(fmax(0.0, dnormf_sq[0]));
+  const double rho = dev_norm_of_sq(dnormf_sq[0]);
   s->in_count += 1;
   s->in_total += 1;
   const bool go = inner_continue(rho, s->in_prev, s->in_rho0, s->in_count, s->in_max, s->in_tol);

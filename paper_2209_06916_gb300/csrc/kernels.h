@@ -217,6 +217,32 @@ struct SdirkSegParams {
   double* partial;       // FRES: one slot per interval
 };
 size_t sdirk_seg_smem_bytes(int n);
+
+// The FP32 stage kernel of MIXED inner cycles (sdirk_seg32.cuh): one CTA per
+// interval, the three stage slots in shared memory, kSeg32Points per thread,
+// the mat-vec form of the stages (R_j += g L Y_i), warm-ups cut at 2^-27;
+// modes CF and FRES with the optional C-point rhs / sub of the FP32 paths.
+constexpr int kSeg32Points = 64;
+struct SdirkSeg32Params {
+  int n, T;
+  int rc1, rc2, ra1, ra2;
+  int c1, c2, a1, a2;    // section orders (the kernel's template)
+  int p1;                // L_p taps (the kernel's template: l(p) west, r(p) east)
+  int stages;            // 1 or 3
+  float cr, cd[2], ar, ad[2];
+  float ik;              // 1/kappa of the factorisation (applied after each solve)
+  float ltaps[8];
+  float g[3];            // -c a_10, -c a_20, -c a_21
+  int mode, zero_start, nsteps;
+  int64_t K;
+  const float* start;
+  const float* rhs;      // optional, rows k+1
+  float* out;            // CF / FRES: rows k+1
+  const float* sub;      // optional, rows k+1
+  double* partial;       // FRES: one slot per interval
+};
+size_t sdirk_seg32_smem_bytes(int n);
+int launch_sdirk_seg32(const SdirkSeg32Params& p, cudaStream_t st);
 // 1 on success, -1 on a launch error or an order the kernel lacks
 int launch_sdirk_seg(const SdirkSegParams& p, cudaStream_t st);
 // Chunk lengths the step kernels are compiled for (one chunk per thread).

@@ -1,0 +1,257 @@
+#pragma once
+// Level-0 SDIRK step kernel of MIXED inner cycles: FP32, one CTA per
+// CF-interval, the vector's three stage slots in shared memory, one segment
+// of S points per thread (Sec. 4.2-4.3: Phi = R_q(-c L_p) through the stages
+// of a stiffly accurate SDIRK method, q = 1 or 3).  The FP32 step keeps the
+// mat-vec form of the stages,
+//   R_j = u (j >= 1);  Y_i = (I + gamma c L_p)^{-1} R_i;
+//   R_j += -c a_ji L_p Y_i  (j > i);  u_new = Y_{s-1},
+// whose rounding leaves the refinement at FP64 accuracy.  The stage solves
+// run the factored recurrences over the thread's segment with warm-ups over
+// the neighbouring segments, as the FP64 kernel (sdirk_seg.cuh) does, with
+// the warm-ups cut where the neglected state falls below 2^-27 (below FP32
+// rounding); the mat-vec L_p Y_i takes its halo (l(p) points to the west,
+// r(p) to the east) from the neighbouring segments.  The slots' roles rotate
+// every step (the last stage's slot holds the next state), so no copy-back.
+// Data move as 4-float quads (segments padded to S + 4 values), the next
+// block of 8 points loading while the current one computes.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dsolve.cuh"
+#include "kernels.h"
+
+namespace mg {
+
+// One pass over `count` points (a multiple of 8) of a shared-memory segment
+// seg (16-byte aligned), ascending or descending: f(x) per point in pass
+// order, st(point index of the quad's first element, r0, r1, r2, r3) stores
+// the results of the quad (in memory order).
+template <bool DESC, typename F, typename ST>
+__device__ __forceinline__ void quad_pass(const float* seg, int count, F f, ST st) {
+  if (count <= 0) return;
+  auto ld = [&](int q) { return *reinterpret_cast<const float4*>(seg + 4 * q); };  // quad q
+  const int nq = count >> 2;
+  auto qidx = [&](int i) { return DESC ? nq - 1 - i : i; };  // pass quad i -> memory quad
+  float4 a[2], b[2];
+  auto run = [&](int i0, const float4 (&v)[2]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = qidx(i0 + h);
+      float r0, r1, r2, r3;
+      if (DESC) {
+        r3 = f(v[h].w);
+        r2 = f(v[h].z);
+        r1 = f(v[h].y);
+        r0 = f(v[h].x);
+      } else {
+        r0 = f(v[h].x);
+        r1 = f(v[h].y);
+        r2 = f(v[h].z);
+        r3 = f(v[h].w);
+      }
+      st(4 * q, r0, r1, r2, r3);
+    }
+  };
+  a[0] = ld(qidx(0));
+  a[1] = ld(qidx(1));
+  int i0 = 0;
+  for (; i0 + 4 <= nq; i0 += 4) {
+    b[0] = ld(qidx(i0 + 2));
+    b[1] = ld(qidx(i0 + 3));
+    run(i0, a);
+    if (i0 + 4 < nq) {
+      a[0] = ld(qidx(i0 + 4));
+      a[1] = ld(qidx(i0 + 5));
+    }
+    run(i0 + 2, b);
+  }
+  if (i0 < nq) run(i0, a);
+}
+
+template <int STAGES, int C1, int C2, int A1, int A2, int HL, int HR, int S>
+__global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant__ SdirkSeg32Params A) {
+  extern __shared__ __align__(16) float smem32[];
+  constexpr int SP = S + 4;  // padded segment stride: 16-byte aligned, conflict-free quad columns
+  constexpr int P1 = HL + 1 + HR;
+  const int T = A.T, t = threadIdx.x, n = A.n;
+  const size_t slot = (size_t)T * SP;
+  float* const sl0 = smem32;
+  float* const sl1 = smem32 + slot;
+  float* const sl2 = smem32 + 2 * slot;
+  auto slot_of = [&](int i) { return i == 0 ? sl0 : (i == 1 ? sl1 : sl2); };
+  double* red = reinterpret_cast<double*>(smem32 + 3 * slot);
+  const int64_t k = blockIdx.x;
+  const int tl = (t == 0) ? T - 1 : t - 1;
+  const int tr = (t == T - 1) ? 0 : t + 1;
+  const int own = t * SP, lft = tl * SP, rgt = tr * SP;
+  const int rc1 = A.rc1, rc2 = A.rc2, ra1 = A.ra1, ra2 = A.ra2;
+  const float cr = A.cr, cd0 = A.cd[0], cd1 = A.cd[1];
+  const float ar = A.ar, ad0 = A.ad[0], ad1 = A.ad[1];
+  const float ik = A.ik;
+  float lt[P1];
+#pragma unroll
+  for (int a = 0; a < P1; ++a) lt[a] = A.ltaps[a];
+
+  {
+    float* w = sl0;
+    if (A.zero_start) {
+      for (int i = t; i < n; i += T) w[i + 4 * (i / S)] = 0.f;
+    } else {
+      const float* src = A.start + k * (int64_t)n;
+      for (int i = t; i < n; i += T) w[i + 4 * (i / S)] = src[i];
+    }
+  }
+  // the load above is strided over the whole vector: every segment is
+  // complete before a thread reads its own
+  __syncthreads();
+
+  float cy, cx1, cx2, au, av1, av2;
+  auto csec1 = [&](float b) {
+    if (!C1) return b;
+    cy = fmaf(cr, cy, b);
+    return cy;
+  };
+  auto csec2 = [&](float y) {
+    float x = y;
+    if (C2 >= 2) x = fmaf(cd1, cx2, x);
+    if (C2 >= 1) {
+      x = fmaf(cd0, cx1, x);
+      cx2 = cx1;
+      cx1 = x;
+    }
+    return x;
+  };
+  auto asec1 = [&](float b) {
+    if (!A1) return b;
+    au = fmaf(ar, au, b);
+    return au;
+  };
+  auto asec2 = [&](float u) {
+    float v = u;
+    if (A2 >= 2) v = fmaf(ad1, av2, v);
+    if (A2 >= 1) {
+      v = fmaf(ad0, av1, v);
+      av2 = av1;
+      av1 = v;
+    }
+    return v;
+  };
+  constexpr bool anti = (A1 + A2) > 0;
+  auto nost = [](int, float, float, float, float) {};
+
+  // solve of slot X in place: X = (1/kappa) U(X)
+  auto solve = [&](float* X) {
+    __syncthreads();  // every write of X is visible, every read of a neighbour's segment done
+    cy = cx1 = cx2 = 0.f;
+    quad_pass<false>(X + lft + S - rc1, rc1 - rc2, [&](float b) { return csec1(b); }, nost);
+    quad_pass<false>(X + lft + S - rc2, rc2, [&](float b) { return csec2(csec1(b)); }, nost);
+    __syncthreads();  // the neighbour's tail is read before it is overwritten
+    float* xo = X + own;
+    auto st4 = [&](int j, float r0, float r1, float r2, float r3) {
+      *reinterpret_cast<float4*>(xo + j) = make_float4(r0, r1, r2, r3);
+    };
+    quad_pass<false>(xo, S, [&](float b) { return csec2(csec1(b)); }, st4);
+    au = av1 = av2 = 0.f;
+    if (anti) {
+      __syncthreads();
+      quad_pass<true>(X + rgt + ra2, ra1 - ra2, [&](float b) { return asec1(b); }, nost);
+      quad_pass<true>(X + rgt, ra2, [&](float b) { return asec2(asec1(b)); }, nost);
+      __syncthreads();  // the neighbour's head is read before it is overwritten
+    }
+    quad_pass<true>(xo, S, [&](float b) { return ik * (anti ? asec2(asec1(b)) : b); }, st4);
+  };
+
+  // D1 += g1 L X, D2 += g2 L X over the own segment (D2 null: one target);
+  // the halo comes from the neighbouring segments of X
+  auto matvec = [&](const float* X, float* D1, float g1, float* D2, float g2) {
+    __syncthreads();  // X complete in every segment
+    float win[P1];
+#pragma unroll
+    for (int a = 0; a < HL; ++a) win[a] = X[lft + S - HL + a];
+    const float* xo = X + own;
+#pragma unroll
+    for (int a = 0; a < HR; ++a) win[HL + a] = xo[a];
+    float* d1 = D1 + own;
+    float* d2 = D2 ? D2 + own : nullptr;
+    // x_{j + HR} enters the window at point j; beyond the segment it is the
+    // right neighbour's head
+    auto tap = [&](int j, float xin) {
+      win[P1 - 1] = xin;
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < P1; ++a) acc = fmaf(lt[a], win[a], acc);
+#pragma unroll
+      for (int a = 0; a < P1 - 1; ++a) win[a] = win[a + 1];
+      (void)j;
+      return acc;
+    };
+    // points 0 .. S-1-HR take x_{j+HR} from the own segment, the last HR
+    // points from the right neighbour: run the pass over the own segment
+    // shifted by HR, the tail by hand
+    for (int j0 = 0; j0 < S; j0 += 4) {
+      float xin[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = j0 + u + HR;
+        xin[u] = jj < S ? xo[jj] : X[rgt + jj - S];
+      }
+      const float4 o1 = *reinterpret_cast<const float4*>(d1 + j0);
+      float4 r1;
+      float4 o2 = d2 ? *reinterpret_cast<const float4*>(d2 + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 r2 = o2;
+      const float t0 = tap(j0, xin[0]), t1 = tap(j0 + 1, xin[1]), t2 = tap(j0 + 2, xin[2]),
+                  t3 = tap(j0 + 3, xin[3]);
+      r1 = make_float4(fmaf(g1, t0, o1.x), fmaf(g1, t1, o1.y), fmaf(g1, t2, o1.z), fmaf(g1, t3, o1.w));
+      *reinterpret_cast<float4*>(d1 + j0) = r1;
+      if (d2) {
+        r2 = make_float4(fmaf(g2, t0, o2.x), fmaf(g2, t1, o2.y), fmaf(g2, t2, o2.z), fmaf(g2, t3, o2.w));
+        *reinterpret_cast<float4*>(d2 + j0) = r2;
+      }
+    }
+  };
+
+  int ia = 0;  // slot holding the state
+  for (int s = 0; s < A.nsteps; ++s) {
+    float* X0 = slot_of(ia);
+    if (STAGES == 1) {
+      solve(X0);
+    } else {
+      float* X1 = slot_of(ia == 2 ? 0 : ia + 1);
+      float* X2 = slot_of(ia == 0 ? 2 : ia - 1);
+      // R_1 = R_2 = u (own segment only; the previous step's last reads of
+      // these slots by neighbours ended before the barriers of its last solve)
+      for (int j = 0; j < S; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(X0 + own + j);
+        *reinterpret_cast<float4*>(X1 + own + j) = v;
+        *reinterpret_cast<float4*>(X2 + own + j) = v;
+      }
+      solve(X0);                                // Y_0
+      matvec(X0, X1, A.g[0], X2, A.g[1]);       // R_1, R_2 -= c a_j0 L Y_0
+      solve(X1);                                // Y_1
+      matvec(X1, X2, A.g[2], nullptr, 0.f);     // R_2 -= c a_21 L Y_1
+      solve(X2);                                // Y_2: the next state
+      ia = (ia == 0 ? 2 : ia - 1);
+    }
+  }
+  __syncthreads();
+  const float* w = slot_of(ia);
+  const int mode = A.mode;
+  float* orow = A.out + (mode == kModeAPPLY ? k : k + 1) * (int64_t)n;
+  const float* rh = A.rhs ? A.rhs + (k + 1) * (int64_t)n : nullptr;
+  const float* sb = A.sub ? A.sub + (k + 1) * (int64_t)n : nullptr;
+  double sq = 0.0;
+  for (int i = t; i < n; i += T) {
+    float v = w[i + 4 * (i / S)];
+    if (rh) v += rh[i];
+    if (sb) v -= sb[i];
+    orow[i] = v;
+    sq += (double)v * (double)v;
+  }
+  if (mode == kModeFRES && A.partial) {
+    const double tot = block_sum(sq, red);
+    if (t == 0) A.partial[k] = tot;
+  }
+}
+
+}  // namespace mg

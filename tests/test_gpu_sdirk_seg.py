@@ -155,3 +155,33 @@ def test_seg_full_size_solve(seg):
             assert err < 1e-10
         s.close()
     assert its[0] == its[1]
+
+
+@pytest.mark.parametrize("p,q,c,nx,m,levels,nt", [
+    (5, 3, 4.0, 16384, 16, 3, 16 * 16 * 2),   # 256 segments of 64 points
+    (3, 3, 5.0, 4096, 4, 3, 4 * 4 * 8),       # 64 segments
+    (1, 1, 1.0, 2048, 4, 3, 4 * 4 * 4),       # 32 segments, one stage
+    (5, 1, 3.0, 8192, 8, 3, 8 * 8 * 2),
+])
+def test_seg32_mixed_solve(seg, p, q, c, nx, m, levels, nt):
+    """MIXED inner cycles with the FP32 segmented stage kernel: the refined
+    solution within 1e-10 of sequential stepping, in as many refinement
+    steps (+-1) as with the chunked FP32 kernel."""
+    u0 = ic_fourier(nx, seed=4)
+    g = np.zeros((nt + 1, nx))
+    g[0] = u0
+    seq = omg.sequential(oops.FineOperator(p, "sdirk", q, c), g)[::m]
+    outer = {}
+    for pol in (1, 0):
+        seg(pol)
+        s = solver(nx, nt, c, p, q, m, levels, seed=2, precision=pkg.MIXED)
+        assert (s.level_info(0)[5] == 1.0) == (pol == 1)
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), out)
+        assert st["converged"]
+        err = _rel(host(out), seq)
+        print("FP32 segmented %d: %d refinement steps, error %.3e" % (pol, st["outer_iterations"], err))
+        assert err < 1e-10, err
+        outer[pol] = st["outer_iterations"]
+        s.close()
+    assert abs(outer[1] - outer[0]) <= 1
