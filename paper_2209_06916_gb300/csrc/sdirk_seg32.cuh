@@ -163,7 +163,10 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
   };
 
   // D1 += g1 L X, D2 += g2 L X over the own segment (D2 null: one target);
-  // the halo comes from the neighbouring segments of X
+  // the halo comes from the neighbouring segments of X.  x_{j+HR} enters
+  // the window at point j; X is read in quads (two at a time cover the
+  // points j .. j+3 + HR), the quad past the segment's end being the right
+  // neighbour's first
   auto matvec = [&](const float* X, float* D1, float g1, float* D2, float g2) {
     __syncthreads();  // X complete in every segment
     float win[P1];
@@ -174,40 +177,31 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
     for (int a = 0; a < HR; ++a) win[HL + a] = xo[a];
     float* d1 = D1 + own;
     float* d2 = D2 ? D2 + own : nullptr;
-    // x_{j + HR} enters the window at point j; beyond the segment it is the
-    // right neighbour's head
-    auto tap = [&](int j, float xin) {
+    auto tap = [&](float xin) {
       win[P1 - 1] = xin;
       float acc = 0.f;
 #pragma unroll
       for (int a = 0; a < P1; ++a) acc = fmaf(lt[a], win[a], acc);
 #pragma unroll
       for (int a = 0; a < P1 - 1; ++a) win[a] = win[a + 1];
-      (void)j;
       return acc;
     };
-    // points 0 .. S-1-HR take x_{j+HR} from the own segment, the last HR
-    // points from the right neighbour: run the pass over the own segment
-    // shifted by HR, the tail by hand
+    float4 qa = *reinterpret_cast<const float4*>(xo);
+#pragma unroll 4
     for (int j0 = 0; j0 < S; j0 += 4) {
-      float xin[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int jj = j0 + u + HR;
-        xin[u] = jj < S ? xo[jj] : X[rgt + jj - S];
-      }
+      const float* nb = (j0 + 4 < S) ? xo + j0 + 4 : X + rgt;
+      const float4 qb = *reinterpret_cast<const float4*>(nb);
       const float4 o1 = *reinterpret_cast<const float4*>(d1 + j0);
-      float4 r1;
-      float4 o2 = d2 ? *reinterpret_cast<const float4*>(d2 + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 r2 = o2;
-      const float t0 = tap(j0, xin[0]), t1 = tap(j0 + 1, xin[1]), t2 = tap(j0 + 2, xin[2]),
-                  t3 = tap(j0 + 3, xin[3]);
-      r1 = make_float4(fmaf(g1, t0, o1.x), fmaf(g1, t1, o1.y), fmaf(g1, t2, o1.z), fmaf(g1, t3, o1.w));
-      *reinterpret_cast<float4*>(d1 + j0) = r1;
+      const float e[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+      const float t0 = tap(e[HR]), t1 = tap(e[HR + 1]), t2 = tap(e[HR + 2]), t3 = tap(e[HR + 3]);
+      *reinterpret_cast<float4*>(d1 + j0) =
+          make_float4(fmaf(g1, t0, o1.x), fmaf(g1, t1, o1.y), fmaf(g1, t2, o1.z), fmaf(g1, t3, o1.w));
       if (d2) {
-        r2 = make_float4(fmaf(g2, t0, o2.x), fmaf(g2, t1, o2.y), fmaf(g2, t2, o2.z), fmaf(g2, t3, o2.w));
-        *reinterpret_cast<float4*>(d2 + j0) = r2;
+        const float4 o2 = *reinterpret_cast<const float4*>(d2 + j0);
+        *reinterpret_cast<float4*>(d2 + j0) =
+            make_float4(fmaf(g2, t0, o2.x), fmaf(g2, t1, o2.y), fmaf(g2, t2, o2.z), fmaf(g2, t3, o2.w));
       }
+      qa = qb;
     }
   };
 
