@@ -167,11 +167,30 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
   const double cr = A.cr, cd0 = A.cd[0], cd1 = A.cd[1];
   const double ar = A.ar, ad0 = A.ad[0], ad1 = A.ad[1];
 
-  if (A.zero_start) {
-    for (int i = t; i < n; i += T) w[i + 2 * (i / S)] = 0.0;
-  } else {
+  // rows of global memory move as 16-byte pairs when the pointers allow it
+  // (a test uniform over the CTA), in batches of independent loads so that
+  // their latencies overlap
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  auto sidx = [&](int i) { return i + 2 * (i / S); };  // vector element -> segment slot
+  constexpr int NPR = S / 2;                              // pairs per thread (n = S T)
+  constexpr int PB = 8;                                   // pairs per batch
+  static_assert(NPR % PB == 0, "segment length");
+  {
     const double* src = A.start + k * (int64_t)n;
-    for (int i = t; i < n; i += T) w[i + 2 * (i / S)] = src[i];
+    if (A.zero_start) {
+      for (int i = t; i < n; i += T) w[sidx(i)] = 0.0;
+    } else if (al16(src)) {
+      const double2* s2 = reinterpret_cast<const double2*>(src);
+      for (int j0 = 0; j0 < NPR; j0 += PB) {
+        double2 v[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) v[u] = s2[t + (j0 + u) * T];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) *reinterpret_cast<double2*>(w + sidx(2 * (t + (j0 + u) * T))) = v[u];
+      }
+    } else {
+      for (int i = t; i < n; i += T) w[sidx(i)] = src[i];
+    }
   }
 
   // causal recurrence, two cascaded sections: y_i = b_i + cr y_{i-1},
@@ -295,11 +314,35 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
   if (mode == kModeCF || mode == kModeFRES || mode == kModeAPPLY) {
     const double* sb = (mode == kModeFRES && A.sub) ? A.sub + (k + 1) * (int64_t)n : nullptr;
     double sq = 0.0;
-    for (int i = t; i < n; i += T) {
-      double v = w[i + 2 * (i / S)];
-      if (sb) v -= sb[i];
-      orow[i] = v;
-      sq = fma(v, v, sq);
+    if (al16(orow) && (!sb || al16(sb))) {
+      const double2* sb2 = reinterpret_cast<const double2*>(sb);
+      double2* o2 = reinterpret_cast<double2*>(orow);
+      for (int j0 = 0; j0 < NPR; j0 += PB) {
+        double2 b[PB];
+        if (sb) {
+#pragma unroll
+          for (int u = 0; u < PB; ++u) b[u] = sb2[t + (j0 + u) * T];
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+          const int pr = t + (j0 + u) * T;
+          double2 v = *reinterpret_cast<const double2*>(w + sidx(2 * pr));
+          if (sb) {
+            v.x -= b[u].x;
+            v.y -= b[u].y;
+          }
+          o2[pr] = v;
+          sq = fma(v.x, v.x, sq);
+          sq = fma(v.y, v.y, sq);
+        }
+      }
+    } else {
+      for (int i = t; i < n; i += T) {
+        double v = w[sidx(i)];
+        if (sb) v -= sb[i];
+        orow[i] = v;
+        sq = fma(v, v, sq);
+      }
     }
     if (mode == kModeFRES && A.partial) {
       const double tot = block_sum(sq, red);

@@ -93,13 +93,29 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
 #pragma unroll
   for (int a = 0; a < P1; ++a) lt[a] = A.ltaps[a];
 
+  // rows of global memory move as 16-byte quads when the pointers allow it
+  // (a test uniform over the CTA), in batches of independent loads so that
+  // their latencies overlap
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  auto sidx = [&](int i) { return i + 4 * (i / S); };  // vector element -> slot index
+  constexpr int NQ = S / 4;                               // quads per thread (n = S T)
+  constexpr int QB = NQ < 8 ? NQ : 8;                     // quads per batch
   {
     float* w = sl0;
+    const float* src = A.start + k * (int64_t)n;
     if (A.zero_start) {
-      for (int i = t; i < n; i += T) w[i + 4 * (i / S)] = 0.f;
+      for (int i = t; i < n; i += T) w[sidx(i)] = 0.f;
+    } else if (al16(src)) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      for (int j0 = 0; j0 < NQ; j0 += QB) {
+        float4 v[QB];
+#pragma unroll
+        for (int u = 0; u < QB; ++u) v[u] = s4[t + (j0 + u) * T];
+#pragma unroll
+        for (int u = 0; u < QB; ++u) *reinterpret_cast<float4*>(w + sidx(4 * (t + (j0 + u) * T))) = v[u];
+      }
     } else {
-      const float* src = A.start + k * (int64_t)n;
-      for (int i = t; i < n; i += T) w[i + 4 * (i / S)] = src[i];
+      for (int i = t; i < n; i += T) w[sidx(i)] = src[i];
     }
   }
   // the load above is strided over the whole vector: every segment is
@@ -235,12 +251,46 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
   const float* rh = A.rhs ? A.rhs + (k + 1) * (int64_t)n : nullptr;
   const float* sb = A.sub ? A.sub + (k + 1) * (int64_t)n : nullptr;
   double sq = 0.0;
-  for (int i = t; i < n; i += T) {
-    float v = w[i + 4 * (i / S)];
-    if (rh) v += rh[i];
-    if (sb) v -= sb[i];
-    orow[i] = v;
-    sq += (double)v * (double)v;
+  if (al16(orow) && (!rh || al16(rh)) && (!sb || al16(sb))) {
+    const float4* rh4 = reinterpret_cast<const float4*>(rh);
+    const float4* sb4 = reinterpret_cast<const float4*>(sb);
+    float4* o4 = reinterpret_cast<float4*>(orow);
+    for (int j0 = 0; j0 < NQ; j0 += QB) {
+      float4 a[QB], b[QB];
+#pragma unroll
+      for (int u = 0; u < QB; ++u) {
+        if (rh) a[u] = rh4[t + (j0 + u) * T];
+        if (sb) b[u] = sb4[t + (j0 + u) * T];
+      }
+#pragma unroll
+      for (int u = 0; u < QB; ++u) {
+        const int qd = t + (j0 + u) * T;
+        float4 v = *reinterpret_cast<const float4*>(w + sidx(4 * qd));
+        if (rh) {
+          v.x += a[u].x;
+          v.y += a[u].y;
+          v.z += a[u].z;
+          v.w += a[u].w;
+        }
+        if (sb) {
+          v.x -= b[u].x;
+          v.y -= b[u].y;
+          v.z -= b[u].z;
+          v.w -= b[u].w;
+        }
+        o4[qd] = v;
+        sq += (double)v.x * (double)v.x + (double)v.y * (double)v.y + (double)v.z * (double)v.z +
+              (double)v.w * (double)v.w;
+      }
+    }
+  } else {
+    for (int i = t; i < n; i += T) {
+      float v = w[sidx(i)];
+      if (rh) v += rh[i];
+      if (sb) v -= sb[i];
+      orow[i] = v;
+      sq += (double)v * (double)v;
+    }
   }
   if (mode == kModeFRES && A.partial) {
     const double tot = block_sum(sq, red);
