@@ -294,6 +294,30 @@ def pretune_shapes(prms, max_s):
     return tuned, len(seen), time.perf_counter() - t0
 
 
+def served_sequential(prms, u0s, chunk=64, nstreams=32):
+    """GPU sequential stepping of the given requests (the served solves'
+    baseline): chunks of `chunk` requests, each chunk's solves stepped at
+    once over the batch's streams, chunks back to back.  Returns (DOF/s,
+    seconds)."""
+    import torch
+    import paper_2209_06916_gb300 as pkg
+    dof, secs = 0, 0.0
+    for i in range(0, len(prms), chunk):
+        ps = prms[i:i + chunk]
+        us = [torch.tensor(u, dtype=torch.float64, device="cuda") for u in u0s[i:i + chunk]]
+        outs = [torch.empty(p.nx, dtype=torch.float64, device="cuda") for p in ps]
+        b = pkg.Batch(ps, nstreams=nstreams)
+        b.sequential(us, outs)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.sequential(us, outs)
+        torch.cuda.synchronize()
+        secs += time.perf_counter() - t0
+        dof += sum(p.nx * p.nt for p in ps)
+        b.close()
+    return (dof / secs if secs > 0 else None), secs
+
+
 def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-11, seed=2000, pretune_s=0.0):
     """A Poisson stream of mixed solves (the batched mix plus 10% SDIRK5+U5
     at c in [2, 8]) through the native continuous-batching server with an
@@ -323,6 +347,10 @@ def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-
             nm = pkg.ERRORS.get(r["status"], str(r["status"]))
             statuses[nm] = statuses.get(nm, 0) + 1
     offered = float(sum(d["nx"] * d["nt"] for d in reqs))
+    # the completed requests stepped sequentially on the same GPU
+    done = [i for i, r in enumerate(res) if r["status"] == 0]
+    seq_rate, seq_s = served_sequential([prms[i] for i in done], [u0s[i] for i in done]) if done else (None, 0.0)
+    served_rate = st["dof_completed"] / st["wall_s"]
     return {"workload": "advection1d_serving_poisson%d" % int(rate), "value": st["dof_completed"] / st["wall_s"],
             "unit": UNIT, "arrival_rate_per_s": rate, "arrivals_s": duration, "window_s": st["wall_s"],
             "requests": len(reqs), "offered_dof_per_s": offered / duration, "hbm_budget_gb": budget_gb,
@@ -337,7 +365,11 @@ def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-
             "service_ms": {"p50": float(np.percentile(svc, 50)) if svc.size else None,
                            "p99": float(np.percentile(svc, 99)) if svc.size else None,
                            "note": "admission to completion"},
-            "failures": statuses}
+            "failures": statuses,
+            "sequential": {"value": seq_rate, "unit": UNIT, "seconds": seq_s, "requests": len(done),
+                           "note": "the completed requests by GPU sequential stepping, 64 at a time over 32 "
+                                   "streams"},
+            "served_over_sequential": (served_rate / seq_rate) if seq_rate else None}
 
 
 def run_serving(args):

@@ -927,6 +927,11 @@ static std::vector<Geom> chunk_geometries(int64_t n, int64_t minpts, int elem, F
 // best-scored candidate): set for the serving thread by mgrit_serve.
 static thread_local bool g_no_measure = false;
 void set_measured_tuning(bool on) { g_no_measure = !on; }
+// Setup that does not wait for the device (calling thread): mgrit_setup and
+// the solve-graph capture return once their device work is queued on the
+// handle's stream, which orders it before anything launched there later.
+static thread_local bool g_setup_nowait = false;
+void set_setup_nowait(bool on) { g_setup_nowait = on; }
 
 static bool tuning_on() {
   if (g_no_measure) return false;
@@ -2428,7 +2433,7 @@ static int capture_solve(mgrit_handle* h, cudaGraph_t g) {
   cudaGraph_t pro = nullptr;
   // capture on private streams (the legacy default stream cannot capture)
   cudaStream_t user = h->st, cap = nullptr, cap2 = nullptr;
-  if (cudaStreamSynchronize(user) != cudaSuccess ||
+  if ((!g_setup_nowait && cudaStreamSynchronize(user) != cudaSuccess) ||
       cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) {
     h->prof.on = prof;
@@ -2820,7 +2825,7 @@ int mgrit_setup(const mgrit_params* params, void* stream, mgrit_handle** out) {
     if (Lv.g) CUDA_TRY(cudaMemsetAsync(Lv.g, 0, row * (Lv.N + 1), h->st));
     if (Lv.gf) CUDA_TRY(cudaMemsetAsync(Lv.gf, 0, sizeof(float) * P.nx * ((l == 0 ? Lv.K : Lv.N) + 1), h->st));
   }
-  CUDA_TRY(cudaStreamSynchronize(h->st));
+  if (!g_setup_nowait) CUDA_TRY(cudaStreamSynchronize(h->st));
   *out = h.release();
   return MGRIT_OK;
 }
@@ -3320,17 +3325,34 @@ int mgrit_gmres_stats(mgrit_handle* h, int level, int64_t out[2]) {
 // Everything a graph-resident solve needs before its graph runs, enqueued
 // on st: the initial iterate (u0 and the random C-points, or the one already
 // set) and the device stop-test state.
+// u0 (n_x values, host or device) and the random initial iterate into level
+// 0, queued on st
+static int stage_u0(mgrit_handle* h, const double* u0, cudaStream_t st) {
+  LevelData& L0 = h->lev[0];
+  const size_t row = sizeof(double) * (size_t)h->nx;
+  int rc = copy_any(h->du0, u0, row, st);
+  if (rc) return rc;
+  launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, st);
+  ++h->launches;
+  CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, st));
+  L0.cur = 0;
+  h->have_initial = true;
+  return MGRIT_OK;
+}
+
+// The initial condition for the next mgrit_solve_async(h, NULL), queued on
+// the handle's stream; from device or pinned host memory nothing waits.
+int solve_stage_initial(mgrit_handle* h, const double* u0) {
+  if (!h || !u0 || h->graph_pending) return MGRIT_ERR_INVALID_ARG;
+  int rc = stage_u0(h, u0, h->st);
+  if (rc) return rc;
+  return check_launch();
+}
+
 static int solve_begin(mgrit_handle* h, const double* u0, cudaStream_t st) {
   int rc;
   if (u0) {
-    LevelData& L0 = h->lev[0];
-    const size_t row = sizeof(double) * (size_t)h->nx;
-    if ((rc = copy_any(h->du0, u0, row, st))) return rc;
-    launch_random_cpoints(L0.uC[0], h->du0, L0.K + 1, h->nx, h->m, h->prm.seed, st);
-    ++h->launches;
-    CUDA_TRY(cudaMemcpyAsync(L0.uC[1], h->du0, row, cudaMemcpyDeviceToDevice, st));
-    L0.cur = 0;
-    h->have_initial = true;
+    if ((rc = stage_u0(h, u0, st))) return rc;
   } else if (!h->have_initial) {
     return MGRIT_ERR_INVALID_ARG;
   }

@@ -22,3 +22,9 @@ void set_measured_tuning(bool on);
 // Build a handle's graph-resident solve now (mgrit_solve_async then only
 // launches it).
 int solve_graph_prepare(mgrit_handle* h);
+// mgrit_setup and solve-graph capture without waiting for the device, for
+// the calling thread (default off).
+void set_setup_nowait(bool on);
+// Queue the initial condition u0 (device or pinned host memory: nothing
+// waits) for the next mgrit_solve_async(h, NULL).
+extern "C" __attribute__((visibility("hidden"))) int solve_stage_initial(mgrit_handle* h, const double* u0);

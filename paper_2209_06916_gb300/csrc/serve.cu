@@ -170,8 +170,12 @@ struct SetupDone {
 
 class SetupWorker {
  public:
-  SetupWorker(const mgrit_params* params, const std::vector<cudaStream_t>* pool, int device)
-      : params_(params), pool_(pool), device_(device), th_([this] { run(); }) {}
+  // stage: pinned host memory of stage_len doubles per slot, through which
+  // an initial condition in pageable memory reaches the device
+  SetupWorker(const mgrit_params* params, const double* const* u0s, const std::vector<cudaStream_t>* pool,
+              double* stage, int64_t stage_len, int device)
+      : params_(params), u0s_(u0s), pool_(pool), stage_(stage), stage_len_(stage_len), device_(device),
+        th_([this] { run(); }) {}
   ~SetupWorker() {
     {
       std::lock_guard<std::mutex> lk(mu_);
@@ -200,9 +204,23 @@ class SetupWorker {
   }
 
  private:
+  // u0 as it can be copied without waiting: device or pinned memory as
+  // given, pageable memory through the slot's pinned stage
+  const double* stage_u0(int slot, int64_t req) {
+    const double* u0 = u0s_[req];
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, u0) == cudaSuccess && a.type != cudaMemoryTypeUnregistered) return u0;
+    cudaGetLastError();
+    double* dst = stage_ + (size_t)slot * (size_t)stage_len_;
+    std::memcpy(dst, u0, sizeof(double) * (size_t)params_[req].nx);
+    return dst;
+  }
   void run() {
     cudaSetDevice(device_);
     set_measured_tuning(false);
+    // setup, capture and the initial condition only queue device work on
+    // the slot's stream: nothing here waits behind the running solves
+    set_setup_nowait(true);
     for (;;) {
       SetupJob j;
       {
@@ -217,6 +235,7 @@ class SetupWorker {
       mgrit_handle* h = nullptr;
       int rc = mgrit_setup(&params_[j.req], (void*)(*pool_)[j.slot], &h);
       if (rc == MGRIT_OK) rc = solve_graph_prepare(h);
+      if (rc == MGRIT_OK) rc = solve_stage_initial(h, stage_u0(j.slot, j.req));
       const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       std::lock_guard<std::mutex> lk(mu_);
       done_.push_back(SetupDone{j.slot, j.req, h, rc, secs});
@@ -224,7 +243,10 @@ class SetupWorker {
     }
   }
   const mgrit_params* params_;
+  const double* const* u0s_;
   const std::vector<cudaStream_t>* pool_;
+  double* stage_;
+  int64_t stage_len_;
   int device_;
   std::mutex mu_;
   std::condition_variable cv_;
@@ -245,11 +267,19 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
     if (arrival_s[i] < arrival_s[i - 1]) return MGRIT_ERR_INVALID_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return MGRIT_ERR_CUDA;
+  int64_t max_nx = 1;
+  for (int64_t i = 0; i < count; ++i) max_nx = std::max<int64_t>(max_nx, params[i].nx);
+  double* stage = nullptr;
+  if (cudaMallocHost((void**)&stage, sizeof(double) * (size_t)max_nx * (size_t)max_inflight) != cudaSuccess) {
+    cudaGetLastError();
+    return MGRIT_ERR_OOM;
+  }
   std::vector<cudaStream_t> pool;
   for (int i = 0; i < max_inflight; ++i) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       for (auto q : pool) cudaStreamDestroy(q);
+      cudaFreeHost(stage);
       return MGRIT_ERR_CUDA;
     }
     pool.push_back(s);
@@ -293,7 +323,7 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
     if (rc == MGRIT_ERR_CUDA) rc_fatal = rc;
   };
   {
-    SetupWorker worker(params, &pool, device);
+    SetupWorker worker(params, u0s, &pool, stage, max_nx, device);
     while (finished < count) {
       const double t = now();
       if (t > time_limit_s) break;
@@ -306,7 +336,7 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
         sl.h = d.h;
         S.setup_s += d.secs;
         int rc = d.rc;
-        if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, u0s[sl.req]);
+        if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, nullptr);  // u0 staged by the worker
         if (rc) {
           finish(sl, rc, nullptr);
         } else {
@@ -384,7 +414,7 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
       sl.h = d.h;
       S.setup_s += d.secs;
       int rc = d.rc;
-      if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, u0s[sl.req]);
+      if (rc == MGRIT_OK) rc = mgrit_solve_async(sl.h, nullptr);  // u0 staged by the worker
       if (rc) {
         finish(sl, rc, nullptr);
       } else {
@@ -404,6 +434,7 @@ extern "C" int mgrit_serve(const mgrit_params* params, const double* const* u0s,
   S.backlog_end = (int64_t)pending.size() + (count - next);
   S.wall_s = now();
   for (auto q : pool) cudaStreamDestroy(q);
+  cudaFreeHost(stage);  // after every queued copy from it (this synchronises)
   if (st) *st = S;
   return rc_fatal;
 }
