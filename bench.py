@@ -318,6 +318,34 @@ def served_sequential(prms, u0s, chunk=64, nstreams=32):
     return (dof / secs if secs > 0 else None), secs
 
 
+def alone_equals_in_mix(prms, u0s, res, u_outs, idx):
+    """Each served request of idx that completed, solved again alone (same
+    parameters, measured tuning off as inside the server, so both take the
+    same launch geometry): are the C-points bitwise equal?"""
+    import paper_2209_06916_gb300 as pkg
+    old = os.environ.get("MGRIT_AUTOTUNE")
+    os.environ["MGRIT_AUTOTUNE"] = "0"
+    checked, equal = [], True
+    try:
+        for i in idx:
+            if res[i]["status"] != 0:
+                continue
+            s = pkg.Solver(prms[i])
+            want = np.zeros_like(u_outs[i])
+            s.solve(u0s[i], want, allow_unconverged=True)
+            s.close()
+            same = bool(np.array_equal(want, u_outs[i]))
+            equal = equal and same
+            checked.append({"request": int(i), "nx": int(prms[i].nx), "nt": int(prms[i].nt), "equal": same})
+    finally:
+        if old is None:
+            os.environ.pop("MGRIT_AUTOTUNE", None)
+        else:
+            os.environ["MGRIT_AUTOTUNE"] = old
+    return {"all_equal": equal if checked else None, "checked": checked,
+            "note": "bitwise, C-points of each request served in the mix against a standalone solve"}
+
+
 def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-11, seed=2000, pretune_s=0.0):
     """A Poisson stream of mixed solves (the batched mix plus 10% SDIRK5+U5
     at c in [2, 8]) through the native continuous-batching server with an
@@ -336,8 +364,15 @@ def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-
                                     nu=1, tol=tol, max_iter=60, precision=pkg.MIXED, seed=d["seed"]))
         u0s.append(ic_sin4_noise(d["nx"], seed=d["seed"]) if d["kind"] == "erk" else ic_fourier(d["nx"], d["seed"]))
     pre = pretune_shapes(prms, pretune_s) if pretune_s > 0 else (0, 0, 0.0)
+    # alone == in mix: the C-points of a few small early requests come back
+    # from the server and are compared with standalone solves below
+    early = sorted(range(min(64, len(prms))), key=lambda i: prms[i].nx * prms[i].nt)[:4]
+    u_outs = [None] * len(prms)
+    for i in early:
+        u_outs[i] = np.zeros((prms[i].nt // prms[i].m + 1, prms[i].nx))
     res, st = pkg.serve(prms, u0s, arrivals, budget_gb * 10 ** 9, max_inflight=inflight,
-                        time_limit_s=duration + drain)
+                        time_limit_s=duration + drain, u_outs=u_outs)
+    alone = alone_equals_in_mix(prms, u0s, res, u_outs, early)
     ok = [r for r in res if r["status"] == 0]
     lat = np.array([r["latency_ms"] for r in ok])
     svc = np.array([(r["finish_s"] - r["start_s"]) * 1e3 for r in ok])
@@ -369,7 +404,8 @@ def serving_record(duration, drain, inflight, rate=2000.0, budget_gb=80, tol=1e-
             "sequential": {"value": seq_rate, "unit": UNIT, "seconds": seq_s, "requests": len(done),
                            "note": "the completed requests by GPU sequential stepping, 64 at a time over 32 "
                                    "streams"},
-            "served_over_sequential": (served_rate / seq_rate) if seq_rate else None}
+            "served_over_sequential": (served_rate / seq_rate) if seq_rate else None,
+            "alone_equals_in_mix": alone}
 
 
 def run_serving(args):

@@ -181,14 +181,18 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
   // D1 += g1 L X, D2 += g2 L X over the own segment (D2 null: one target);
   // the halo comes from the neighbouring segments of X.  x_{j+HR} enters
   // the window at point j; X is read in quads (two at a time cover the
-  // points j .. j+3 + HR), the quad past the segment's end being the right
-  // neighbour's first
+  // points j .. j+3 + HR), the quads past the segment's end being the right
+  // neighbour's first.  The next step's quads of X and D are loaded before
+  // this step's results are stored (the compiler cannot move those loads
+  // above the stores itself: it does not know that the slots are disjoint)
   auto matvec = [&](const float* X, float* D1, float g1, float* D2, float g2) {
     __syncthreads();  // X complete in every segment
+    auto ld4 = [](const float* q) { return *reinterpret_cast<const float4*>(q); };
     float win[P1];
 #pragma unroll
     for (int a = 0; a < HL; ++a) win[a] = X[lft + S - HL + a];
     const float* xo = X + own;
+    const float* xr = X + rgt;
 #pragma unroll
     for (int a = 0; a < HR; ++a) win[HL + a] = xo[a];
     float* d1 = D1 + own;
@@ -202,22 +206,29 @@ __global__ void __launch_bounds__(256) sdirk_seg32_kernel(const __grid_constant_
       for (int a = 0; a < P1 - 1; ++a) win[a] = win[a + 1];
       return acc;
     };
-    float4 qa = *reinterpret_cast<const float4*>(xo);
+    static_assert(S % 4 == 0 && S >= 8, "segment length");
+    float4 qa = ld4(xo), qb = ld4(xo + 4);
+    float4 o1 = ld4(d1), o2 = d2 ? ld4(d2) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
     for (int j0 = 0; j0 < S; j0 += 4) {
-      const float* nb = (j0 + 4 < S) ? xo + j0 + 4 : X + rgt;
-      const float4 qb = *reinterpret_cast<const float4*>(nb);
-      const float4 o1 = *reinterpret_cast<const float4*>(d1 + j0);
+      const int jn = j0 + 8;  // quad after qb: own segment, else the right neighbour's 1st / 2nd
+      const float4 qc = ld4(jn < S ? xo + jn : xr + (jn - S));
+      float4 n1 = o1, n2 = o2;
+      if (j0 + 4 < S) {
+        n1 = ld4(d1 + j0 + 4);
+        if (d2) n2 = ld4(d2 + j0 + 4);
+      }
       const float e[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
       const float t0 = tap(e[HR]), t1 = tap(e[HR + 1]), t2 = tap(e[HR + 2]), t3 = tap(e[HR + 3]);
       *reinterpret_cast<float4*>(d1 + j0) =
           make_float4(fmaf(g1, t0, o1.x), fmaf(g1, t1, o1.y), fmaf(g1, t2, o1.z), fmaf(g1, t3, o1.w));
-      if (d2) {
-        const float4 o2 = *reinterpret_cast<const float4*>(d2 + j0);
+      if (d2)
         *reinterpret_cast<float4*>(d2 + j0) =
             make_float4(fmaf(g2, t0, o2.x), fmaf(g2, t1, o2.y), fmaf(g2, t2, o2.z), fmaf(g2, t3, o2.w));
-      }
       qa = qb;
+      qb = qc;
+      o1 = n1;
+      o2 = n2;
     }
   };
 
