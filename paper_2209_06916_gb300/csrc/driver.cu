@@ -1730,7 +1730,12 @@ static int sdirk_launch(mgrit_handle* h, int mode, int zero_start, const double*
   sp.every = every;
   sp.partial = (mode == kModeFRES) ? h->partials : nullptr;
   ProfScope ps(h, cat_flops, sdirk_flops(sp, h->nx, K, nsteps));
-  if (!base && h->seg0 && !traj && (mode == kModeCF || mode == kModeFRES || mode == kModeAPPLY)) {
+  // the segmented kernel keeps a stage vector in each output row and moves
+  // it in 16-byte pairs: it runs only on rows that start 16-byte aligned
+  // (rows of n_x % 128 == 0 values keep the base pointer's alignment); a
+  // caller's row views that do not go to the chunked kernel
+  const bool rows16 = (((uintptr_t)start | (uintptr_t)out | (uintptr_t)sub) & 15) == 0;
+  if (!base && h->seg0 && !traj && rows16 && (mode == kModeCF || mode == kModeFRES || mode == kModeAPPLY)) {
     SdirkSegParams gp = *h->seg0;
     gp.mode = mode;
     gp.zero_start = zero_start;

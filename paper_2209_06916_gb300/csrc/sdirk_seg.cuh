@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(128) sdirk_seg_kernel(const __grid_constant__ 
   const int64_t k = blockIdx.x;
   const int mode = A.mode;
   double* orow = A.out + (mode == kModeAPPLY ? k : k + 1) * (int64_t)n;
-  double* aux = orow;  // scratch until the final write
+  double* aux = orow;  // scratch until the final write (the host launches this kernel on 16-byte aligned rows only)
   const int tl = (t == 0) ? T - 1 : t - 1;
   const int tr = (t == T - 1) ? 0 : t + 1;
   // streams: own / left / right segments, own / left scratch pairs

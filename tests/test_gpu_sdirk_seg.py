@@ -71,6 +71,27 @@ def test_seg_step_matches_oracle(seg, p, q, c, nx):
     s.close()
 
 
+def test_seg_step_unaligned_rows(seg):
+    """Caller rows that start 8 bytes past a 16-byte boundary (views one
+    element into a buffer): the segmented kernel keeps a stage vector in the
+    output rows in 16-byte pairs, so the host sends such rows to the chunked
+    kernel instead, with the same result."""
+    seg(1)
+    p, q, c, nx, nv = 5, 3, 4.0, 4096, 5
+    s = solver(nx, 64, c, p, q, 4, 2)
+    assert s.level_info(0)[4] == 2.0
+    x = np.random.default_rng(9).standard_normal((nv, nx))
+    xb = torch.zeros(nv * nx + 1, dtype=torch.float64, device="cuda")
+    xb[1:] = dev(x).reshape(-1)
+    yb = torch.full((nv * nx + 1,), np.nan, dtype=torch.float64, device="cuda")
+    xv, yv = xb[1:], yb[1:]
+    assert xv.data_ptr() % 16 == 8 and yv.data_ptr() % 16 == 8
+    s.coarse_apply(0, xv, yv, nv)
+    want = oops.FineOperator(p, "sdirk", q, c).apply(x)
+    assert _rel(host(yv).reshape(nv, nx), want) < 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("p,q,c,nx", [(5, 3, 8.0, 4096), (1, 1, 4.0, 4096), (5, 3, 4.0, 1024), (5, 5, 4.0, 4096),
                                       (5, 3, 4.0, 32768)])
 def test_seg_not_used_where_it_does_not_fit(seg, p, q, c, nx):
