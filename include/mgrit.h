@@ -60,7 +60,8 @@ extern "C" {
                       /* error correction solves                              */
 #define MGRIT_MIXED_FAST 2 /* as MGRIT_MIXED, but the correction solves run  */
                       /* in FP32 on levels whose correction matrix has        */
-                      /* condition number <= 1e3 (FP64 on the others)         */
+                      /* condition number <= 1e6 (FP64 on the others; the     */
+                      /* environment variable MGRIT_FAST_KAPPA sets the bound) */
 
 #define MGRIT_MAX_LEVELS 16
 #define MGRIT_COARSE_SL_CORRECTED 0
