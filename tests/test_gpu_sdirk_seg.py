@@ -206,3 +206,23 @@ def test_seg32_mixed_solve(seg, p, q, c, nx, m, levels, nt):
         outer[pol] = st["outer_iterations"]
         s.close()
     assert abs(outer[1] - outer[0]) <= 1
+
+
+@pytest.mark.parametrize("precision", [pkg.FP64, pkg.MIXED])
+def test_seg_solve_is_deterministic(seg, precision):
+    """The same solve in two handles through the segmented kernels: bitwise
+    equal C-points and residual histories (fixed-order sums, no atomics on
+    the data path)."""
+    seg(1)
+    p, q, c, m, levels, nx, nt = 5, 3, 4.0, 16, 3, 4096, 16 * 16 * 2
+    u0 = ic_fourier(nx, seed=6)
+    runs = []
+    for _ in range(2):
+        s = solver(nx, nt, c, p, q, m, levels, seed=4, precision=precision)
+        assert s.level_info(0)[4] == 2.0
+        out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        st = s.solve(dev(u0), out)
+        runs.append((host(out), st["history"]))
+        s.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
