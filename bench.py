@@ -236,6 +236,24 @@ def batched_record(count, steps, warmup, tol=1e-11):
         ref = outs[i].cpu().numpy()
         err = max(err, float(np.max(np.abs(last - ref)) / np.max(np.abs(ref))))
     b.close()
+    # plain FP64 single-solve MGRIT on a sample of the same problems (every
+    # 8th), one solve at a time after a warm-up solve of each
+    single_dof, single_s = 0, 0.0
+    for i in range(0, count, 8):
+        d = mix[i]
+        p64 = pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=tol,
+                              max_iter=60, precision=pkg.FP64, seed=d["seed"])
+        s = pkg.Solver(p64)
+        out = torch.empty((d["nt"] // d["m"] + 1, d["nx"]), dtype=torch.float64, device="cuda")
+        s.solve(u0s[i], out, allow_unconverged=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.solve(u0s[i], out, allow_unconverged=True)
+        torch.cuda.synchronize()
+        single_s += time.perf_counter() - t0
+        single_dof += d["nx"] * d["nt"]
+        s.close()
+    single_rate = single_dof / single_s
     # FP64 floor: every refinement step needs one FP64 level-0 residual, the
     # composite stencil Phi^m over all intervals; for ERKp+Up its flops per
     # space-time point equal those of one explicit step (2 p^2 taps' worth,
@@ -258,7 +276,10 @@ def batched_record(count, steps, warmup, tol=1e-11):
             "max_rel_err_final_row_vs_sequential": err, "err_sample": "every %d-th solve" % max(1, count // 8),
             "sequential": {"value": dof / sdt, "unit": UNIT, "ms": sdt * 1e3,
                            "kernel": "seq_kernel per solve, all solves over the 32 streams"},
-            "mgrit_over_sequential": sdt / dt}
+            "mgrit_over_sequential": sdt / dt,
+            "fp64_single_solve": {"value": single_rate, "unit": UNIT, "sample": "every 8th problem, %d solves "
+                                  "one at a time in FP64" % len(range(0, count, 8)), "seconds": single_s},
+            "mgrit_over_fp64_single_solve": (dof / dt) / single_rate}
 
 
 def run_batched(args):
