@@ -189,19 +189,26 @@ def cpu_baseline(w, sample_nt, workers=None):
                       % (workers, w["nx"], sample_nt, sample_nt, w["nt"], levels, its[0], its[-1], wall)}
 
 
-def batched_record(count, steps, warmup, tol=1e-11):
+def batched_record(count, steps, warmup, tol=1e-11, implicit=False):
     """The batched workload: `count` independent solves (nx, nt, p, c, m
-    mixed; ERK of matching order), FP32 relaxation in FP64 refinement,
-    captured into one CUDA graph and run with one launch; against GPU
-    sequential stepping of the same problems, all at once over the batch's
-    streams.  value = total DOF / batch time."""
+    mixed; ERK of matching order, or with implicit=True SDIRK of order
+    min(p, 3)), FP32 relaxation in FP64 refinement, captured into one CUDA
+    graph and run with one launch; against GPU sequential stepping of the
+    same problems, all at once over the batch's streams, and against FP64
+    single-solve MGRIT of a sample.  value = total DOF / batch time."""
     import torch
     import paper_2209_06916_gb300 as pkg
-    from workloads import batch_mix, ic_sin4_noise
-    mix = batch_mix(count, seed=1000)
-    prms = [pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=tol,
-                            max_iter=60, precision=pkg.MIXED, seed=d["seed"]) for d in mix]
-    u0s = [torch.tensor(ic_sin4_noise(d["nx"], seed=d["seed"]), dtype=torch.float64, device="cuda") for d in mix]
+    from workloads import batch_mix, batch_mix_sdirk, ic_fourier, ic_sin4_noise
+    kind = pkg.SDIRK if implicit else pkg.ERK
+    if implicit:
+        mix = batch_mix_sdirk(count, seed=3000)
+        u0h = [ic_fourier(d["nx"], seed=d["seed"]) for d in mix]
+    else:
+        mix = batch_mix(count, seed=1000)
+        u0h = [ic_sin4_noise(d["nx"], seed=d["seed"]) for d in mix]
+    prms = [pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=kind, q=d.get("q", d["p"]), m=d["m"], levels=0,
+                            nu=1, tol=tol, max_iter=60, precision=pkg.MIXED, seed=d["seed"]) for d in mix]
+    u0s = [torch.tensor(u, dtype=torch.float64, device="cuda") for u in u0h]
     t0 = time.perf_counter()
     b = pkg.Batch(prms, nstreams=32)
     setup_s = time.perf_counter() - t0
@@ -241,8 +248,8 @@ def batched_record(count, steps, warmup, tol=1e-11):
     single_dof, single_s = 0, 0.0
     for i in range(0, count, 8):
         d = mix[i]
-        p64 = pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=pkg.ERK, m=d["m"], levels=0, nu=1, tol=tol,
-                              max_iter=60, precision=pkg.FP64, seed=d["seed"])
+        p64 = pkg.make_params(d["nx"], d["nt"], d["cfl"], d["p"], kind=kind, q=d.get("q", d["p"]), m=d["m"], levels=0,
+                              nu=1, tol=tol, max_iter=60, precision=pkg.FP64, seed=d["seed"])
         s = pkg.Solver(p64)
         out = torch.empty((d["nt"] // d["m"] + 1, d["nx"]), dtype=torch.float64, device="cuda")
         s.solve(u0s[i], out, allow_unconverged=True)
@@ -262,30 +269,37 @@ def batched_record(count, steps, warmup, tol=1e-11):
     # peak this bounds the batch time from below whatever the FP32 and coarse
     # work cost.
     sweeps = [x["outer_iterations"] + 1 for x in st]
-    fl = [2.0 * min(d["m"] * d["p"] ** 2 + 1, d["nx"]) * d["nx"] * (d["nt"] // d["m"]) for d in mix]
-    floor_s = sum(k * f for k, f in zip(sweeps, fl)) / (0.8 * FP64_PEAK_FLOPS)
-    return {"workload": "advection1d_batched_%d_erk_mixed" % count, "value": dof / dt, "unit": UNIT,
-            "fp64_residual_sweeps": {"median": float(np.median(sweeps)), "max": int(max(sweeps)),
-                                     "floor_ms": floor_s * 1e3,
-                                     "floor_over_sequential": (floor_s * 1e3) / (sdt * 1e3),
-                                     "note": "FP64 residual sweeps alone at 0.8 of the FP64 peak; each sweep has "
-                                             "the flops of the whole sequential solve"},
+    if implicit:  # the explicit-step argument does not apply
+        floor = {"median": float(np.median(sweeps)), "max": int(max(sweeps)), "floor_ms": None,
+                 "floor_over_sequential": None, "note": "implicit steps: a residual sweep costs far less than the "
+                                                       "sequential solve's dependent stage solves"}
+    else:
+        fl = [2.0 * min(d["m"] * d["p"] ** 2 + 1, d["nx"]) * d["nx"] * (d["nt"] // d["m"]) for d in mix]
+        floor_s = sum(k * f for k, f in zip(sweeps, fl)) / (0.8 * FP64_PEAK_FLOPS)
+        floor = {"median": float(np.median(sweeps)), "max": int(max(sweeps)), "floor_ms": floor_s * 1e3,
+                 "floor_over_sequential": (floor_s * 1e3) / (sdt * 1e3),
+                 "note": "FP64 residual sweeps alone at 0.8 of the FP64 peak; each sweep has the flops of the whole "
+                         "sequential solve"}
+    return {"workload": "advection1d_batched_%d_%s_mixed" % (count, "sdirk" if implicit else "erk"),
+            "value": dof / dt, "unit": UNIT,
+            "fp64_residual_sweeps": floor,
             "ms_per_batch": dt * 1e3, "batches_timed": steps, "solves": count, "dof_total": dof,
             "converged": conv, "iterations_median": float(np.median(its)), "iterations_max": int(max(its)),
             "tol": tol, "setup_s": setup_s, "launch": "one CUDA graph, one branch per solve",
             "max_rel_err_final_row_vs_sequential": err, "err_sample": "every %d-th solve" % max(1, count // 8),
             "sequential": {"value": dof / sdt, "unit": UNIT, "ms": sdt * 1e3,
-                           "kernel": "seq_kernel per solve, all solves over the 32 streams"},
+                           "kernel": "one sequential-stepping cluster per solve, all solves over the 32 streams"},
             "mgrit_over_sequential": sdt / dt,
             "fp64_single_solve": {"value": single_rate, "unit": UNIT, "sample": "every 8th problem, %d solves "
                                   "one at a time in FP64" % len(range(0, count, 8)), "seconds": single_s},
             "mgrit_over_fp64_single_solve": (dof / dt) / single_rate}
 
 
-def run_batched(args):
+def run_batched(args, implicit=False):
     import torch
     torch.cuda.set_device(0)
-    rec = batched_record(args.count, args.steps, args.warmup)
+    count = 128 if implicit and args.count == 512 else args.count
+    rec = batched_record(count, args.steps, args.warmup, implicit=implicit)
     line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": rec["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 relax / f64 residual", "data": "synthetic",
@@ -974,7 +988,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["c4", "c5", "coarse_ops", "table3",
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["c4", "c4_sdirk", "c5", "coarse_ops", "table3",
                                                                       "parallel_problems"])
     ap.add_argument("--count", type=int, default=512, help="c4: number of solves")
     ap.add_argument("--duration", type=float, default=60.0, help="c5: seconds of arrivals")
@@ -1003,8 +1017,8 @@ def main():
                     help="correction solves of the coarse operator (gmres: Sec. 6.3's GMRES)")
     args = ap.parse_args()
     global WORKLOAD
-    if args.workload == "c4" and args.impl == "ours":
-        return run_batched(args)
+    if args.workload in ("c4", "c4_sdirk") and args.impl == "ours":
+        return run_batched(args, implicit=args.workload == "c4_sdirk")
     if args.workload == "c5" and args.impl == "ours":
         return run_serving(args)
     if args.workload == "coarse_ops" and args.impl == "ours":

@@ -11,6 +11,8 @@ the oracle draw their inputs from here.
   ic_fourier(nx, seed)     sum_{k=1}^{20} (a_k cos(pi k x) + b_k sin(pi k x))/k^2,
                            a_k, b_k ~ N(0, 1): a smooth periodic random IC
   batch_mix(count, seed)   parameter sets of the 512-solve batched workload
+  batch_mix_sdirk(count, seed)  an implicit batch: SDIRK with upwind order
+                           p in {1, 3, 5} (stage order q = min(p, 3))
 """
 import numpy as np
 
@@ -85,3 +87,19 @@ def serving_stream(rate, duration, seed, sdirk_fraction=0.1, nx_max_sdirk=65536,
         reqs.append(req)
         i += 1
     return np.array(arrivals), reqs
+
+
+def batch_mix_sdirk(count, seed, nx_choices=(1024, 2048, 4096, 8192), nt_choices=(1024, 2048, 4096, 8192),
+                    orders=(1, 3, 5), cfl_range=(1.0, 4.0), m_choices=(4, 8, 16)):
+    """Independent implicit problems: nx, nt powers of two, upwind order p
+    with SDIRK of order q = min(p, 3), CFL uniform in cfl_range, coarsening
+    factor m, per-solve seed = seed + index."""
+    r = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        p = int(r.choice(orders))
+        out.append({
+            "nx": int(r.choice(nx_choices)), "nt": int(r.choice(nt_choices)), "p": p, "q": min(p, 3),
+            "cfl": float(r.uniform(*cfl_range)), "m": int(r.choice(m_choices)), "seed": seed + i,
+        })
+    return out
