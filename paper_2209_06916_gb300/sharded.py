@@ -204,7 +204,10 @@ class ShardedSolver:
         for _ in range(self.params.nu):
             self.ex.c_relax()
             self._exchange_boundary()
-        return math.sqrt(max(0.0, self._all_sum(self.ex.residual())))
+        sq = self._all_sum(self.ex.residual())
+        # a NaN sum stays NaN (the stop test reads it as divergence); only a
+        # rounding-negative sum is clamped
+        return math.sqrt(sq) if sq >= 0.0 else (sq if math.isnan(sq) else 0.0)
 
     def solve(self, u0):
         """Solve from the initial condition u0 (host array or tensor of nx

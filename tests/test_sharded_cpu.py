@@ -185,3 +185,51 @@ def test_failed_rank_surfaces_as_error_on_the_others():
         p.join(timeout=60)
     assert got[1] == "RuntimeError"
     assert got[0] != "finished"
+
+
+def _rank_nan(rank, world, port, q):
+    """Rank 1's residual turns NaN after the first iteration: every rank
+    must stop with the divergence status, not read the norm as zero."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import sys
+    sys.path.insert(0, ROOT)
+    import paper_2209_06916_gb300 as pkg
+    from paper_2209_06916_gb300.sharded import ShardedSolver
+    from workloads import ic_sin4
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        case = CASES["erk3_vcycle"]
+        kind, p, qq, c, m, levels, nu, nx, nt, seed = case
+        prm = pkg.make_params(nx, nt, c, p, m=m, levels=levels, nu=nu, tol=1e-10, max_iter=40, seed=seed)
+        ex = OracleExecutor(case, rank, world)
+        if rank == 1:
+            calls = {"n": 0}
+            plain = ex.residual
+
+            def residual():
+                calls["n"] += 1
+                v = plain()
+                return float("nan") if calls["n"] > 1 else v
+            ex.residual = residual
+        s = ShardedSolver(prm, executor=ex, comm_device="cpu", timeout_s=60.0)
+        _, st = s.solve(ic_sin4(nx))
+        q.put((rank, st))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def test_nan_residual_is_divergence_on_every_rank():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_nan, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, st in got.items():
+        assert st["status"] == -4 and not st["converged"], (rank, st["status"])
+        assert st["iterations"] == 1
